@@ -1,0 +1,450 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU needed).
+
+Each test pins one oracle function to something other than itself: the paper's worked example,
+closed forms, an independent formula, brute force on tiny meshes, or an invariant.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dense_from_csr(rp, col, val, n):
+    A = np.zeros((rp.size - 1, n))
+    for r in range(rp.size - 1):
+        A[r, col[rp[r]:rp[r + 1]]] = val[rp[r]:rp[r + 1]]
+    return A
+
+
+def brute_local(p, k=1.0):
+    """Local stiffness by inverting [x_i 1]: column i of the inverse holds lambda_i's coefficients."""
+    d = p.shape[1]
+    M = np.hstack([p, np.ones((d + 1, 1))])
+    Minv = np.linalg.inv(M)
+    G = Minv[:d, :].T  # rows: grad lambda_i
+    vol = abs(np.linalg.det(M)) / math.factorial(d)
+    return k * vol * G @ G.T, G, vol
+
+
+def random_simplex(rng, d):
+    while True:
+        p = rng.uniform(-1, 1, size=(d + 1, d))
+        det = np.linalg.det(p[1:] - p[0])  # d! times the signed measure
+        if abs(det) > 0.05:
+            if det < 0:  # positive orientation (Sec. 1.1): swap two vertices
+                p[[0, 1]] = p[[1, 0]]
+            return p
+
+
+# --- Sec. 2.1 / 2.2: sparse -----------------------------------------------------------------------
+
+def test_sparse_worked_example():
+    g = json.load(open(os.path.join(GOLDEN, "sparse_worked_example.json")))
+    I = np.array(g["i_1based"]) - 1
+    J = np.array(g["j_1based"]) - 1
+    rp, col, val = oracle.sparse(g["m"], g["n"], I, J, np.array(g["s"], float))
+    assert rp.tolist() == g["csr_row_ptr_0based"]
+    assert col.tolist() == g["csr_col_0based"]
+    assert val.tolist() == g["csr_val"]
+    A = dense_from_csr(rp, col, val, g["n"])
+    assert A.tolist() == g["dense"]
+    # CSC of the same matrix = CSR of its transpose: the column pointer printed in the paper
+    rpt, _, _ = oracle.sparse(g["n"], g["m"], J, I, np.array(g["s"], float))
+    assert (rpt + 1).tolist() == g["csc_colptr_1based"]
+
+
+def test_sparse_sums_duplicates_in_given_order():
+    I = np.array([2, 0, 2, 2, 1])
+    J = np.array([1, 0, 1, 1, 2])
+    S = np.array([1e16, 3.0, 1.0, -1e16, 5.0])
+    rp, col, val = oracle.sparse(3, 3, I, J, S)
+    assert rp.tolist() == [0, 1, 2, 3]
+    assert col.tolist() == [0, 2, 1]
+    # ((1e16 + 1) - 1e16) in the given order is 0 in double; any reordering that adds 1 last gives 1
+    assert val.tolist() == [3.0, 5.0, (1e16 + 1.0) - 1e16]
+
+
+def test_sparse_keeps_exact_zero_sums():
+    rp, col, val = oracle.sparse(2, 2, np.array([0, 0, 1]), np.array([1, 1, 1]), np.array([2.0, -2.0, 1.0]))
+    assert col.tolist() == [1, 1] and val.tolist() == [0.0, 1.0]
+
+
+# --- Sec. 3.1: local stiffness by three independent formulas --------------------------------------
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_local_stiffness_three_formulas(d):
+    rng = np.random.default_rng(7 + d)
+    for _ in range(200):
+        p = random_simplex(rng, d)
+        k = float(np.exp(rng.normal()))
+        elem = np.arange(d + 1, dtype=np.int32)[None, :]
+        rp, col, val, scale = oracle.assemble(d, p, elem, np.array([k]))
+        A = dense_from_csr(rp, col, val, d + 1)
+        B, _, _ = brute_local(p, k)
+        assert np.all(np.abs(A - B) <= 1e-13 * dense_from_csr(rp, col, scale, d + 1) + 1e-300)
+        if d == 2:
+            Aff = oracle.local_affine(p) * k
+            assert np.allclose(A, Aff, rtol=0, atol=1e-13 * np.abs(B).max())
+
+
+def test_local_affine_reference_triangle():
+    # reference triangle (1,0), (0,1), (0,0): At = 1/2 * [[1,0,-1],[0,1,-1],[-1,-1,2]]
+    At = oracle.local_affine(np.array([[1.0, 0.0], [0.0, 1.0], [0.0, 0.0]]))
+    assert At.tolist() == [[0.5, 0.0, -0.5], [0.0, 0.5, -0.5], [-0.5, -0.5, 1.0]]
+
+
+@pytest.mark.parametrize("d,n", [(2, 3), (3, 2)])
+def test_dense_elementwise_assembly(d, n):
+    """Sec. 3.1.1 element loop into a dense matrix, with brute-force local matrices."""
+    mesh = meshgen.square_mesh(n, 0.2, 11) if d == 2 else meshgen.kuhn_mesh(n, 0.1, 11)
+    node, elem = mesh["node"], mesh["elem"]
+    k = meshgen.lognormal(5, 3, elem.shape[0])
+    N = node.shape[0]
+    D = np.zeros((N, N))
+    for t, e in enumerate(elem):
+        At, _, _ = brute_local(node[e], k[t])
+        D[np.ix_(e, e)] += At
+    rp, col, val, scale = oracle.assemble(d, node, elem, k)
+    A = dense_from_csr(rp, col, val, N)
+    S = dense_from_csr(rp, col, scale, N)
+    assert np.all(np.abs(A - D) <= 1e-13 * S + 1e-300)
+    # pattern: structural pairs; the dense nonzero set lies inside it
+    P = dense_from_csr(rp, col, np.ones_like(val), N) > 0
+    assert not np.any((np.abs(D) > 1e-14) & ~P)
+    # the pattern is exactly the set of vertex pairs sharing an element
+    Q = np.zeros((N, N), bool)
+    for e in elem:
+        Q[np.ix_(e, e)] = True
+    assert np.array_equal(P, Q)
+
+
+# --- closed forms on uniform meshes ---------------------------------------------------------------
+
+def test_five_point_stencil_exact():
+    m = meshgen.make_config("c1")
+    n = m["n"]
+    rp, col, val, _ = oracle.assemble(2, m["node"], m["elem"])
+    assert rp[-1] == 29057
+    for j in range(1, n):
+        for i in range(1, n):
+            r = j * (n + 1) + i
+            c = col[rp[r]:rp[r + 1]] - r
+            v = val[rp[r]:rp[r + 1]]
+            assert c.tolist() == [-(n + 2), -(n + 1), -1, 0, 1, n + 1, n + 2]
+            assert v.tolist() == [0.0, -1.0, -1.0, 4.0, -1.0, -1.0, 0.0]
+
+
+def test_kuhn_stencil():
+    n = 4
+    m = meshgen.kuhn_mesh(n)
+    h = 1.0 / n
+    rp, col, val, scale = oracle.assemble(3, m["node"], m["elem"])
+    n1 = n + 1
+    for c3 in range(1, n):
+        for b3 in range(1, n):
+            for a3 in range(1, n):
+                r = a3 + n1 * (b3 + n1 * c3)
+                cols = col[rp[r]:rp[r + 1]] - r
+                v = val[rp[r]:rp[r + 1]]
+                assert cols.size == 15
+                exp = {0: 6 * h, 1: -h, -1: -h, n1: -h, -n1: -h, n1 * n1: -h, -n1 * n1: -h}
+                for cc, vv in zip(cols.tolist(), v.tolist()):
+                    assert abs(vv - exp.get(cc, 0.0)) <= 1e-15
+    # 24 incident tetrahedra per interior vertex
+    cnt = np.bincount(m["elem"].ravel(), minlength=n1 ** 3)
+    assert cnt[1 + n1 * (1 + n1 * 1)] == 24
+
+
+@pytest.mark.parametrize("d,n", [(2, 1), (2, 2), (2, 5), (2, 16), (3, 1), (3, 2), (3, 3), (3, 6)])
+def test_nnz_closed_form(d, n):
+    m = meshgen.square_mesh(n) if d == 2 else meshgen.kuhn_mesh(n)
+    N = m["node"].shape[0]
+    rp, col = oracle.pattern(d, N, m["elem"])
+    if d == 2:
+        exp = N + 2 * (3 * n * n + 2 * n)
+    else:
+        exp = N + 2 * (3 * n * (n + 1) ** 2 + 3 * n * n * (n + 1) + n ** 3)
+    assert rp[-1] == exp
+
+
+# --- invariants -------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_symmetry_rowsum_measure(d):
+    m = meshgen.square_mesh(12, 0.2, 3) if d == 2 else meshgen.kuhn_mesh(5, 0.1, 3)
+    node, elem = m["node"], m["elem"]
+    k = meshgen.lognormal(4, 3, elem.shape[0])
+    N = node.shape[0]
+    rp, col, val, scale = oracle.assemble(d, node, elem, k)
+    A = dense_from_csr(rp, col, val, N)
+    S = dense_from_csr(rp, col, scale, N)
+    assert np.all(np.abs(A - A.T) <= 1e-14 * S)
+    assert np.all(np.abs(A.sum(axis=1)) <= 1e-13 * S.sum(axis=1))
+    meas = oracle.measure(d, node, elem)
+    assert np.all(meas > 0)
+    assert abs(meas.sum() - 1.0) <= 1e-13
+    # positive semidefinite with the constants as kernel (Sec. 3.3, pure Neumann): rank N-1
+    w = np.linalg.eigvalsh(A)
+    assert w[0] > -1e-12 * w[-1] and w[1] > 1e-10 * w[-1]
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_linear_annihilation(d):
+    """Interior rows of A kill linear functions when the coefficient is constant."""
+    m = meshgen.square_mesh(10, 0.2, 5) if d == 2 else meshgen.kuhn_mesh(4, 0.1, 5)
+    node, elem, isbd = m["node"], m["elem"], m["is_bd"]
+    rp, col, val, _ = oracle.assemble(d, node, elem)
+    N = node.shape[0]
+    A = dense_from_csr(rp, col, val, N)
+    g = np.array([0.3, -1.7, 0.9][:d])
+    ell = 2.0 + node @ g
+    res = A @ ell
+    mag = np.abs(A) @ np.abs(ell)
+    assert np.all(np.abs(res[isbd == 0]) <= 1e-13 * mag[isbd == 0])
+    # and not for a boundary row in general
+    assert np.max(np.abs(res[isbd == 1])) > 1e-6
+
+
+def test_variable_k_does_not_annihilate():
+    m = meshgen.square_mesh(6, 0.2, 5)
+    k = meshgen.lognormal(1, 3, m["elem"].shape[0])
+    rp, col, val, _ = oracle.assemble(2, m["node"], m["elem"], k)
+    A = dense_from_csr(rp, col, val, m["node"].shape[0])
+    res = A @ (m["node"] @ np.array([1.0, 0.0]))
+    assert np.max(np.abs(res[m["is_bd"] == 0])) > 1e-3
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_mesh_relabelling_invariance(d):
+    """Sec. 1.1: any row permutation of elem and any even vertex permutation is the same mesh."""
+    m = meshgen.square_mesh(7, 0.2, 9) if d == 2 else meshgen.kuhn_mesh(3, 0.1, 9)
+    node, elem = m["node"], m["elem"]
+    k = meshgen.lognormal(2, 3, elem.shape[0])
+    rng = np.random.default_rng(0)
+    perm = rng.permutation(elem.shape[0])
+    even = [[0, 1, 2], [1, 2, 0], [2, 0, 1]] if d == 2 else [[0, 1, 2, 3], [1, 2, 0, 3], [0, 2, 3, 1], [1, 0, 3, 2]]
+    e2 = np.stack([elem[perm[t]][even[t % len(even)]] for t in range(elem.shape[0])])
+    rp1, c1, v1, s1 = oracle.assemble(d, node, elem, k)
+    rp2, c2, v2, _ = oracle.assemble(d, node, e2, k[perm])
+    assert np.array_equal(rp1, rp2) and np.array_equal(c1, c2)
+    assert np.all(np.abs(v1 - v2) <= 1e-13 * s1)
+
+
+def test_orientation_is_enforced():
+    m = meshgen.square_mesh(3)
+    e = m["elem"].copy()
+    e[4] = e[4][[1, 0, 2]]
+    with pytest.raises(RuntimeError):  # 2-D takes abs() of the area, so only zero area is rejected
+        oracle.assemble(2, np.zeros_like(m["node"]), e)
+    k3 = meshgen.kuhn_mesh(2)
+    e3 = k3["elem"].copy()
+    e3[5] = e3[5][[1, 0, 2, 3]]
+    with pytest.raises(RuntimeError):  # 3-D uses the signed volume
+        oracle.assemble(3, k3["node"], e3)
+    with pytest.raises(RuntimeError):
+        oracle.assemble(2, m["node"], np.array([[0, 1, 99]], np.int32))
+
+
+# --- Sec. 3.2 and Sec. 4: load vector --------------------------------------------------------------
+
+def quad_points_by_rule(d, p):
+    """Points of the rule (2-D: edge midpoints, point q opposite vertex q; 3-D: (a,b,b,b) rule)."""
+    if d == 2:
+        return np.stack([(p[(q + 1) % 3] + p[(q + 2) % 3]) / 2 for q in range(3)])
+    s5 = math.sqrt(5.0)
+    a, b = (5 + 3 * s5) / 20, (5 - s5) / 20
+    L = np.full((4, 4), b) + np.eye(4) * (a - b)
+    return L @ p
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_rhs_f1_closed_form(d):
+    m = meshgen.square_mesh(9, 0.2, 1) if d == 2 else meshgen.kuhn_mesh(4, 0.1, 1)
+    node, elem = m["node"], m["elem"]
+    b = oracle.rhs(d, node, elem)
+    meas = np.array([brute_local(node[e])[2] for e in elem])
+    exp = np.zeros(node.shape[0])
+    np.add.at(exp, elem.ravel(), np.repeat(meas / (d + 1), d + 1))
+    assert np.allclose(b, exp, rtol=1e-13, atol=0)
+    assert abs(b.sum() - 1.0) < 1e-13
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_rhs_linear_f_closed_form(d):
+    """int_tau f lambda_i = |tau|/((d+1)(d+2)) (sum_m f(x_m) + f(x_i)) for linear f."""
+    m = meshgen.square_mesh(6, 0.2, 2) if d == 2 else meshgen.kuhn_mesh(3, 0.1, 2)
+    node, elem = m["node"], m["elem"]
+    g, c = np.array([0.7, -0.4, 1.1][:d]), 0.35
+    fq = np.stack([quad_points_by_rule(d, node[e]) @ g + c for e in elem])
+    b = oracle.rhs(d, node, elem, oracle.F_QP, fq.ravel())
+    exp = np.zeros(node.shape[0])
+    for e in elem:
+        vol = brute_local(node[e])[2]
+        fv = node[e] @ g + c
+        exp[e] += vol / ((d + 1) * (d + 2)) * (fv.sum() + fv)
+    assert np.allclose(b, exp, rtol=1e-13, atol=1e-16)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_rule_exact_for_quadratics(d):
+    """Sec. 4: sum_i b_i = int_tau f exactly for quadratic f = (g.x + c)^2, by the barycentric formula
+    int lambda_i lambda_j = d! |tau| (1 + delta_ij) / (d+2)!."""
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        p = random_simplex(rng, d)
+        g, c = rng.normal(size=d), rng.normal()
+        a = p @ g + c
+        vol = brute_local(p)[2]
+        exact = math.factorial(d) * vol / math.factorial(d + 2) * (a.sum() ** 2 + (a ** 2).sum())
+        fq = (quad_points_by_rule(d, p) @ g + c) ** 2
+        b = oracle.rhs(d, p, np.arange(d + 1, dtype=np.int32)[None, :], oracle.F_QP, fq)
+        assert abs(b.sum() - exact) <= 1e-13 * max(1.0, abs(exact))
+    # a first-order rule would fail: the centroid value times |tau| misses the quadratic part
+    assert abs(vol * ((p.mean(axis=0) @ g + c) ** 2) - exact) > 1e-6
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_rhs_sinprod_matches_point_values(d):
+    m = meshgen.square_mesh(5, 0.2, 8) if d == 2 else meshgen.kuhn_mesh(3, 0.1, 8)
+    node, elem = m["node"], m["elem"]
+    fq = np.stack([np.prod(np.sin(np.pi * quad_points_by_rule(d, node[e])), axis=1) for e in elem])
+    b1 = oracle.rhs(d, node, elem, oracle.F_SINPROD)
+    b2 = oracle.rhs(d, node, elem, oracle.F_QP, fq.ravel())
+    assert np.allclose(b1, b2, rtol=1e-13, atol=1e-18)
+
+
+def test_sinpi_special_values():
+    # f = sin(pi x) sin(pi y) at (1/2, 1/6) is 1 * 1/2; at integers it is exactly 0
+    node = np.array([[0.5, 1.0 / 6.0], [0.5, 1.0 / 6.0], [0.5, 1.0 / 6.0]])
+    # a degenerate "element" is rejected, so probe f through a real one whose midpoints are known
+    p = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    fq = np.stack([np.prod(np.sin(np.pi * quad_points_by_rule(2, p)), axis=1)])
+    b = oracle.rhs(2, p, np.array([[0, 1, 2]], np.int32), oracle.F_SINPROD)
+    # midpoints (0.5,0.5), (0,0.5), (0.5,0): f = 1, 0, 0 exactly
+    assert fq[0, 0] == 1.0
+    assert b.tolist() == [0.5 * (0.0 + 0.0) / 6, 0.5 * (0.0 + 1.0) / 6, 0.5 * (1.0 + 0.0) / 6]
+    del node
+
+
+# --- Sec. 1.2 and 3.3: boundary and Dirichlet ------------------------------------------------------
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_boundary_whole_and_bdflag(d):
+    m = meshgen.square_mesh(7, 0.2, 4, permute=True) if d == 2 else meshgen.kuhn_mesh(3, 0.1, 4)
+    N = m["node"].shape[0]
+    assert np.array_equal(oracle.boundary(d, N, m["elem"]), m["is_bd"])
+    assert np.array_equal(oracle.boundary(d, N, m["elem"], m["bdflag"]), m["is_bd"])
+    # a partial flag marks only that side's vertices
+    bf = np.zeros_like(m["bdflag"])
+    t, i = np.argwhere(m["bdflag"] == 1)[0]
+    bf[t, i] = 1
+    mask = oracle.boundary(d, N, m["elem"], bf)
+    assert mask.sum() == d
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_dirichlet_reproduces_linear_solution(d):
+    """Sec. 3.3: with f = 0, k = 1 and linear g_D, the reduced solve returns the linear function."""
+    m = meshgen.square_mesh(8, 0.2, 6) if d == 2 else meshgen.kuhn_mesh(4, 0.1, 6)
+    node, elem = m["node"], m["elem"]
+    N = node.shape[0]
+    rp, col, val, _ = oracle.assemble(d, node, elem)
+    b = oracle.rhs(d, node, elem, oracle.F_CONST, np.array([0.0]))
+    isbd = oracle.boundary(d, N, elem)
+    gD = 0.5 - 1.3 * node[:, 0] + 0.8 * node[:, 1]
+    val2, b2, free = oracle.dirichlet(rp, col, val, b, isbd, gD)
+    assert np.array_equal(free, np.flatnonzero(isbd == 0))
+    A = dense_from_csr(rp, col, val, N)
+    u_free = np.linalg.solve(A[np.ix_(free, free)], b2[free])
+    assert np.allclose(u_free, gD[free], rtol=0, atol=1e-12)
+    # the eliminated square system gives the same solution everywhere
+    A2 = dense_from_csr(rp, col, val2, N)
+    assert np.allclose(np.linalg.solve(A2, b2), gD, rtol=0, atol=1e-12)
+    assert np.array_equal(A2, A2.T)
+    bd = np.flatnonzero(isbd)
+    assert np.array_equal(A2[bd], np.eye(N)[bd])
+    assert np.array_equal(b2[bd], gD[bd])
+
+
+def test_dirichlet_lift_is_b_minus_Au():
+    m = meshgen.square_mesh(5, 0.2, 2)
+    node, elem = m["node"], m["elem"]
+    N = node.shape[0]
+    k = meshgen.lognormal(3, 3, elem.shape[0])
+    rp, col, val, _ = oracle.assemble(2, node, elem, k)
+    b = oracle.rhs(2, node, elem, oracle.F_SINPROD)
+    isbd = m["is_bd"]
+    gD = np.cos(node[:, 0] * 3) + node[:, 1]
+    _, b2, _ = oracle.dirichlet(rp, col, val, b, isbd, gD)
+    u = np.where(isbd == 1, gD, 0.0)
+    exp = b - dense_from_csr(rp, col, val, N) @ u
+    free = isbd == 0
+    assert np.allclose(b2[free], exp[free], rtol=1e-14, atol=1e-15)
+
+
+# --- backward: closed-form adjoint vs finite differences and invariants ----------------------------
+
+def loss(d, node, elem, k, rp, col, fkind, w, r):
+    I, J, S, _ = oracle.triples(d, node, elem, k)
+    rp2, col2, val = oracle.sparse(node.shape[0], node.shape[0], I, J, S)
+    assert np.array_equal(rp2, rp) and np.array_equal(col2, col)
+    b = oracle.rhs(d, node, elem, fkind)
+    return float(w @ val + r @ b)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_backward_central_fd(d):
+    m = meshgen.square_mesh(3, 0.2, 12) if d == 2 else meshgen.kuhn_mesh(2, 0.1, 12)
+    node, elem = m["node"], m["elem"]
+    N, NT = node.shape[0], elem.shape[0]
+    k = meshgen.lognormal(12, 3, NT)
+    rp, col = oracle.pattern(d, N, elem)
+    slot = oracle.slots(d, N, elem, rp, col)
+    w = meshgen.normal(13, 4, rp[-1])
+    r = meshgen.normal(13, 5, N)
+    gn, gk = oracle.backward(d, node, elem, k, oracle.F_SINPROD, None, slot, w, r)
+    eps = 1e-6
+    for v in range(N):
+        for c in range(d):
+            xp, xm = node.copy(), node.copy()
+            xp[v, c] += eps
+            xm[v, c] -= eps
+            fd = (loss(d, xp, elem, k, rp, col, oracle.F_SINPROD, w, r)
+                  - loss(d, xm, elem, k, rp, col, oracle.F_SINPROD, w, r)) / (2 * eps)
+            assert abs(fd - gn[v, c]) <= 1e-6 * max(1.0, abs(gn[v, c])), (v, c, fd, gn[v, c])
+    for t in range(NT):
+        kp, km = k.copy(), k.copy()
+        kp[t] += eps
+        km[t] -= eps
+        fd = (loss(d, node, elem, kp, rp, col, oracle.F_SINPROD, w, r)
+              - loss(d, node, elem, km, rp, col, oracle.F_SINPROD, w, r)) / (2 * eps)
+        assert abs(fd - gk[t]) <= 1e-6 * max(1.0, abs(gk[t]))
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_backward_invariants(d):
+    """Stiffness part only (r = 0): translation invariance, homogeneity of degree d-2, and
+    k dL/dk = L element by element (a^tau is linear in k)."""
+    m = meshgen.square_mesh(6, 0.2, 14) if d == 2 else meshgen.kuhn_mesh(3, 0.1, 14)
+    node, elem = m["node"], m["elem"]
+    N, NT = node.shape[0], elem.shape[0]
+    k = meshgen.lognormal(14, 3, NT)
+    rp, col = oracle.pattern(d, N, elem)
+    slot = oracle.slots(d, N, elem, rp, col)
+    w = meshgen.normal(15, 4, rp[-1])
+    gn, gk = oracle.backward(d, node, elem, k, oracle.F_CONST, None, slot, w, np.zeros(N))
+    I, J, S, _ = oracle.triples(d, node, elem, k)
+    _, _, val = oracle.sparse(N, N, I, J, S)
+    L = float(w @ val)
+    scale = float(np.abs(gn).sum() + abs(L))
+    assert np.all(np.abs(gn.sum(axis=0)) <= 1e-12 * scale)
+    homog = float((node * gn).sum())
+    assert abs(homog - (d - 2) * L) <= 1e-12 * scale
+    assert abs(float(k @ gk) - L) <= 1e-12 * (abs(L) + float(np.abs(k * gk).sum()))
