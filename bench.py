@@ -1,0 +1,309 @@
+#!/usr/bin/env python3
+"""Benchmark: P1 assembly throughput (Melem/s, FP64) on the 2048^2 jittered, element-permuted
+triangle mesh (N = 4,198,401 vertices, NT = 8,388,608 elements, lognormal k, f = sin(pi x) sin(pi y)).
+
+A step is one pass of the value phase of the assembly on a built pattern: stiffness values and the
+load vector (one fem_assemble call), inputs resident in HBM. The pattern build (once per topology)
+is timed separately and reported as pattern_build_ms. e2e repeats the step through the same C ABI
+call with the inputs copied from pinned host memory and the outputs read back inside the timed
+region. The L2 is flushed (a 512 MB write) between timed steps, outside the timed events.
+
+--impl reference times the CPU oracle (the plain FP64 reference) on a bounded sample of the same
+workload, on this host's cores. Under torchrun each rank assembles its own copy of the mesh
+(independent problems, no data-path collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import meshgen  # noqa: E402
+
+METRIC = "P1 assembly Melem/s (FP64) + % HBM peak; batched & fwd+bwd vs plain fwd"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return float(j.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def algorithmic_bytes(d, N, NT, nnz):
+    """Minimum bytes of the value phase: elem, node (each vertex once), k, val, b."""
+    return NT * (d + 1) * 4 + N * d * 8 + NT * 8 + nnz * 8 + N * 8
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.rows, self.proc, self.idx = [], None, gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(mesh, f_kind, target_s=12.0):
+    """The oracle as it stands on a bounded sample (the first M elements of the same mesh), one core."""
+    import oracle
+    oracle.build()
+    d, node, elem, k = mesh["d"], mesh["node"], mesh["elem"], mesh["coef"]
+    NT = elem.shape[0]
+
+    def run(m):
+        e, kk = elem[:m], (None if k is None else k[:m])
+        t0 = time.perf_counter()
+        oracle.assemble(d, node, e, kk)
+        oracle.rhs(d, node, e, f_kind)
+        return time.perf_counter() - t0
+
+    m = min(NT, 100_000)
+    dt = run(m)
+    m2 = int(min(NT, max(m, m * target_s / max(dt, 1e-3))))
+    if m2 > m:
+        m, dt = m2, run(m2)
+    return {"value": m / dt / 1e6, "unit": "Melem/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d of %d elements of the same mesh (stiffness triples + sparse summation + "
+                      "load vector), single-threaded C, %.1f s" % (m, NT, dt)}
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+        return dist, dist.get_rank(), ws
+    return None, 0, 1
+
+
+def run_reference(args):
+    dist, rank, ws = dist_init(args)
+    if rank != 0:
+        return
+    mesh = meshgen.make_config(args.config)
+    import oracle
+    f_kind = oracle.F_SINPROD if mesh["f"] == "sinprod" else oracle.F_CONST
+    d, node, elem, k = mesh["d"], mesh["node"], mesh["elem"], mesh["coef"]
+    oracle.build()
+    m = min(elem.shape[0], args.ref_sample)
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.assemble(d, node, elem[:m], None if k is None else k[:m])
+        oracle.rhs(d, node, elem[:m], f_kind)
+        if it >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    v = m / (ms * 1e-3) / 1e6
+    line = {"metric": METRIC, "value": v, "unit": "Melem/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": workload_name(args.config), "sample_elements": m},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "Melem/s",
+                             "sample": "first %d elements of the mesh per step, single-threaded C oracle" % m},
+            "e2e": {"value": v, "unit": "Melem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_name(cfg):
+    return {"c1": "2-D unit square 64x64, uniform, k=1, f=1",
+            "c2": "2-D unit square 2048x2048, jittered 0.2h, element rows permuted, k~LN(0,1), f=sin(pi x)sin(pi y)",
+            "c3": "3-D unit cube 128^3 Kuhn tets, jittered 0.1h, k~LN(0,1), f=1"}[cfg]
+
+
+def run_ours(args):
+    import torch
+    import paper_1804_05156_gb300 as fa
+
+    dist, rank, ws = dist_init(args)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    fa.build()
+    mesh = meshgen.make_config(args.config)
+    d, node, elem, k = mesh["d"], mesh["node"], mesh["elem"], mesh["coef"]
+    N, NT = node.shape[0], elem.shape[0]
+    f_kind = fa.FEM_F_SINPROD if mesh["f"] == "sinprod" else fa.FEM_F_CONST
+    variant = fa.FEM_ATOMIC if args.variant == "atomic" else fa.FEM_DETERMINISTIC
+    s = torch.cuda.current_stream()
+
+    elem_d = torch.as_tensor(elem).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p = fa.Pattern(elem_d, N)
+    torch.cuda.synchronize()
+    pattern_ms = 1e3 * (time.perf_counter() - t0)
+
+    node_d = torch.as_tensor(node).cuda()
+    k_d = torch.as_tensor(k).cuda() if k is not None else None
+    val = torch.empty(p.nnz, dtype=torch.float64, device="cuda")
+    b = torch.empty(N, dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        fa.fem_assemble(p, node_d, k_d, f_kind, None, val, b, variant)
+
+    for _ in range(args.warmup):
+        step()
+    fa.get_error()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    fa.fem_timing_report()
+    fa.fem_timing_enable(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = fa.launch_count()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            evs[i][0].record(s)
+            step()
+            evs[i][1].record(s)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    launches = fa.launch_count() - l0
+    fa.fem_timing_enable(False)
+    kt = fa.fem_timing_report()
+    fa.get_error()
+    step_ms = [a.elapsed_time(bb) for a, bb in evs]
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * NT / (ms * 1e-3) / 1e6
+
+    # roofline of the dominant kernel: algorithmic bytes of the step / that kernel's mean duration
+    peak, peak_kind = peaks()
+    alg = algorithmic_bytes(d, N, NT, p.nnz)
+    dom = max(kt.items(), key=lambda kv: kv[1][1]) if kt else ("step", (args.steps, ms * args.steps))
+    dom_ms = dom[1][1] / dom[1][0]
+    achieved = alg / (dom_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": dom[0], "kernel_ms": dom_ms, "peak_source": peak_kind,
+            "algorithmic_bytes": alg, "step_algorithmic_GBs": alg / (ms * 1e-3) / 1e9,
+            "kernels": {n: {"launches": c, "mean_ms": t / c} for n, (c, t) in kt.items()}}
+
+    # e2e: host buffers through the same call, copies inside the timed region
+    node_h = torch.as_tensor(node).pin_memory()
+    k_h = torch.as_tensor(k).pin_memory() if k is not None else None
+    val_h = torch.empty(p.nnz, dtype=torch.float64).pin_memory()
+    b_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, args.steps // 2)
+    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+    for i in range(e2e_steps + 1):
+        flush.zero_()
+        if i > 0:
+            e_ev[i - 1][0].record(s)
+        node_d.copy_(node_h, non_blocking=True)
+        if k_h is not None:
+            k_d.copy_(k_h, non_blocking=True)
+        step()
+        val_h.copy_(val, non_blocking=True)
+        b_h.copy_(b, non_blocking=True)
+        if i > 0:
+            e_ev[i - 1][1].record(s)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(bb) for a, bb in e_ev) / e2e_steps
+    h2d = node_h.numel() * 8 + (k_h.numel() * 8 if k_h is not None else 0)
+    d2h = (val_h.numel() + b_h.numel()) * 8
+
+    out = {"metric": METRIC, "value": value, "unit": "Melem/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_name(args.config), "N": N, "NT": NT, "nnz": p.nnz,
+                      "variant": args.variant, "l2": "flushed by a 512 MB write between steps (outside timing)",
+                      "parallelism": "independent mesh per rank" if ws > 1 else "single GPU"},
+           "wall_s_timed_region": wall, "pattern_build_ms": pattern_ms,
+           "roofline": roof,
+           "e2e": {"value": ws * NT / (e2e_ms * 1e-3) / 1e6, "unit": "Melem/s", "ms_per_step": e2e_ms,
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+           "gpu_launches": launches,
+           "clocks": clk.summary()}
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(mesh, 1 if mesh["f"] == "sinprod" else 0, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=["c1", "c2", "c3"], default="c2")
+    ap.add_argument("--variant", choices=["deterministic", "atomic"], default="deterministic")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-sample", type=int, default=400_000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/*
+ * femasm.h - C ABI of the GB300 (sm_103a) library for P1 finite-element assembly of the Poisson
+ * problem -div(k grad u) = f, following L. Chen, "Programming of Finite Element Methods in MATLAB"
+ * (arXiv:1804.05156).
+ *
+ * Conventions (all entry points):
+ *  - Array arguments are DEVICE pointers owned by the caller unless stated otherwise; the library
+ *    never frees them. Library-owned objects are opaque handles with an explicit destroy call.
+ *  - Indices are 0-based int32 (the paper is 1-based). Element arrays are row-major [NT][d+1]
+ *    (Sec. 1.1 `elem`); coordinates are row-major double [N][d] (Sec. 1.1 `node`).
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the legacy default stream)
+ *    unless its comment says it synchronises.
+ *  - Every call returns FEM_OK (0) or a negative FEM_ERR_* code; fem_last_error_string() gives a
+ *    host-side message for the last failure in the calling process. No call aborts the process,
+ *    throws, or traps the GPU.
+ *  - Errors found by kernels (a degenerate element, an index out of range) are recorded in a
+ *    device error word; they surface at the next fem_get_error() call.
+ *  - Double arrays must be 8-byte aligned and int32 arrays 4-byte aligned (FEM_ERR_ARG otherwise).
+ */
+#ifndef FEMASM_H
+#define FEMASM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FEM_OK 0
+#define FEM_ERR_ARG -1        /* null pointer, d not in {2,3}, negative or oversized count, misaligned pointer */
+#define FEM_ERR_INDEX -2      /* an element names a vertex outside [0, N) or the same vertex twice */
+#define FEM_ERR_DEGENERATE -3 /* 2-D element of zero area, or 3-D element of non-positive volume */
+#define FEM_ERR_CUDA -4       /* a CUDA runtime call failed */
+#define FEM_ERR_OOM -5        /* device allocation failed */
+#define FEM_ERR_TIMEOUT -6    /* a bounded device-side wait gave up */
+#define FEM_ERR_STATE -7      /* handle used in a way its construction does not allow */
+
+/* Reduction variants of the value kernels (Sec. 2.2: `sparse` sums duplicate (i, j) entries). */
+#define FEM_DETERMINISTIC 0 /* fixed summation order per CSR slot: bitwise reproducible */
+#define FEM_ATOMIC 1        /* FP64 atomicAdd into the CSR values: order varies run to run */
+
+/* Right-hand side f (Sec. 3.2). */
+#define FEM_F_CONST 0    /* f = f_arg[0] (device), or 1 when f_arg is NULL */
+#define FEM_F_SINPROD 1  /* f = prod_m sin(pi x_m) over the d coordinates; f_arg unused */
+#define FEM_F_QPVALUES 2 /* f given at the quadrature points: f_arg[t * nq + q] (device, caller's
+                            element order; 2-D nq = 3, point q = midpoint of the side opposite
+                            vertex q; 3-D nq = 4, point q has barycentric weight a on vertex q) */
+
+typedef struct fem_pattern_s* fem_pattern_t;
+typedef struct fem_batch_s* fem_batch_t;
+typedef void* fem_stream_t; /* cudaStream_t */
+
+/* ---- pattern (Sec. 2.1-2.2 and the (i, j) index lists of Sec. 3.1.2-3.1.3) --------------------
+ * Builds the structural CSR pattern of the P1 stiffness matrix of the mesh `elem` [NT][d+1] over N
+ * vertices: the set of pairs (elem[t][i], elem[t][j]), rows ascending, columns ascending within a
+ * row, kept even where values later cancel. For the symmetric matrix these arrays equal the CSC
+ * arrays MATLAB keeps (Sec. 2.1). Also builds the per-element slot map
+ *   slot[(i*(d+1) + j) * NT + t] = CSR position of (elem[t][i], elem[t][j])
+ * and the vertex-to-element incidence lists used by the deterministic reduction.
+ * `elem` is read during the call only; the pattern keeps its own copy of the topology, so later
+ * value calls take no `elem` argument. Synchronises `stream` (twice: after validation, and to size
+ * col_idx). Errors: FEM_ERR_ARG (d, N, NT out of range: N < 2^31, NT*(d+1)^2 < 2^31),
+ * FEM_ERR_INDEX (bad vertex id), FEM_ERR_OOM, FEM_ERR_CUDA. NT = 0 gives an empty pattern. */
+int fem_mesh_build_pattern(int d, int64_t N, int64_t NT, const int32_t* elem, fem_pattern_t* out,
+                           fem_stream_t stream);
+
+/* Sizes and library-owned device arrays of a pattern (valid until fem_pattern_destroy):
+ * row_ptr [N+1], col_idx [nnz], slot [(d+1)^2 * NT] (layout above). Any output pointer may be NULL. */
+int fem_pattern_info(fem_pattern_t p, int* d, int64_t* N, int64_t* NT, int64_t* nnz, const int32_t** row_ptr,
+                     const int32_t** col_idx, const int32_t** slot);
+
+void fem_pattern_destroy(fem_pattern_t p);
+
+/* ---- values (Sec. 3.1.3 eq. (dlambda) and the a_ij formula below it; Sec. 3.2) -----------------
+ * One pass over the elements: barycentric gradients from the scaled normals n_i, signed measure,
+ *   a_ij^tau = k_t * n_i . n_j / (d!^2 |tau|)   (2-D |tau| = |area| as in the paper; 3-D signed)
+ * summed into val [nnz] over the pattern (the `sparse(ii, jj, sA)` summation), and the load vector
+ *   2-D: b_i += |tau| (f(m_{i+1}) + f(m_{i+2})) / 6, m_q = midpoint of the side opposite vertex q
+ *   3-D: b_i += |tau| / 4 * sum_q f(x_q) lambda_i(x_q), points (a,b,b,b) with a = (5+3 sqrt5)/20,
+ *        b = (5-sqrt5)/20 (the paper names a 4-point rule without printing it; this is its reading)
+ * summed into b [N] (the `accumarray` of Sec. 3.2).
+ * node [N][d]; k [NT] per-element coefficient in the caller's element order (NULL means k = 1);
+ * val and/or b may be NULL to skip that output; both are overwritten, not accumulated.
+ * variant: FEM_DETERMINISTIC or FEM_ATOMIC. A degenerate element sets FEM_ERR_DEGENERATE in the
+ * device error word (see fem_get_error); its contribution is then unspecified. */
+int fem_assemble(fem_pattern_t p, const double* node, const double* k, int f_kind, const double* f_arg,
+                 double* val, double* b, int variant, fem_stream_t stream);
+int fem_assemble_stiffness(fem_pattern_t p, const double* node, const double* k, double* val, int variant,
+                           fem_stream_t stream);
+int fem_assemble_rhs(fem_pattern_t p, const double* node, int f_kind, const double* f_arg, double* b,
+                     int variant, fem_stream_t stream);
+
+/* ---- boundary (Sec. 1.2, Sec. 3.3) -------------------------------------------------------------
+ * is_bd [N] (uint8, overwritten) = 1 for every vertex of a Dirichlet side. Side i of element t is
+ * the side opposite vertex i (2-D: vertices (i+1, i+2) mod 3; 3-D: faces [2 4 3], [1 3 4],
+ * [1 4 2], [1 2 3] in the paper's 1-based numbering). With bdflag [NT][d+1] (int8), Dirichlet
+ * sides are those with bdflag == 1. With bdflag == NULL every side that belongs to exactly one
+ * element is Dirichlet ("whole boundary"). */
+int fem_boundary_nodes(fem_pattern_t p, const int8_t* bdflag, uint8_t* is_bd, fem_stream_t stream);
+
+/* ---- Dirichlet (Sec. 3.3) ------------------------------------------------------------------------
+ * With u = gD on boundary vertices (0 when gD is NULL) and 0 elsewhere:
+ *   b <- b - A u, each (A u)_r summed over row r in ascending column order, s = s + val*u, no FMA;
+ *   then the eliminated square system: boundary rows of val become identity rows, boundary
+ *   columns of free rows become 0, and b[bd] = gD[bd] (0 when gD is NULL). The pattern is unchanged.
+ * free_node (nullable, int32 [N]) receives the free vertices in ascending order; when n_free (a
+ * HOST pointer, nullable) is given the call synchronises and stores their count. */
+int fem_apply_dirichlet(fem_pattern_t p, const uint8_t* is_bd, const double* gD, double* val, double* b,
+                        int32_t* free_node, int64_t* n_free, fem_stream_t stream);
+
+/* ---- backward (gradients of the assembled system) ----------------------------------------------
+ * For L = sum_s w[s] val[s] + sum_i r[i] b[i] (w [nnz], r [N]; either may be NULL = 0), writes
+ * gnode [N][d] = dL/dnode and gk [NT] = dL/dk (either may be NULL to skip). The basis gradients are
+ * recomputed from node, not stored. Derivatives follow from eq. (dlambda): d|tau|/dx_m = |tau| g_m
+ * and dg_i/dx_m = -g_m g_i^T with g_i = grad lambda_i. f_kind FEM_F_QPVALUES contributes only
+ * through |tau| and the point weights (the values are inputs). Node gradients are summed over the
+ * incident elements in ascending element order (deterministic). */
+int fem_assemble_backward(fem_pattern_t p, const double* node, const double* k, int f_kind, const double* f_arg,
+                          const double* w, const double* r, double* gnode, double* gk, fem_stream_t stream);
+
+/* ---- batched assembly of many independent meshes -----------------------------------------------
+ * B meshes of dimension d; mesh m has N[m] vertices and NT[m] elements (HOST arrays). elem_cat is
+ * the DEVICE concatenation of the meshes' elem arrays with each mesh's own 0-based vertex ids. The
+ * plan builds the block-diagonal pattern of all meshes at once (vertex ids offset by the preceding
+ * meshes' N) and tunes the launch shape of the batched value kernel on the device (synchronises).
+ * Offsets (HOST, int64, B+1 entries each, owned by the plan): node_off, elem_off, nnz_off. */
+int fem_batch_plan(int d, int B, const int64_t* N, const int64_t* NT, const int32_t* elem_cat, fem_batch_t* out,
+                   fem_stream_t stream);
+int fem_batch_info(fem_batch_t bt, int* B, const int64_t** node_off, const int64_t** elem_off,
+                   const int64_t** nnz_off, fem_pattern_t* pattern);
+/* One persistent launch over all meshes' elements (work tiles taken from a device counter), plus
+ * the per-slot reduction: node_cat [sum N][d], k_cat [sum NT] (nullable), val_cat [sum nnz],
+ * b_cat [sum N] (either output nullable). No allocation and no host synchronisation, so the call
+ * can be captured in a CUDA graph. */
+int fem_batch_assemble(fem_batch_t bt, const double* node_cat, const double* k_cat, int f_kind, const double* f_arg,
+                       double* val_cat, double* b_cat, int variant, fem_stream_t stream);
+/* Same work, replayed from a CUDA graph the plan captures on first use for these exact pointers
+ * (re-captured when any pointer or argument changes). */
+int fem_batch_assemble_graph(fem_batch_t bt, const double* node_cat, const double* k_cat, int f_kind,
+                             const double* f_arg, double* val_cat, double* b_cat, int variant, fem_stream_t stream);
+void fem_batch_destroy(fem_batch_t bt);
+
+/* ---- errors and counters -----------------------------------------------------------------------*/
+/* Synchronises `stream`, returns the first error recorded by a kernel since the last call on this
+ * device (FEM_OK if none), and clears it. */
+int fem_get_error(fem_stream_t stream);
+/* Host message for the last failed call in this process (static storage; never NULL). */
+const char* fem_last_error_string(void);
+/* Number of kernels this library has launched in this process (all devices). */
+int64_t fem_launch_count(void);
+/* Per-kernel timing, off by default. When on, every kernel launch outside stream capture is
+ * bracketed by CUDA events recorded on its own stream. fem_timing_report synchronises those events,
+ * writes one line "kernel_name launches total_ms" per kernel into buf (HOST, buflen bytes,
+ * NUL-terminated, truncated to fit) and clears the records. */
+int fem_timing_enable(int on);
+int fem_timing_report(char* buf, int64_t buflen);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEMASM_H */

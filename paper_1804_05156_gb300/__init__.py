@@ -1,0 +1,270 @@
+"""GB300-native P1 finite-element assembly (Poisson), after L. Chen, "Programming of Finite Element
+Methods in MATLAB" (arXiv:1804.05156).
+
+This module is a thin ctypes binding of the C ABI in ``include/femasm.h`` (same names, argument
+marshalling only): every step of the assembly runs in the CUDA kernels of ``libfemasm.so``.
+PyTorch provides device memory, streams and autograd plumbing. There is no CPU fallback: if the
+library has not been built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfemasm.so")
+
+FEM_OK = 0
+FEM_ERR_ARG, FEM_ERR_INDEX, FEM_ERR_DEGENERATE, FEM_ERR_CUDA, FEM_ERR_OOM, FEM_ERR_TIMEOUT, FEM_ERR_STATE = (
+    -1, -2, -3, -4, -5, -6, -7)
+FEM_DETERMINISTIC, FEM_ATOMIC = 0, 1
+FEM_F_CONST, FEM_F_SINPROD, FEM_F_QPVALUES = 0, 1, 2
+
+_lib = None
+
+
+class FemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("femasm error %d: %s" % (code, msg))
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile libfemasm.so in-tree for sm_103a (see buildlib.py)."""
+    from . import buildlib
+    return buildlib.build(force=force)
+
+
+def lib():
+    """The loaded C library (raises if it was not built: there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise FemError(FEM_ERR_STATE, "libfemasm.so is not built; run paper_1804_05156_gb300.build()")
+        L = C.CDLL(LIB_PATH)
+        P, I32, I64 = C.c_void_p, C.c_int, C.c_int64
+        sig = {
+            "fem_mesh_build_pattern": (I32, [I32, I64, I64, P, P, P]),
+            "fem_pattern_info": (I32, [P, P, P, P, P, P, P, P]),
+            "fem_pattern_destroy": (None, [P]),
+            "fem_assemble": (I32, [P, P, P, I32, P, P, P, I32, P]),
+            "fem_assemble_stiffness": (I32, [P, P, P, P, I32, P]),
+            "fem_assemble_rhs": (I32, [P, P, I32, P, P, I32, P]),
+            "fem_boundary_nodes": (I32, [P, P, P, P]),
+            "fem_apply_dirichlet": (I32, [P, P, P, P, P, P, P, P]),
+            "fem_assemble_backward": (I32, [P, P, P, I32, P, P, P, P, P, P]),
+            "fem_batch_plan": (I32, [I32, I32, P, P, P, P, P]),
+            "fem_batch_info": (I32, [P, P, P, P, P, P]),
+            "fem_batch_assemble": (I32, [P, P, P, I32, P, P, P, I32, P]),
+            "fem_batch_assemble_graph": (I32, [P, P, P, I32, P, P, P, I32, P]),
+            "fem_batch_destroy": (None, [P]),
+            "fem_get_error": (I32, [P]),
+            "fem_last_error_string": (C.c_char_p, []),
+            "fem_launch_count": (I64, []),
+            "fem_timing_enable": (I32, [I32]),
+            "fem_timing_report": (I32, [C.c_char_p, I64]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int) -> int:
+    if rc != FEM_OK:
+        raise FemError(rc, lib().fem_last_error_string().decode())
+    return rc
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise FemError(FEM_ERR_ARG, "expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise FemError(FEM_ERR_ARG, "expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def launch_count() -> int:
+    return int(lib().fem_launch_count())
+
+
+def fem_timing_enable(on: bool) -> None:
+    _check(lib().fem_timing_enable(1 if on else 0))
+
+
+def fem_timing_report() -> dict:
+    """{kernel name: (launches, total ms)} since the last report; synchronises the recorded events."""
+    buf = C.create_string_buffer(1 << 16)
+    _check(lib().fem_timing_report(buf, len(buf)))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, n, ms = line.rsplit(" ", 2)
+        out[name] = (int(n), float(ms))
+    return out
+
+
+def get_error(stream=None) -> None:
+    """Raise if a kernel recorded an error (synchronises the stream)."""
+    _check(lib().fem_get_error(_stream(stream)))
+
+
+class _DevArray:
+    """Zero-copy view of a library-owned device array (kept alive by its owner)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str, owner):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr or 0, False),
+                                         "version": 3, "strides": None}
+        self._owner = owner
+
+
+class Pattern:
+    """Structural CSR pattern + slot map of a mesh (``fem_mesh_build_pattern``)."""
+
+    def __init__(self, elem: torch.Tensor, N: int, stream=None, _handle=None):
+        self._h = C.c_void_p()
+        if _handle is not None:
+            self._h = _handle
+        else:
+            if elem.dtype != torch.int32 or elem.dim() != 2:
+                raise FemError(FEM_ERR_ARG, "elem must be an int32 [NT, d+1] CUDA tensor")
+            d = elem.shape[1] - 1
+            _check(lib().fem_mesh_build_pattern(d, int(N), int(elem.shape[0]), _ptr(elem), C.byref(self._h),
+                                                _stream(stream)))
+        d, n, nt, nnz = C.c_int(), C.c_int64(), C.c_int64(), C.c_int64()
+        rp, ci, sl = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        _check(lib().fem_pattern_info(self._h, C.byref(d), C.byref(n), C.byref(nt), C.byref(nnz), C.byref(rp),
+                                      C.byref(ci), C.byref(sl)))
+        self.d, self.N, self.NT, self.nnz = d.value, n.value, nt.value, nnz.value
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.row_ptr = torch.as_tensor(_DevArray(rp.value, self.N + 1, "<i4", self), device=dev)
+        self.col_idx = torch.as_tensor(_DevArray(ci.value, self.nnz, "<i4", self), device=dev)
+        self.slot = torch.as_tensor(_DevArray(sl.value, (self.d + 1) ** 2 * self.NT, "<i4", self), device=dev)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def destroy(self):
+        if self._h and self._h.value:
+            lib().fem_pattern_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            if getattr(self, "_owned", True):
+                self.destroy()
+        except Exception:
+            pass
+
+
+def fem_mesh_build_pattern(elem: torch.Tensor, N: int, stream=None) -> Pattern:
+    return Pattern(elem, N, stream)
+
+
+def fem_assemble(p: Pattern, node, k=None, f_kind=FEM_F_CONST, f_arg=None, val=None, b=None,
+                 variant=FEM_DETERMINISTIC, stream=None):
+    _check(lib().fem_assemble(p.handle, _ptr(node), _ptr(k), f_kind, _ptr(f_arg), _ptr(val), _ptr(b), variant,
+                              _stream(stream)))
+
+
+def fem_assemble_stiffness(p: Pattern, node, k, val, variant=FEM_DETERMINISTIC, stream=None):
+    _check(lib().fem_assemble_stiffness(p.handle, _ptr(node), _ptr(k), _ptr(val), variant, _stream(stream)))
+
+
+def fem_assemble_rhs(p: Pattern, node, f_kind, f_arg, b, variant=FEM_DETERMINISTIC, stream=None):
+    _check(lib().fem_assemble_rhs(p.handle, _ptr(node), f_kind, _ptr(f_arg), _ptr(b), variant, _stream(stream)))
+
+
+def fem_boundary_nodes(p: Pattern, bdflag, is_bd, stream=None):
+    _check(lib().fem_boundary_nodes(p.handle, _ptr(bdflag), _ptr(is_bd), _stream(stream)))
+
+
+def fem_apply_dirichlet(p: Pattern, is_bd, gD, val, b, free_node=None, want_count=True, stream=None):
+    nf = C.c_int64(-1)
+    _check(lib().fem_apply_dirichlet(p.handle, _ptr(is_bd), _ptr(gD), _ptr(val), _ptr(b), _ptr(free_node),
+                                     C.byref(nf) if want_count else None, _stream(stream)))
+    return nf.value if want_count else None
+
+
+def fem_assemble_backward(p: Pattern, node, k, f_kind, f_arg, w, r, gnode, gk, stream=None):
+    _check(lib().fem_assemble_backward(p.handle, _ptr(node), _ptr(k), f_kind, _ptr(f_arg), _ptr(w), _ptr(r),
+                                       _ptr(gnode), _ptr(gk), _stream(stream)))
+
+
+class Batch:
+    """Block-diagonal assembly of many meshes (``fem_batch_plan``)."""
+
+    def __init__(self, d: int, Ns, NTs, elem_cat: torch.Tensor, stream=None):
+        B = len(Ns)
+        self._h = C.c_void_p()
+        n_arr = (C.c_int64 * B)(*[int(x) for x in Ns])
+        t_arr = (C.c_int64 * B)(*[int(x) for x in NTs])
+        _check(lib().fem_batch_plan(d, B, n_arr, t_arr, _ptr(elem_cat), C.byref(self._h), _stream(stream)))
+        bb = C.c_int()
+        no, eo, zo = C.POINTER(C.c_int64)(), C.POINTER(C.c_int64)(), C.POINTER(C.c_int64)()
+        ph = C.c_void_p()
+        _check(lib().fem_batch_info(self._h, C.byref(bb), C.byref(no), C.byref(eo), C.byref(zo), C.byref(ph)))
+        self.B = bb.value
+        self.node_off = [no[i] for i in range(B + 1)]
+        self.elem_off = [eo[i] for i in range(B + 1)]
+        self.nnz_off = [zo[i] for i in range(B + 1)]
+        self.pattern = Pattern(None, 0, _handle=ph)
+        self.pattern._owned = False  # owned by the batch
+
+    def assemble(self, node_cat, k_cat, f_kind, f_arg, val_cat, b_cat, variant=FEM_DETERMINISTIC, graph=False,
+                 stream=None):
+        f = lib().fem_batch_assemble_graph if graph else lib().fem_batch_assemble
+        _check(f(self._h, _ptr(node_cat), _ptr(k_cat), f_kind, _ptr(f_arg), _ptr(val_cat), _ptr(b_cat), variant,
+                 _stream(stream)))
+
+    def destroy(self):
+        if self._h and self._h.value:
+            lib().fem_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def assemble(p: Pattern, node, k=None, f_kind=FEM_F_CONST, f_arg=None, variant=FEM_DETERMINISTIC):
+    """Convenience: returns (val [nnz], b [N]) as new CUDA tensors."""
+    val = torch.empty(p.nnz, dtype=torch.float64, device=node.device)
+    b = torch.empty(p.N, dtype=torch.float64, device=node.device)
+    fem_assemble(p, node, k, f_kind, f_arg, val, b, variant)
+    return val, b
+
+
+class FemAssemble(torch.autograd.Function):
+    """(node [N, d], k [NT]) -> (val [nnz], b [N]); backward recomputes the basis gradients."""
+
+    @staticmethod
+    def forward(ctx, node, k, p: Pattern, f_kind: int = FEM_F_CONST, f_arg=None):
+        node_c, k_c = node.detach().contiguous(), k.detach().contiguous()
+        val, b = assemble(p, node_c, k_c, f_kind, f_arg)
+        ctx.save_for_backward(node_c, k_c)
+        ctx.p, ctx.f_kind, ctx.f_arg = p, f_kind, f_arg
+        return val, b
+
+    @staticmethod
+    def backward(ctx, gval, gb):
+        node, k = ctx.saved_tensors
+        gnode = torch.empty_like(node) if ctx.needs_input_grad[0] else None
+        gk = torch.empty_like(k) if ctx.needs_input_grad[1] else None
+        w = None if gval is None else gval.contiguous()
+        r = None if gb is None else gb.contiguous()
+        fem_assemble_backward(ctx.p, node, k, ctx.f_kind, ctx.f_arg, w, r, gnode, gk)
+        return gnode, gk, None, None, None

@@ -1,0 +1,296 @@
+// C ABI entry points (include/femasm.h): argument checks, handle lifetime, dispatch to the kernels.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fem {
+
+std::atomic<int64_t> g_launches{0};
+std::atomic<bool> g_timing{false};
+
+namespace {
+struct TimingRec {
+  const char* name;
+  cudaEvent_t b, e;
+};
+std::mutex g_tm_mu;
+std::vector<TimingRec> g_tm_recs;
+cudaEvent_t g_tm_pending = nullptr;
+}  // namespace
+
+void timing_mark(const char* name, cudaStream_t s, bool begin) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+  std::lock_guard<std::mutex> lk(g_tm_mu);
+  cudaEvent_t ev = nullptr;
+  if (cudaEventCreate(&ev) != cudaSuccess) return;
+  cudaEventRecord(ev, s);
+  if (begin) {
+    if (g_tm_pending) cudaEventDestroy(g_tm_pending);
+    g_tm_pending = ev;
+  } else if (g_tm_pending) {
+    g_tm_recs.push_back({name, g_tm_pending, ev});
+    g_tm_pending = nullptr;
+  } else {
+    cudaEventDestroy(ev);
+  }
+}
+
+namespace {
+thread_local char g_msg[512] = "no error";
+std::mutex g_err_mu;
+int* g_err_word[64] = {nullptr};
+}  // namespace
+
+const char* g_msg_ptr() { return g_msg; }
+
+int set_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* what) {
+  cudaGetLastError();
+  return set_error(e == cudaErrorMemoryAllocation ? FEM_ERR_OOM : FEM_ERR_CUDA, "%s failed: %s", what,
+                   cudaGetErrorString(e));
+}
+
+int* device_error_word() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (!g_err_word[dev]) {
+    int* p = nullptr;
+    if (cudaMalloc((void**)&p, sizeof(int)) != cudaSuccess) return nullptr;
+    if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
+    if (cudaDeviceSynchronize() != cudaSuccess) return nullptr;
+    g_err_word[dev] = p;
+  }
+  return g_err_word[dev];
+}
+
+}  // namespace fem
+
+using fem::Pattern;
+using fem::set_error;
+
+namespace {
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+void free_pattern(Pattern& P) {
+  cudaFree(P.elem);
+  cudaFree(P.row_ptr);
+  cudaFree(P.col_idx);
+  cudaFree(P.slot);
+  cudaFree(P.inc_ptr);
+  cudaFree(P.inc);
+  cudaFree(P.scratch);
+  P = Pattern();
+}
+
+int check_values_args(fem_pattern_t p, const double* node, const double* k, int f_kind, const double* f_arg,
+                      int variant) {
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  if (p->P.NT > 0 && !node) return set_error(FEM_ERR_ARG, "null node array");
+  if (!aligned(node, 8) || !aligned(k, 8) || !aligned(f_arg, 8)) return set_error(FEM_ERR_ARG, "misaligned double array");
+  if (f_kind != FEM_F_CONST && f_kind != FEM_F_SINPROD && f_kind != FEM_F_QPVALUES)
+    return set_error(FEM_ERR_ARG, "unknown f_kind %d", f_kind);
+  if (f_kind == FEM_F_QPVALUES && !f_arg && p->P.NT > 0) return set_error(FEM_ERR_ARG, "FEM_F_QPVALUES needs f_arg");
+  if (variant != FEM_DETERMINISTIC && variant != FEM_ATOMIC) return set_error(FEM_ERR_ARG, "unknown variant %d", variant);
+  return FEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fem_mesh_build_pattern(int d, int64_t N, int64_t NT, const int32_t* elem, fem_pattern_t* out, fem_stream_t stream) {
+  if (!out) return set_error(FEM_ERR_ARG, "null output handle");
+  *out = nullptr;
+  if (d != 2 && d != 3) return set_error(FEM_ERR_ARG, "d must be 2 or 3 (got %d)", d);
+  if (N < 0 || NT < 0 || N >= ((int64_t)1 << 31)) return set_error(FEM_ERR_ARG, "bad sizes N=%lld NT=%lld", (long long)N, (long long)NT);
+  const int64_t d1 = d + 1;
+  if (NT * d1 * d1 >= ((int64_t)1 << 31)) return set_error(FEM_ERR_ARG, "NT=%lld too large for int32 slot indexing", (long long)NT);
+  if (NT > 0 && !elem) return set_error(FEM_ERR_ARG, "null elem array");
+  if (!aligned(elem, 4)) return set_error(FEM_ERR_ARG, "misaligned elem array");
+  fem_pattern_s* h = new (std::nothrow) fem_pattern_s();
+  if (!h) return set_error(FEM_ERR_OOM, "host allocation failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  Pattern& P = h->P;
+  P.d = d;
+  P.d1 = d + 1;
+  P.N = N;
+  P.NT = NT;
+  cudaGetDevice(&P.device);
+  if (!fem::device_error_word()) {
+    delete h;
+    return set_error(FEM_ERR_OOM, "cannot allocate the device error word");
+  }
+  int rc = fem::build_pattern(&P, elem, s);
+  if (rc == FEM_OK && NT > 0) {
+    P.scratch_elems = fem::scratch_per_elem(d) * NT;
+    if (cudaMallocAsync((void**)&P.scratch, sizeof(double) * (size_t)P.scratch_elems, s) != cudaSuccess) {
+      cudaGetLastError();
+      P.scratch = nullptr;
+      rc = set_error(FEM_ERR_OOM, "scratch allocation failed");
+    }
+  }
+  if (rc == FEM_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = fem::cuda_error(cudaGetLastError(), "pattern build");
+  if (rc != FEM_OK) {
+    cudaStreamSynchronize(s);
+    free_pattern(P);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return FEM_OK;
+}
+
+int fem_pattern_info(fem_pattern_t p, int* d, int64_t* N, int64_t* NT, int64_t* nnz, const int32_t** row_ptr,
+                     const int32_t** col_idx, const int32_t** slot) {
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  if (d) *d = p->P.d;
+  if (N) *N = p->P.N;
+  if (NT) *NT = p->P.NT;
+  if (nnz) *nnz = p->P.nnz;
+  if (row_ptr) *row_ptr = p->P.row_ptr;
+  if (col_idx) *col_idx = p->P.col_idx;
+  if (slot) *slot = p->P.slot;
+  return FEM_OK;
+}
+
+void fem_pattern_destroy(fem_pattern_t p) {
+  if (!p) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(p->P.device);
+  cudaDeviceSynchronize();
+  free_pattern(p->P);
+  cudaSetDevice(cur);
+  delete p;
+}
+
+int fem_assemble(fem_pattern_t p, const double* node, const double* k, int f_kind, const double* f_arg, double* val,
+                 double* b, int variant, fem_stream_t stream) {
+  int rc = check_values_args(p, node, k, f_kind, f_arg, variant);
+  if (rc) return rc;
+  if (!aligned(val, 8) || !aligned(b, 8)) return set_error(FEM_ERR_ARG, "misaligned output array");
+  if (!val && !b) return FEM_OK;
+  return fem::assemble_values(&p->P, node, k, f_kind, f_arg, val, b, variant, (cudaStream_t)stream);
+}
+
+int fem_assemble_stiffness(fem_pattern_t p, const double* node, const double* k, double* val, int variant,
+                           fem_stream_t stream) {
+  if (!val) return set_error(FEM_ERR_ARG, "null val");
+  return fem_assemble(p, node, k, FEM_F_CONST, nullptr, val, nullptr, variant, stream);
+}
+
+int fem_assemble_rhs(fem_pattern_t p, const double* node, int f_kind, const double* f_arg, double* b, int variant,
+                     fem_stream_t stream) {
+  if (!b) return set_error(FEM_ERR_ARG, "null b");
+  return fem_assemble(p, node, nullptr, f_kind, f_arg, nullptr, b, variant, stream);
+}
+
+int fem_boundary_nodes(fem_pattern_t p, const int8_t* bdflag, uint8_t* is_bd, fem_stream_t stream) {
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  if (p->P.N > 0 && !is_bd) return set_error(FEM_ERR_ARG, "null is_bd");
+  return fem::boundary_nodes(&p->P, bdflag, is_bd, (cudaStream_t)stream);
+}
+
+int fem_apply_dirichlet(fem_pattern_t p, const uint8_t* is_bd, const double* gD, double* val, double* b,
+                        int32_t* free_node, int64_t* n_free, fem_stream_t stream) {
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  if (p->P.N > 0 && (!is_bd || !val)) return set_error(FEM_ERR_ARG, "null is_bd or val");
+  if (!aligned(gD, 8) || !aligned(val, 8) || !aligned(b, 8) || !aligned(free_node, 4))
+    return set_error(FEM_ERR_ARG, "misaligned array");
+  return fem::apply_dirichlet(&p->P, is_bd, gD, val, b, free_node, n_free, (cudaStream_t)stream);
+}
+
+int fem_assemble_backward(fem_pattern_t p, const double* node, const double* k, int f_kind, const double* f_arg,
+                          const double* w, const double* r, double* gnode, double* gk, fem_stream_t stream) {
+  int rc = check_values_args(p, node, k, f_kind, f_arg, FEM_DETERMINISTIC);
+  if (rc) return rc;
+  if (!aligned(w, 8) || !aligned(r, 8) || !aligned(gnode, 8) || !aligned(gk, 8))
+    return set_error(FEM_ERR_ARG, "misaligned array");
+  if (!gnode && !gk) return FEM_OK;
+  return fem::assemble_backward(&p->P, node, k, f_kind, f_arg, w, r, gnode, gk, (cudaStream_t)stream);
+}
+
+int fem_get_error(fem_stream_t stream) {
+  int* w = fem::device_error_word();
+  if (!w) return set_error(FEM_ERR_CUDA, "no device error word");
+  cudaStream_t s = (cudaStream_t)stream;
+  int code = 0;
+  if (cudaMemcpyAsync(&code, w, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return fem::cuda_error(cudaGetLastError(), "reading the device error word");
+  if (code != 0) {
+    cudaMemsetAsync(w, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    return set_error(code, "a kernel reported error %d (%s)", code,
+                     code == FEM_ERR_DEGENERATE ? "degenerate or inverted element"
+                     : code == FEM_ERR_INDEX    ? "index out of range"
+                     : code == FEM_ERR_TIMEOUT  ? "device wait timed out"
+                                                : "see femasm.h");
+  }
+  return FEM_OK;
+}
+
+const char* fem_last_error_string(void) { return fem::g_msg_ptr(); }
+
+int64_t fem_launch_count(void) { return fem::g_launches.load(); }
+
+int fem_timing_enable(int on) {
+  fem::g_timing.store(on != 0);
+  return FEM_OK;
+}
+
+int fem_timing_report(char* buf, int64_t buflen) {
+  std::lock_guard<std::mutex> lk(fem::g_tm_mu);
+  struct Acc {
+    const char* name;
+    int64_t n;
+    double ms;
+  };
+  std::vector<Acc> acc;
+  int rc = FEM_OK;
+  for (auto& r : fem::g_tm_recs) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.e) != cudaSuccess || cudaEventElapsedTime(&ms, r.b, r.e) != cudaSuccess) {
+      cudaGetLastError();
+      rc = set_error(FEM_ERR_CUDA, "timing event failed");
+    }
+    cudaEventDestroy(r.b);
+    cudaEventDestroy(r.e);
+    size_t i = 0;
+    while (i < acc.size() && strcmp(acc[i].name, r.name) != 0) ++i;
+    if (i == acc.size()) acc.push_back({r.name, 0, 0.0});
+    acc[i].n += 1;
+    acc[i].ms += ms;
+  }
+  fem::g_tm_recs.clear();
+  if (buf && buflen > 0) {
+    int64_t off = 0;
+    buf[0] = 0;
+    for (auto& x : acc) {
+      int w = snprintf(buf + off, (size_t)(buflen - off), "%s %lld %.6f\n", x.name, (long long)x.n, x.ms);
+      if (w < 0 || off + w >= buflen) break;
+      off += w;
+    }
+  }
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// Shared internals of the femasm CUDA library (sm_103a). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "femasm.h"
+
+namespace fem {
+
+// ---- error word --------------------------------------------------------------------------------
+// One int per device, allocated on first use: the first non-zero code a kernel reports wins;
+// fem_get_error reads and clears it. Kernels receive its address as an argument.
+__device__ __forceinline__ void report(int* err, int code) { atomicCAS(err, 0, code); }
+int* device_error_word();  // for the current device; nullptr on allocation failure
+
+// ---- host-side bookkeeping -----------------------------------------------------------------------
+extern std::atomic<int64_t> g_launches;
+int set_error(int code, const char* fmt, ...);
+const char* g_msg_ptr();
+int cuda_error(cudaError_t e, const char* what);
+
+#define FEM_CUDA(call)                                        \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return ::fem::cuda_error(e_, #call); \
+  } while (0)
+
+// Per-kernel timing (off by default): CUDA events recorded on the launching stream around each
+// launch, summed per kernel name by fem_timing_report.
+extern std::atomic<bool> g_timing;
+void timing_mark(const char* name, cudaStream_t s, bool begin);
+
+// Launch helper: counts every kernel launch, optionally times it, and checks the launch error.
+#define FEM_LAUNCH(kernel, grid, block, smem, stream, ...)                        \
+  do {                                                                            \
+    if ((grid) > 0) {                                                             \
+      const bool tm_ = ::fem::g_timing.load(std::memory_order_relaxed);           \
+      if (tm_) ::fem::timing_mark(#kernel, (stream), true);                       \
+      kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                 \
+      ::fem::g_launches.fetch_add(1, std::memory_order_relaxed);                  \
+      cudaError_t e_ = cudaGetLastError();                                        \
+      if (e_ != cudaSuccess) return ::fem::cuda_error(e_, #kernel);              \
+      if (tm_) ::fem::timing_mark(#kernel, (stream), false);                      \
+    }                                                                             \
+  } while (0)
+
+inline int grid_for(int64_t n, int block, int max_blocks = 152 * 32) {
+  int64_t g = (n + block - 1) / block;
+  if (g > max_blocks) g = max_blocks;
+  return (int)g;
+}
+
+// ---- pattern object --------------------------------------------------------------------------------
+struct Pattern {
+  int d = 0, d1 = 0;
+  int64_t N = 0, NT = 0, nnz = 0;
+  int device = 0;
+  int32_t* elem = nullptr;     // [NT][d+1], copy of the caller's topology
+  int32_t* row_ptr = nullptr;  // [N+1]
+  int32_t* col_idx = nullptr;  // [nnz]
+  int32_t* slot = nullptr;     // [(d+1)^2][NT]
+  int32_t* inc_ptr = nullptr;  // [N+1] vertex -> incidence list offsets
+  int32_t* inc = nullptr;      // [NT*(d+1)] entries t*(d+1)+i, ascending within a vertex
+  double* scratch = nullptr;   // per-element values for the deterministic reduction
+  int64_t scratch_elems = 0;   // doubles in scratch
+};
+
+// scratch doubles per element: stiffness unique entries + rhs entries (+ gradient entries)
+inline int64_t scratch_per_elem(int d) { return d == 2 ? 9 : 14; }
+
+// ---- device-wide exclusive scan of int32 counts -> int32 offsets (n+1 entries), total on host ----
+int exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int64_t* total_host, cudaStream_t s);
+
+// ---- kernels entry points (host launchers) ----------------------------------------------------------
+int build_pattern(Pattern* P, const int32_t* elem_in, cudaStream_t s);
+int assemble_values(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg,
+                    double* val, double* b, int variant, cudaStream_t s);
+int boundary_nodes(const Pattern* P, const int8_t* bdflag, uint8_t* is_bd, cudaStream_t s);
+int apply_dirichlet(const Pattern* P, const uint8_t* is_bd, const double* gD, double* val, double* b,
+                    int32_t* free_node, int64_t* n_free, cudaStream_t s);
+struct BatchPlan;
+int assemble_backward(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg,
+                      const double* w, const double* r, double* gnode, double* gk, cudaStream_t s);
+
+}  // namespace fem
+
+struct fem_pattern_s {
+  fem::Pattern P;
+};

@@ -1,0 +1,329 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Pattern, slot map, boundary mask, freeNode and the Dirichlet rows: bit-exact. FP64 values:
+|gpu - oracle| <= 1e-12 * scale, scale = sum over the slot's contributions of their magnitude bound.
+"""
+import numpy as np
+import pytest
+import torch
+
+import meshgen
+import oracle
+from tests._common import TOL, assert_close_scaled, dev, gpu_slot_to_tij, host, mesh_case, sample_rows
+
+pytestmark = pytest.mark.gpu
+
+fa = pytest.importorskip("paper_1804_05156_gb300")
+
+CASES = ["c1", "sq2", "sq37p", "kuhn5", "kuhn7s", "delaunay2", "delaunay3"]
+VARIANTS = [fa.FEM_DETERMINISTIC, fa.FEM_ATOMIC]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fa.build()
+    oracle.build()
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_pattern_bit_exact(case):
+    d, node, elem, _, _ = mesh_case(case)
+    N = node.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    rp, col = oracle.pattern(d, N, elem)
+    assert p.nnz == rp[-1]
+    assert np.array_equal(host(p.row_ptr), rp)
+    assert np.array_equal(host(p.col_idx), col)
+    slot_o = oracle.slots(d, N, elem, rp, col)
+    assert np.array_equal(gpu_slot_to_tij(host(p.slot), elem.shape[0], d + 1), slot_o)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("case", CASES)
+def test_values_match_oracle(case, variant):
+    d, node, elem, k, f_kind = mesh_case(case)
+    N = node.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    val, b = fa.assemble(p, dev(node), None if k is None else dev(k), f_kind, None, variant)
+    fa.get_error()
+    rp, col, vo, so = oracle.assemble(d, node, elem, k)
+    assert_close_scaled(host(val), vo, so, what="stiffness")
+    bo = oracle.rhs(d, node, elem, f_kind)
+    # all meshes lie in the unit box, where f >= 0: every contribution to b_i has the sign of b_i
+    assert_close_scaled(host(b), bo, np.abs(bo), what="rhs")
+    if case == "c1":
+        v = host(val)
+        n = 64
+        for j in range(1, n):
+            for i in range(1, n):
+                r = j * (n + 1) + i
+                assert v[rp[r]:rp[r + 1]].tolist() == [0.0, -1.0, -1.0, 4.0, -1.0, -1.0, 0.0]
+
+
+def test_qp_values_rhs():
+    d, node, elem, k, _ = mesh_case("sq37p")
+    rng = np.random.default_rng(5)
+    fq = rng.normal(size=(elem.shape[0], 3))
+    p = fa.Pattern(dev(elem), node.shape[0])
+    b = torch.empty(node.shape[0], dtype=torch.float64, device="cuda")
+    fa.fem_assemble_rhs(p, dev(node), fa.FEM_F_QPVALUES, dev(fq.ravel()), b, fa.FEM_DETERMINISTIC)
+    bo = oracle.rhs(d, node, elem, oracle.F_QP, fq.ravel())
+    bs = oracle.rhs(d, node, elem, oracle.F_QP, np.abs(fq).ravel())
+    assert_close_scaled(host(b), bo, bs, what="rhs qp")
+    d3, node3, elem3, _, _ = mesh_case("kuhn5")
+    fq3 = rng.normal(size=(elem3.shape[0], 4))
+    p3 = fa.Pattern(dev(elem3), node3.shape[0])
+    b3 = torch.empty(node3.shape[0], dtype=torch.float64, device="cuda")
+    fa.fem_assemble_rhs(p3, dev(node3), fa.FEM_F_QPVALUES, dev(fq3.ravel()), b3, fa.FEM_ATOMIC)
+    assert_close_scaled(host(b3), oracle.rhs(3, node3, elem3, oracle.F_QP, fq3.ravel()),
+                        oracle.rhs(3, node3, elem3, oracle.F_QP, np.abs(fq3).ravel()), what="rhs qp 3d")
+
+
+def test_const_f_value_and_stiffness_only_calls():
+    d, node, elem, k, _ = mesh_case("kuhn5")
+    p = fa.Pattern(dev(elem), node.shape[0])
+    val = torch.empty(p.nnz, dtype=torch.float64, device="cuda")
+    fa.fem_assemble_stiffness(p, dev(node), dev(k), val, fa.FEM_DETERMINISTIC)
+    _, _, vo, so = oracle.assemble(d, node, elem, k)
+    assert_close_scaled(host(val), vo, so)
+    b = torch.empty(p.N, dtype=torch.float64, device="cuda")
+    fa.fem_assemble_rhs(p, dev(node), fa.FEM_F_CONST, dev(np.array([2.5])), b, fa.FEM_DETERMINISTIC)
+    bo = oracle.rhs(d, node, elem, oracle.F_CONST, np.array([2.5]))
+    assert_close_scaled(host(b), bo, np.abs(bo))
+    assert abs(float(b.sum()) - 2.5) < 1e-12
+
+
+def test_deterministic_variant_is_bitwise_reproducible():
+    m = meshgen.square_mesh(200, 0.2, 3, permute=True)
+    k = meshgen.lognormal(3, 3, m["elem"].shape[0])
+    p = fa.Pattern(dev(m["elem"]), m["node"].shape[0])
+    outs = [fa.assemble(p, dev(m["node"]), dev(k), fa.FEM_F_SINPROD, None, fa.FEM_DETERMINISTIC) for _ in range(3)]
+    for v, b in outs[1:]:
+        assert torch.equal(v, outs[0][0]) and torch.equal(b, outs[0][1])
+    va, ba = fa.assemble(p, dev(m["node"]), dev(k), fa.FEM_F_SINPROD, None, fa.FEM_ATOMIC)
+    _, _, vo, so = oracle.assemble(2, m["node"], m["elem"], k)
+    assert_close_scaled(host(va), vo, so)
+    assert_close_scaled(host(outs[0][0]), vo, so)
+
+
+@pytest.mark.parametrize("case", ["sq37p", "kuhn5", "delaunay2", "delaunay3"])
+def test_boundary_bit_exact(case):
+    d, node, elem, _, _ = mesh_case(case)
+    N = node.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    isbd = torch.empty(N, dtype=torch.uint8, device="cuda")
+    fa.fem_boundary_nodes(p, None, isbd)
+    assert np.array_equal(host(isbd), oracle.boundary(d, N, elem))
+    rng = np.random.default_rng(1)
+    flag = (rng.uniform(size=elem.shape) < 0.2).astype(np.int8) * rng.integers(0, 4, size=elem.shape).astype(np.int8)
+    fa.fem_boundary_nodes(p, dev(flag), isbd)
+    assert np.array_equal(host(isbd), oracle.boundary(d, N, elem, flag))
+
+
+@pytest.mark.parametrize("with_gd", [False, True])
+@pytest.mark.parametrize("case", ["sq37p", "kuhn5", "delaunay2"])
+def test_dirichlet_bit_exact(case, with_gd):
+    d, node, elem, k, f_kind = mesh_case(case)
+    N = node.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    val, b = fa.assemble(p, dev(node), dev(k), f_kind, None, fa.FEM_DETERMINISTIC)
+    isbd = torch.empty(N, dtype=torch.uint8, device="cuda")
+    fa.fem_boundary_nodes(p, None, isbd)
+    gD = np.cos(3 * node[:, 0]) + node[:, 1] if with_gd else None
+    v0, b0 = host(val).copy(), host(b).copy()
+    free = torch.full((N,), -1, dtype=torch.int32, device="cuda")
+    nf = fa.fem_apply_dirichlet(p, isbd, None if gD is None else dev(gD), val, b, free)
+    vo, bo, fo = oracle.dirichlet(host(p.row_ptr).astype(np.int64), host(p.col_idx).astype(np.int64), v0, b0,
+                                  host(isbd), gD)
+    assert nf == fo.size
+    assert np.array_equal(host(free)[:nf], fo)
+    assert np.array_equal(host(val), vo)  # bit-exact
+    assert np.array_equal(host(b), bo)
+
+
+@pytest.mark.parametrize("f_kind", [fa.FEM_F_CONST, fa.FEM_F_SINPROD, fa.FEM_F_QPVALUES])
+@pytest.mark.parametrize("case", ["sq37p", "kuhn5", "delaunay3"])
+def test_backward_matches_oracle_adjoint(case, f_kind):
+    d, node, elem, k, _ = mesh_case(case)
+    N, NT = node.shape[0], elem.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    rp, col = host(p.row_ptr).astype(np.int64), host(p.col_idx).astype(np.int64)
+    slot = oracle.slots(d, N, elem, rp, col)
+    w = meshgen.normal(1808, meshgen.TAG_W, p.nnz)
+    r = meshgen.normal(1808, meshgen.TAG_R, N)
+    farg = meshgen.normal(7, 9, NT * (d + 1)) if f_kind == fa.FEM_F_QPVALUES else None
+    gn = torch.empty((N, d), dtype=torch.float64, device="cuda")
+    gk = torch.empty(NT, dtype=torch.float64, device="cuda")
+    fa.fem_assemble_backward(p, dev(node), dev(k), f_kind, None if farg is None else dev(farg), dev(w), dev(r), gn, gk)
+    fa.get_error()
+    gno, gko = oracle.backward(d, node, elem, k, f_kind, farg, slot, w, r)
+    # magnitude scale: the same adjoint with |w|, |r| bounds no cancellation; use max-based scale per array
+    sn = 1e-10 * (np.abs(gno) + np.abs(gno).max())
+    sk = 1e-10 * (np.abs(gko) + np.abs(gko).max())
+    assert np.all(np.abs(host(gn) - gno) <= sn)
+    assert np.all(np.abs(host(gk) - gko) <= sk)
+
+
+def test_backward_central_fd_on_gpu():
+    """Gradients of L = w.A + r.b from the GPU backward vs central differences of the GPU forward."""
+    m = meshgen.kuhn_mesh(3, 0.1, 21)
+    node, elem = m["node"], m["elem"]
+    N, NT = node.shape[0], elem.shape[0]
+    k = meshgen.lognormal(21, 3, NT)
+    p = fa.Pattern(dev(elem), N)
+    w = dev(meshgen.normal(22, 4, p.nnz))
+    r = dev(meshgen.normal(22, 5, N))
+
+    def L(x, kk):
+        v, b = fa.assemble(p, dev(x), dev(kk), fa.FEM_F_SINPROD, None, fa.FEM_DETERMINISTIC)
+        return float((w * v).sum() + (r * b).sum())
+
+    gn = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+    gk = torch.empty(NT, dtype=torch.float64, device="cuda")
+    fa.fem_assemble_backward(p, dev(node), dev(k), fa.FEM_F_SINPROD, None, w, r, gn, gk)
+    gn, gk = host(gn), host(gk)
+    rng = np.random.default_rng(0)
+    eps = 1e-6
+    for v in rng.choice(N, 40, replace=False):
+        for c in range(3):
+            xp, xm = node.copy(), node.copy()
+            xp[v, c] += eps
+            xm[v, c] -= eps
+            fd = (L(xp, k) - L(xm, k)) / (2 * eps)
+            assert abs(fd - gn[v, c]) <= 1e-6 * max(1.0, abs(gn[v, c]))
+    for t in rng.choice(NT, 40, replace=False):
+        kp, km = k.copy(), k.copy()
+        kp[t] += eps
+        km[t] -= eps
+        fd = (L(node, kp) - L(node, km)) / (2 * eps)
+        assert abs(fd - gk[t]) <= 1e-6 * max(1.0, abs(gk[t]))
+
+
+def test_autograd_function():
+    d, node, elem, k, _ = mesh_case("kuhn5")
+    p = fa.Pattern(dev(elem), node.shape[0])
+    x = dev(node).requires_grad_(True)
+    kk = dev(k).requires_grad_(True)
+    val, b = fa.FemAssemble.apply(x, kk, p, fa.FEM_F_SINPROD, None)
+    w = torch.randn_like(val)
+    r = torch.randn_like(b)
+    loss = (w * val).sum() + (r * b).sum()
+    gx, gk = torch.autograd.grad(loss, [x, kk])
+    gn2 = torch.empty_like(gx)
+    gk2 = torch.empty_like(gk)
+    fa.fem_assemble_backward(p, dev(node), dev(k), fa.FEM_F_SINPROD, None, w, r, gn2, gk2)
+    assert torch.equal(gx, gn2) and torch.equal(gk, gk2)
+
+
+def test_batched_matches_per_mesh_oracle():
+    sides = [3, 5, 8, 2, 13, 1]
+    meshes = [meshgen.square_mesh(s, 0.2, 100 + i) for i, s in enumerate(sides)]
+    ks = [meshgen.lognormal(100 + i, 3, m["elem"].shape[0]) for i, m in enumerate(meshes)]
+    elem_cat = np.concatenate([m["elem"] for m in meshes])
+    node_cat = np.concatenate([m["node"] for m in meshes])
+    k_cat = np.concatenate(ks)
+    bt = fa.Batch(2, [m["node"].shape[0] for m in meshes], [m["elem"].shape[0] for m in meshes], dev(elem_cat))
+    val = torch.empty(bt.nnz_off[-1], dtype=torch.float64, device="cuda")
+    b = torch.empty(bt.node_off[-1], dtype=torch.float64, device="cuda")
+    bt.assemble(dev(node_cat), dev(k_cat), fa.FEM_F_SINPROD, None, val, b, fa.FEM_DETERMINISTIC)
+    fa.get_error()
+    v, bb = host(val), host(b)
+    for i, m in enumerate(meshes):
+        rp, col, vo, so = oracle.assemble(2, m["node"], m["elem"], ks[i])
+        assert np.array_equal(host(bt.pattern.col_idx)[bt.nnz_off[i]:bt.nnz_off[i + 1]] - bt.node_off[i], col)
+        assert_close_scaled(v[bt.nnz_off[i]:bt.nnz_off[i + 1]], vo, so)
+        bo = oracle.rhs(2, m["node"], m["elem"], oracle.F_SINPROD)
+        assert_close_scaled(bb[bt.node_off[i]:bt.node_off[i + 1]], bo, np.abs(bo) + 1e-30)
+    # graph replay gives the same bits
+    val2, b2 = torch.empty_like(val), torch.empty_like(b)
+    n0 = fa.launch_count()
+    for _ in range(2):
+        bt.assemble(dev(node_cat), dev(k_cat), fa.FEM_F_SINPROD, None, val2, b2, fa.FEM_DETERMINISTIC, graph=True)
+    torch.cuda.synchronize()
+    assert fa.launch_count() > n0
+    assert torch.equal(val, val2) and torch.equal(b, b2)
+
+
+def test_edge_cases():
+    # empty mesh
+    p = fa.Pattern(torch.zeros((0, 3), dtype=torch.int32, device="cuda"), 5)
+    assert p.nnz == 0 and host(p.row_ptr).tolist() == [0] * 6
+    val, b = fa.assemble(p, dev(np.zeros((5, 2))))
+    assert b.abs().sum().item() == 0.0
+    # one element
+    node = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    p1 = fa.Pattern(dev(np.array([[0, 1, 2]], np.int32)), 3)
+    v1, b1 = fa.assemble(p1, dev(node))
+    assert host(v1).tolist() == [1.0, -0.5, -0.5, -0.5, 0.5, 0.0, -0.5, 0.0, 0.5]
+    assert host(b1).tolist() == [0.5 / 3] * 3
+    # bad vertex id and repeated vertex are rejected at pattern build
+    with pytest.raises(fa.FemError) as e:
+        fa.Pattern(dev(np.array([[0, 1, 7]], np.int32)), 3)
+    assert e.value.code == fa.FEM_ERR_INDEX
+    with pytest.raises(fa.FemError) as e:
+        fa.Pattern(dev(np.array([[0, 1, 1]], np.int32)), 3)
+    assert e.value.code == fa.FEM_ERR_INDEX
+    with pytest.raises(fa.FemError) as e:
+        fa.Pattern(dev(np.array([[0, 1, -1]], np.int32)), 3)
+    assert e.value.code == fa.FEM_ERR_INDEX
+    # degenerate element is reported through the device error word, and the word is then cleared
+    flat = np.array([[0.0, 0.0], [1.0, 0.0], [2.0, 0.0]])
+    for variant in VARIANTS:
+        fa.assemble(p1, dev(flat), variant=variant)
+        with pytest.raises(fa.FemError) as e:
+            fa.get_error()
+        assert e.value.code == fa.FEM_ERR_DEGENERATE
+        fa.get_error()
+    # inverted tetrahedron (signed volume < 0) is degenerate in 3-D
+    m = meshgen.kuhn_mesh(1)
+    e3 = m["elem"].copy()
+    e3[0] = e3[0][[1, 0, 2, 3]]
+    p3 = fa.Pattern(dev(e3), m["node"].shape[0])
+    fa.assemble(p3, dev(m["node"]))
+    with pytest.raises(fa.FemError):
+        fa.get_error()
+
+
+# ---- full-size workloads, in the launch configuration the benchmark times -------------------------
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("cfg", ["c2", "c3"])
+def test_full_size_sampled_rows(cfg, variant):
+    m = meshgen.make_config(cfg)
+    d = m["d"]
+    node, elem, k = m["node"], m["elem"], m["coef"]
+    N, NT = node.shape[0], elem.shape[0]
+    f_kind = oracle.F_SINPROD if m["f"] == "sinprod" else oracle.F_CONST
+    p = fa.Pattern(dev(elem), N)
+    n = m["n"]
+    exp_nnz = N + 2 * (3 * n * n + 2 * n) if d == 2 else N + 2 * (3 * n * (n + 1) ** 2 + 3 * n * n * (n + 1) + n ** 3)
+    assert p.nnz == exp_nnz
+    val, b = fa.assemble(p, dev(node), dev(k), f_kind, None, variant)
+    fa.get_error()
+    rows = sample_rows(N, 600, 11)
+    rp_o, col_o, v_o, s_o = oracle.assemble(d, node, elem, k, rows=rows)
+    rp, col, v = host(p.row_ptr), host(p.col_idx), host(val)
+    for r in rows:
+        seg = slice(rp[r], rp[r + 1])
+        oseg = slice(rp_o[r], rp_o[r + 1])
+        assert np.array_equal(col[seg], col_o[oseg])
+        assert_close_scaled(v[seg], v_o[oseg], s_o[oseg])
+    b_o = oracle.rhs(d, node, elem, f_kind, rows=rows)
+    bh = host(b)
+    assert_close_scaled(bh[rows], b_o[rows], np.abs(b_o[rows]) + 1e-30, what="rhs rows")
+    # zero row sums everywhere (constants are in the kernel), relative to the row's magnitude
+    rowid = torch.repeat_interleave(torch.arange(N, device="cuda"), (p.row_ptr[1:] - p.row_ptr[:-1]).long())
+    rs = torch.zeros(N, dtype=torch.float64, device="cuda").index_add_(0, rowid, val)
+    ra = torch.zeros(N, dtype=torch.float64, device="cuda").index_add_(0, rowid, val.abs())
+    assert bool((rs.abs() <= 1e-12 * ra).all())
+    # symmetry through the slot map, sampled elements
+    ts = torch.as_tensor(np.random.default_rng(3).choice(NT, 20000, replace=False), device="cuda")
+    sl = host(p.slot.view((d + 1) ** 2, NT)[:, ts]).T.reshape(-1, d + 1, d + 1)
+    a = v[sl]
+    assert np.all(np.abs(a - np.transpose(a, (0, 2, 1))) <= 1e-13 * np.abs(a).max(axis=(1, 2), keepdims=True))
+    # whole-boundary mask equals the generator's geometric one
+    isbd = torch.empty(N, dtype=torch.uint8, device="cuda")
+    fa.fem_boundary_nodes(p, None, isbd)
+    assert np.array_equal(host(isbd), m["is_bd"])
