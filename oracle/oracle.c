@@ -108,17 +108,39 @@ static double local_entry(int d, double n[4][3], double meas, double k, int i, i
   return k * (dot(n[i], n[j], d) / (dd * meas));
 }
 
-/* Magnitude bound of that entry's rounding: k * sum_m |n_im n_jm| / (d!^2 |tau|); for the diagonal,
- * k * sum_{j != i} sum_m |n_im n_jm| / (d!^2 |tau|), which also bounds the diagonal formed as minus
- * the off-diagonal row sum (sum_j n_j = 0). This is the scale the parity tolerance is relative to. */
-static double local_scale(int d, double n[4][3], double meas, double k, int i, int j) {
+/* Magnitude bound of the rounding of that entry: k * sum_m |n|_im |n|_jm / (d!^2 |tau|), where |n|_im
+ * is the magnitude of the terms that form n_im (2-D: |n_im| itself, an edge component; 3-D: the two
+ * products of the cross product, |u_a v_b| + |u_b v_a|). For the diagonal the sum runs over
+ * j != i, which also bounds the diagonal formed as minus the off-diagonal row sum (sum_j n_j = 0).
+ * This is the scale the parity tolerance is relative to. */
+static void normal_magnitudes(int d, const double* node, const int32_t* e, double nm[4][3]) {
+  if (d == 2) {
+    double n[4][3];
+    element_normals(d, node, e, n);
+    for (int i = 0; i < 3; ++i)
+      for (int m = 0; m < 2; ++m) nm[i][m] = fabs(n[i][m]);
+    return;
+  }
+  const double* x[4];
+  for (int i = 0; i < 4; ++i) x[i] = node + 3 * (int64_t)e[i];
+  for (int i = 0; i < 4; ++i) {
+    double u[3], v[3];
+    sub3(x[FACE3[i][1]], x[FACE3[i][0]], u);
+    sub3(x[FACE3[i][2]], x[FACE3[i][0]], v);
+    nm[i][0] = fabs(u[1] * v[2]) + fabs(u[2] * v[1]);
+    nm[i][1] = fabs(u[2] * v[0]) + fabs(u[0] * v[2]);
+    nm[i][2] = fabs(u[0] * v[1]) + fabs(u[1] * v[0]);
+  }
+}
+
+static double local_scale(int d, double nm[4][3], double meas, double k, int i, int j) {
   double dd = (d == 2) ? 4.0 : 36.0, s = 0.0;
   if (i != j) {
-    for (int m = 0; m < d; ++m) s = s + fabs(n[i][m] * n[j][m]);
+    for (int m = 0; m < d; ++m) s = s + nm[i][m] * nm[j][m];
   } else {
     for (int q = 0; q <= d; ++q)
       if (q != i)
-        for (int m = 0; m < d; ++m) s = s + fabs(n[i][m] * n[q][m]);
+        for (int m = 0; m < d; ++m) s = s + nm[i][m] * nm[q][m];
   }
   return fabs(k) * (s / (dd * fabs(meas)));
 }
@@ -214,13 +236,15 @@ int64_t ora_triples(int d, int64_t N, int64_t NT, const double* node, const int3
     double meas = element_normals(d, node, e, n);
     if (!(meas > 0.0)) return ORA_ERR_DEGENERATE;
     double kt = k ? k[t] : 1.0;
+    double nm[4][3];
+    if (Sscale) normal_magnitudes(d, node, e, nm);
     for (int i = 0; i <= d; ++i) {
       if (row_mask && !row_mask[e[i]]) continue;
       for (int j = 0; j <= d; ++j) {
         I[q] = e[i];
         J[q] = e[j];
         S[q] = local_entry(d, n, meas, kt, i, j);
-        if (Sscale) Sscale[q] = local_scale(d, n, meas, kt, i, j);
+        if (Sscale) Sscale[q] = local_scale(d, nm, meas, kt, i, j);
         q += 1;
       }
     }
