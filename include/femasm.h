@@ -140,6 +140,29 @@ int fem_batch_assemble_graph(fem_batch_t bt, const double* node_cat, const doubl
                              const double* f_arg, double* val_cat, double* b_cat, int variant, fem_stream_t stream);
 void fem_batch_destroy(fem_batch_t bt);
 
+/* ---- allocation-free assembly --------------------------------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that cannot allocate device
+ * memory while they assemble. One example is an application that hands all device memory to its own
+ * pool at start-up. Another is a loop with a fixed latency budget, where the implicit device
+ * synchronisation of an allocation is unacceptable.
+ * Same result and arguments as fem_assemble with FEM_DETERMINISTIC (bitwise the same values). It
+ * calls no cudaMalloc, cudaFree or other allocating routine. Its per-element scratch lives in a
+ * fixed device array of FEM_NOALLOC_SCRATCH_DOUBLES doubles (16 MiB), compiled into the library.
+ * Every GPU that loads the library holds that array until the process exits.
+ *  - Size limit: d = 2 meshes up to FEM_NOALLOC_SCRATCH_DOUBLES / 9 = 233,016 elements, d = 3 up to
+ *    FEM_NOALLOC_SCRATCH_DOUBLES / 14 = 149,796 elements. Larger meshes return FEM_ERR_ARG and
+ *    launch nothing.
+ *  - Set-up: the first call on a device (with that device current) looks up the array's device
+ *    address with cudaGetSymbolAddress and caches it. Make that first call before any stream capture.
+ *  - The pattern p must have been built on the current device (FEM_ERR_STATE otherwise).
+ *  - Sharing: all calls on a device share the one array, which keeps the last call's contents.
+ *    Every call overwrites the scratch it reads, and val/b are cleared before they are
+ *    accumulated. Calls that overlap on the GPU (for example on two streams at once) race on the
+ *    array and produce wrong results: serialise them. */
+#define FEM_NOALLOC_SCRATCH_DOUBLES ((int64_t)1 << 21)
+int fem_assemble_noalloc(fem_pattern_t p, const double* node, const double* k, int f_kind, const double* f_arg,
+                         double* val, double* b, fem_stream_t stream);
+
 /* ---- errors and counters -----------------------------------------------------------------------*/
 /* Synchronises `stream`, returns the first error recorded by a kernel since the last call on this
  * device (FEM_OK if none), and clears it. */

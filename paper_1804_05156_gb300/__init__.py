@@ -63,6 +63,7 @@ def lib():
             "fem_get_error": (I32, [P]),
             "fem_last_error_string": (C.c_char_p, []),
             "fem_launch_count": (I64, []),
+            "fem_assemble_noalloc": (I32, [P, P, P, I32, P, P, P, P]),
             "fem_timing_enable": (I32, [I32]),
             "fem_timing_report": (I32, [C.c_char_p, I64]),
         }
@@ -176,6 +177,12 @@ def fem_assemble(p: Pattern, node, k=None, f_kind=FEM_F_CONST, f_arg=None, val=N
                  variant=FEM_DETERMINISTIC, stream=None):
     _check(lib().fem_assemble(p.handle, _ptr(node), _ptr(k), f_kind, _ptr(f_arg), _ptr(val), _ptr(b), variant,
                               _stream(stream)))
+
+
+def fem_assemble_noalloc(p: Pattern, node, k=None, f_kind=FEM_F_CONST, f_arg=None, val=None, b=None, stream=None):
+    """Deterministic assembly that allocates nothing (scratch in a fixed device array; see femasm.h)."""
+    _check(lib().fem_assemble_noalloc(p.handle, _ptr(node), _ptr(k), f_kind, _ptr(f_arg), _ptr(val), _ptr(b),
+                                      _stream(stream)))
 
 
 def fem_assemble_stiffness(p: Pattern, node, k, val, variant=FEM_DETERMINISTIC, stream=None):

@@ -80,6 +80,13 @@ int* device_error_word() {
   return g_err_word[dev];
 }
 
+int* device_error_word_if_ready() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  return g_err_word[dev];
+}
+
 }  // namespace fem
 
 using fem::Pattern;

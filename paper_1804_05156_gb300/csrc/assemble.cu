@@ -127,4 +127,23 @@ int assemble_values(const Pattern* P, const double* node, const double* k, int f
   return FEM_OK;
 }
 
+int assemble_values_two_pass(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg,
+                              double* val, double* b, double* scratch, int* err, cudaStream_t s) {
+  const int64_t NT = P->NT, N = P->N;
+  if (val && P->nnz > 0) FEM_CUDA(cudaMemsetAsync(val, 0, sizeof(double) * P->nnz, s));
+  if (b && N > 0) FEM_CUDA(cudaMemsetAsync(b, 0, sizeof(double) * N, s));
+  if (NT == 0) return FEM_OK;
+  const int grid = grid_for(NT, 256, 152 * 16);
+  if (P->d == 2) {
+    FEM_LAUNCH_UNTIMED(k_element_values<2>, grid, 256, 0, s, P->elem, NT, node, k, f_kind, f_arg, val != nullptr, b != nullptr,
+               scratch, err);
+    FEM_LAUNCH_UNTIMED(k_row_reduce<2>, grid_for(N, 256), 256, 0, s, P->inc_ptr, P->inc, P->slot, N, NT, scratch, val, b);
+  } else {
+    FEM_LAUNCH_UNTIMED(k_element_values<3>, grid, 256, 0, s, P->elem, NT, node, k, f_kind, f_arg, val != nullptr, b != nullptr,
+               scratch, err);
+    FEM_LAUNCH_UNTIMED(k_row_reduce<3>, grid_for(N, 256), 256, 0, s, P->inc_ptr, P->inc, P->slot, N, NT, scratch, val, b);
+  }
+  return FEM_OK;
+}
+
 }  // namespace fem

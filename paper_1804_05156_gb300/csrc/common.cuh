@@ -47,6 +47,17 @@ void timing_mark(const char* name, cudaStream_t s, bool begin);
     }                                                                             \
   } while (0)
 
+// Same, without the optional timing events (for paths that must not create any CUDA objects).
+#define FEM_LAUNCH_UNTIMED(kernel, grid, block, smem, stream, ...)                \
+  do {                                                                            \
+    if ((grid) > 0) {                                                             \
+      kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                 \
+      ::fem::g_launches.fetch_add(1, std::memory_order_relaxed);                  \
+      cudaError_t e_ = cudaGetLastError();                                        \
+      if (e_ != cudaSuccess) return ::fem::cuda_error(e_, #kernel);              \
+    }                                                                             \
+  } while (0)
+
 inline int grid_for(int64_t n, int block, int max_blocks = 152 * 32) {
   int64_t g = (n + block - 1) / block;
   if (g > max_blocks) g = max_blocks;
@@ -78,6 +89,11 @@ int exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int64_t* total_ho
 int build_pattern(Pattern* P, const int32_t* elem_in, cudaStream_t s);
 int assemble_values(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg,
                     double* val, double* b, int variant, cudaStream_t s);
+// Deterministic two-pass value path with caller-provided per-element scratch (scratch_per_elem(d) * NT
+// doubles) and error word; allocates nothing.
+int assemble_values_two_pass(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg,
+                              double* val, double* b, double* scratch, int* err, cudaStream_t s);
+int* device_error_word_if_ready();  // the current device's error word, or nullptr if never allocated
 int boundary_nodes(const Pattern* P, const int8_t* bdflag, uint8_t* is_bd, cudaStream_t s);
 int apply_dirichlet(const Pattern* P, const uint8_t* is_bd, const double* gD, double* val, double* b,
                     int32_t* free_node, int64_t* n_free, cudaStream_t s);
