@@ -184,11 +184,14 @@ def run_ours(args):
     elem_d = torch.as_tensor(elem).cuda()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    node_d = torch.as_tensor(node).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     p = fa.Pattern(elem_d, N)
+    fa.fem_pattern_set_locality(p, node_d)
     torch.cuda.synchronize()
     pattern_ms = 1e3 * (time.perf_counter() - t0)
 
-    node_d = torch.as_tensor(node).cuda()
     k_d = torch.as_tensor(k).cuda() if k is not None else None
     val = torch.empty(p.nnz, dtype=torch.float64, device="cuda")
     b = torch.empty(N, dtype=torch.float64, device="cuda")

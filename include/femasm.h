@@ -64,6 +64,16 @@ typedef void* fem_stream_t; /* cudaStream_t */
 int fem_mesh_build_pattern(int d, int64_t N, int64_t NT, const int32_t* elem, fem_pattern_t* out,
                            fem_stream_t stream);
 
+/* Locality plan of the deterministic value kernel. The pattern build makes one from the vertex
+ * numbering. Vertices are cut into blocks of consecutive ids, and one CTA owns each block's rows;
+ * elements on block boundaries are computed once per block they touch. This call rebuilds the plan
+ * from a geometric order instead: a Morton code of the coordinates `node` [N][d] (device), grouped
+ * first by group [N] (device int32, nullable; for example the mesh id in a batch). Compact blocks
+ * mean fewer boundary elements. The coordinates only choose the order: any values give the same
+ * results, and later calls may pass different coordinates. Synchronises `stream`. Meshes whose rows
+ * exceed 32 entries keep the two-pass deterministic path. */
+int fem_pattern_set_locality(fem_pattern_t p, const double* node, const int32_t* group, fem_stream_t stream);
+
 /* Sizes and library-owned device arrays of a pattern (valid until fem_pattern_destroy):
  * row_ptr [N+1], col_idx [nnz], slot [(d+1)^2 * NT] (layout above). Any output pointer may be NULL. */
 int fem_pattern_info(fem_pattern_t p, int* d, int64_t* N, int64_t* NT, int64_t* nnz, const int32_t** row_ptr,

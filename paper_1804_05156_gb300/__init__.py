@@ -48,6 +48,7 @@ def lib():
         sig = {
             "fem_mesh_build_pattern": (I32, [I32, I64, I64, P, P, P]),
             "fem_pattern_info": (I32, [P, P, P, P, P, P, P, P]),
+            "fem_pattern_set_locality": (I32, [P, P, P, P]),
             "fem_pattern_destroy": (None, [P]),
             "fem_assemble": (I32, [P, P, P, I32, P, P, P, I32, P]),
             "fem_assemble_stiffness": (I32, [P, P, P, P, I32, P]),
@@ -167,6 +168,10 @@ class Pattern:
                 self.destroy()
         except Exception:
             pass
+
+
+def fem_pattern_set_locality(p: Pattern, node, group=None, stream=None):
+    _check(lib().fem_pattern_set_locality(p.handle, _ptr(node), _ptr(group), _stream(stream)))
 
 
 def fem_mesh_build_pattern(elem: torch.Tensor, N: int, stream=None) -> Pattern:

@@ -97,6 +97,7 @@ namespace {
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 void free_pattern(Pattern& P) {
+  fem::free_block_plan(P.blk);
   cudaFree(P.elem);
   cudaFree(P.row_ptr);
   cudaFree(P.col_idx);
@@ -155,6 +156,7 @@ int fem_mesh_build_pattern(int d, int64_t N, int64_t NT, const int32_t* elem, fe
     }
   }
   if (rc == FEM_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = fem::cuda_error(cudaGetLastError(), "pattern build");
+  if (rc == FEM_OK) rc = fem::rebuild_block_plan(&P, nullptr, nullptr, s);
   if (rc != FEM_OK) {
     cudaStreamSynchronize(s);
     free_pattern(P);
@@ -163,6 +165,12 @@ int fem_mesh_build_pattern(int d, int64_t N, int64_t NT, const int32_t* elem, fe
   }
   *out = h;
   return FEM_OK;
+}
+
+int fem_pattern_set_locality(fem_pattern_t p, const double* node, const int32_t* group, fem_stream_t stream) {
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  if (!aligned(node, 8) || !aligned(group, 4)) return set_error(FEM_ERR_ARG, "misaligned array");
+  return fem::rebuild_block_plan(&p->P, node, group, (cudaStream_t)stream);
 }
 
 int fem_pattern_info(fem_pattern_t p, int* d, int64_t* N, int64_t* NT, int64_t* nnz, const int32_t** row_ptr,
@@ -195,6 +203,8 @@ int fem_assemble(fem_pattern_t p, const double* node, const double* k, int f_kin
   if (rc) return rc;
   if (!aligned(val, 8) || !aligned(b, 8)) return set_error(FEM_ERR_ARG, "misaligned output array");
   if (!val && !b) return FEM_OK;
+  if (variant == FEM_DETERMINISTIC && p->P.blk.ok)
+    return fem::assemble_blocked(&p->P, node, k, f_kind, f_arg, val, b, (cudaStream_t)stream);
   return fem::assemble_values(&p->P, node, k, f_kind, f_arg, val, b, variant, (cudaStream_t)stream);
 }
 

@@ -1,0 +1,371 @@
+// Locality plan for the owner-computes value kernel.
+//
+// The vertices (rows) are ordered by a locality key (a Morton code of the coordinates when the caller
+// gives them, else the vertex id) and cut into blocks of V consecutive vertices. One CTA owns one
+// block: it computes every element that touches one of its rows (elements on a block boundary are
+// computed by each block they touch) and sums the rows' entries on chip in a fixed order, so every
+// CSR entry is written once, by its owner, with no atomics.
+//
+// Per block the plan stores: its element list (ascending caller element id), the vertices those
+// elements use (ascending id; local vertex ids are positions in it), each element's local vertex ids,
+// and for every owned row its incidences in ascending element order, packed as
+//   e (15 bits, position in the block's element list) | i << 15 (2 bits, local vertex of the row)
+//   | in-row position of column elem[t][j] for the d vertices j != i, ascending j, 5 bits each.
+// Limits of the packed form: <= 32768 elements per block and <= 32 entries per row; a mesh outside
+// them keeps the two-pass path.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace fem {
+
+int radix_sort_u64(uint64_t* keys, uint64_t* tmp, int64_t n, cudaStream_t s, uint64_t** result);
+int unique_u64(const uint64_t* keys, int64_t n, uint64_t* out, int64_t* n_out, cudaStream_t s);
+int segment_starts(const uint64_t* keys, int64_t n, int64_t nseg, int32_t* seg_off, cudaStream_t s);
+
+namespace {
+
+__device__ __forceinline__ unsigned long long ordered_bits(double x) {
+  unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double from_ordered(unsigned long long u) {
+  return __longlong_as_double((long long)((u >> 63) ? (u & 0x7fffffffffffffffull) : ~u));
+}
+
+__global__ void k_bbox(const double* __restrict__ node, int64_t N, int d, unsigned long long* __restrict__ lo,
+                       unsigned long long* __restrict__ hi) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x)
+    for (int m = 0; m < d; ++m) {
+      const unsigned long long u = ordered_bits(node[v * d + m]);
+      atomicMin(lo + m, u);
+      atomicMax(hi + m, u);
+    }
+}
+
+__device__ __forceinline__ uint32_t spread2(uint32_t x) {  // 12 bits -> every other bit
+  x &= 0xfff;
+  x = (x | (x << 8)) & 0x00ff00ffu;
+  x = (x | (x << 4)) & 0x0f0f0f0fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}
+__device__ __forceinline__ uint32_t spread3(uint32_t x) {  // 8 bits -> every third bit
+  x &= 0xff;
+  x = (x | (x << 16)) & 0x030000ffu;
+  x = (x | (x << 8)) & 0x0300f00fu;
+  x = (x | (x << 4)) & 0x030c30c3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
+}
+
+// key = group (8 bits) << 56 | morton (24 bits) << 32 | vertex id
+__global__ void k_vertex_keys(const double* __restrict__ node, const int32_t* __restrict__ group, int64_t N, int d,
+                              const unsigned long long* __restrict__ lo, const unsigned long long* __restrict__ hi,
+                              uint64_t* __restrict__ keys) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t code = 0;
+    if (node) {
+      const int bits = (d == 2) ? 12 : 8;
+      const double cells = (double)(1 << bits);
+      uint32_t q[3] = {0, 0, 0};
+      for (int m = 0; m < d; ++m) {
+        const double a = from_ordered(lo[m]), b = from_ordered(hi[m]);
+        double u = (b > a) ? (node[v * d + m] - a) / (b - a) : 0.0;
+        u = fmin(fmax(u * cells, 0.0), cells - 1.0);
+        q[m] = (uint32_t)u;
+      }
+      code = (d == 2) ? (spread2(q[0]) | (spread2(q[1]) << 1))
+                      : (spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2));
+    }
+    const uint64_t g = group ? (uint64_t)(group[v] & 255) : 0;
+    keys[v] = (g << 56) | ((uint64_t)(code & 0xffffff) << 32) | (uint64_t)v;
+  }
+}
+
+__global__ void k_order_from_keys(const uint64_t* __restrict__ keys, int64_t N, int V, int32_t* __restrict__ order,
+                                  int32_t* __restrict__ vblock) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = (int32_t)(keys[p] & 0xffffffffu);
+    order[p] = v;
+    vblock[v] = (int32_t)(p / V);
+  }
+}
+
+// (block of elem[t][i], t) for every incidence
+__global__ void k_elem_keys(const int32_t* __restrict__ elem, int64_t total, int d1, const int32_t* __restrict__ vblock,
+                            uint64_t* __restrict__ keys) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x)
+    keys[p] = ((uint64_t)vblock[elem[p]] << 32) | (uint64_t)(p / d1);
+}
+
+// (block, elem[t][i]) for every listed element and i
+__global__ void k_vert_keys(const uint64_t* __restrict__ ekeys, int64_t E, const int32_t* __restrict__ elem, int d1,
+                            uint64_t* __restrict__ keys) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E * d1; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = q / d1;
+    const int i = (int)(q - e * d1);
+    const uint64_t k = ekeys[e];
+    const int64_t t = (int64_t)(k & 0xffffffffu);
+    keys[q] = (k & 0xffffffff00000000ull) | (uint64_t)(uint32_t)elem[t * d1 + i];
+  }
+}
+
+__device__ __forceinline__ int lower_bound_low32(const uint64_t* __restrict__ keys, int lo, int hi, uint32_t x) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((uint32_t)(keys[mid] & 0xffffffffu) < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_split_lists(const uint64_t* __restrict__ ekeys, int64_t E, const uint64_t* __restrict__ vkeys,
+                              int64_t VT, const int32_t* __restrict__ elem, int d1, const int32_t* __restrict__ voff,
+                              int32_t* __restrict__ elist, uint16_t* __restrict__ lelem, int32_t* __restrict__ vlist,
+                              int* __restrict__ bad) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E; q += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = ekeys[q];
+    const int b = (int)(k >> 32);
+    const int32_t t = (int32_t)(k & 0xffffffffu);
+    elist[q] = t;
+    const int lo = voff[b], hi = voff[b + 1];
+    for (int i = 0; i < d1; ++i) {
+      const int pos = lower_bound_low32(vkeys, lo, hi, (uint32_t)elem[(int64_t)t * d1 + i]);
+      const int l = pos - lo;
+      if (l > 65535) atomicOr(bad, 1);
+      lelem[(int64_t)i * E + q] = (uint16_t)l;
+    }
+  }
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < VT; q += (int64_t)gridDim.x * blockDim.x)
+    vlist[q] = (int32_t)(vkeys[q] & 0xffffffffu);
+}
+
+__global__ void k_sorted_degrees(const int32_t* __restrict__ order, const int32_t* __restrict__ inc_ptr, int64_t N,
+                                 int32_t* __restrict__ deg) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+    const int v = order[p];
+    deg[p] = inc_ptr[v + 1] - inc_ptr[v];
+  }
+}
+
+// per owned row (position p in the locality order): local index, diagonal position, records
+__global__ void k_records(const int32_t* __restrict__ order, int64_t N, int V, int d1, int64_t NT,
+                          const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc,
+                          const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ slot,
+                          const int32_t* __restrict__ eoff, const int32_t* __restrict__ elist,
+                          const int32_t* __restrict__ voff, const int32_t* __restrict__ vlist,
+                          const int32_t* __restrict__ rec_off, uint16_t* __restrict__ own_local,
+                          uint8_t* __restrict__ dpos, uint32_t* __restrict__ rec, int* __restrict__ bad) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+    const int R = order[p];
+    const int b = (int)(p / V);
+    // local index of R in the block's vertex list
+    int lo = voff[b], hi = voff[b + 1];
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (vlist[mid] < R) lo = mid + 1;
+      else hi = mid;
+    }
+    own_local[p] = (uint16_t)(lo - voff[b]);
+    const int rp = row_ptr[R];
+    if (row_ptr[R + 1] - rp > 32) atomicOr(bad, 2);
+    const int e0 = eoff[b], e1 = eoff[b + 1];
+    if (e1 - e0 > 32768) atomicOr(bad, 4);
+    int w = rec_off[p];
+    uint8_t dp = 0;
+    for (int q = inc_ptr[R]; q < inc_ptr[R + 1]; ++q, ++w) {
+      const int pp = inc[q];
+      const int t = pp / d1, i = pp - t * d1;
+      int a = e0, c = e1;
+      while (a < c) {
+        const int mid = (a + c) >> 1;
+        if (elist[mid] < t) a = mid + 1;
+        else c = mid;
+      }
+      uint32_t r = (uint32_t)((a - e0) & 0x7fff) | ((uint32_t)i << 15);
+      int sh = 17;
+      for (int j = 0; j < d1; ++j) {
+        const int pos = slot[(int64_t)(i * d1 + j) * NT + t] - rp;
+        if (j == i) {
+          dp = (uint8_t)pos;
+          continue;
+        }
+        r |= (uint32_t)(pos & 31) << sh;
+        sh += 5;
+      }
+      rec[w] = r;
+    }
+    dpos[p] = dp;
+  }
+}
+
+__global__ void k_block_maxima(const int32_t* __restrict__ eoff, const int32_t* __restrict__ voff,
+                               const int32_t* __restrict__ order, const int32_t* __restrict__ row_ptr, int64_t N, int V,
+                               int nblocks, int* __restrict__ mx) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblocks; b += gridDim.x * blockDim.x) {
+    atomicMax(mx + 0, eoff[b + 1] - eoff[b]);
+    atomicMax(mx + 1, voff[b + 1] - voff[b]);
+    int s = 0;
+    const int64_t p1 = ((int64_t)(b + 1) * V < N) ? (int64_t)(b + 1) * V : N;
+    for (int64_t p = (int64_t)b * V; p < p1; ++p) s += row_ptr[order[p] + 1] - row_ptr[order[p]];
+    atomicMax(mx + 2, s);
+  }
+}
+
+}  // namespace
+
+void free_block_plan(BlockPlan& B) {
+  cudaFree(B.order);
+  cudaFree(B.rec_off);
+  cudaFree(B.own_local);
+  cudaFree(B.dpos);
+  cudaFree(B.eoff);
+  cudaFree(B.voff);
+  cudaFree(B.elist);
+  cudaFree(B.lelem);
+  cudaFree(B.vlist);
+  cudaFree(B.rec);
+  B = BlockPlan();
+}
+
+int build_block_plan(const Pattern* P, const double* node_hint, const int32_t* group, int V, BlockPlan* out,
+                     cudaStream_t s) {
+  const int d = P->d, d1 = P->d1;
+  const int64_t N = P->N, NT = P->NT, total = NT * d1;
+  BlockPlan B;
+  B.V = V;
+  B.nblocks = (int)((N + V - 1) / V);
+  if (N == 0 || NT == 0) {
+    *out = B;
+    return FEM_OK;
+  }
+  int rc = FEM_OK;
+  uint64_t *k1 = nullptr, *k2 = nullptr, *sorted = nullptr, *ek = nullptr, *vk = nullptr;
+  int32_t *vblock = nullptr, *deg = nullptr;
+  int* dev_int = nullptr;  // [0] bad flag, [1..3] maxima
+  unsigned long long* bbox = nullptr;
+  auto cleanup = [&]() {
+    cudaFreeAsync(k1, s);
+    cudaFreeAsync(k2, s);
+    cudaFreeAsync(ek, s);
+    cudaFreeAsync(vk, s);
+    cudaFreeAsync(vblock, s);
+    cudaFreeAsync(deg, s);
+    cudaFreeAsync(dev_int, s);
+    cudaFreeAsync(bbox, s);
+  };
+#define BP_TRY(x)              \
+  do {                         \
+    cudaError_t e_ = (x);      \
+    if (e_ != cudaSuccess) {   \
+      cleanup();               \
+      free_block_plan(B);      \
+      return cuda_error(e_, #x); \
+    }                          \
+  } while (0)
+#define BP_RC(x)             \
+  do {                       \
+    rc = (x);                \
+    if (rc) {                \
+      cleanup();             \
+      free_block_plan(B);    \
+      return rc;             \
+    }                        \
+  } while (0)
+  const int64_t big = std::max<int64_t>(N, total);
+  BP_TRY(cudaMallocAsync((void**)&k1, sizeof(uint64_t) * big, s));
+  BP_TRY(cudaMallocAsync((void**)&k2, sizeof(uint64_t) * big, s));
+  BP_TRY(cudaMallocAsync((void**)&vblock, sizeof(int32_t) * N, s));
+  BP_TRY(cudaMallocAsync((void**)&dev_int, sizeof(int) * 4, s));
+  BP_TRY(cudaMallocAsync((void**)&bbox, sizeof(unsigned long long) * 6, s));
+  BP_TRY(cudaMallocAsync((void**)&B.order, sizeof(int32_t) * N, s));
+  BP_TRY(cudaMemsetAsync(dev_int, 0, sizeof(int) * 4, s));
+  // 1. locality order of the vertices
+  if (node_hint) {
+    unsigned long long init[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
+    BP_TRY(cudaMemcpyAsync(bbox, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    FEM_LAUNCH(k_bbox, grid_for(N, 256, 1024), 256, 0, s, node_hint, N, d, bbox, bbox + 3);
+  }
+  FEM_LAUNCH(k_vertex_keys, grid_for(N, 256), 256, 0, s, node_hint, group, N, d, bbox, bbox + 3, k1);
+  BP_RC(radix_sort_u64(k1, k2, N, s, &sorted));
+  FEM_LAUNCH(k_order_from_keys, grid_for(N, 256), 256, 0, s, sorted, N, V, B.order, vblock);
+  // 2. element lists: unique (block, t) over all incidences
+  FEM_LAUNCH(k_elem_keys, grid_for(total, 256), 256, 0, s, P->elem, total, d1, vblock, k1);
+  BP_RC(radix_sort_u64(k1, k2, total, s, &sorted));
+  int64_t E = 0;
+  BP_TRY(cudaMallocAsync((void**)&ek, sizeof(uint64_t) * total, s));
+  BP_RC(unique_u64(sorted, total, ek, &E, s));
+  BP_TRY(cudaMallocAsync((void**)&B.eoff, sizeof(int32_t) * (B.nblocks + 1), s));
+  BP_RC(segment_starts(ek, E, B.nblocks, B.eoff, s));
+  // 3. vertex lists: unique (block, vertex) over the listed elements' vertices
+  const int64_t nvk = E * d1;
+  uint64_t *k3 = nullptr, *k4 = nullptr;
+  BP_TRY(cudaMallocAsync((void**)&k3, sizeof(uint64_t) * nvk, s));
+  BP_TRY(cudaMallocAsync((void**)&k4, sizeof(uint64_t) * nvk, s));
+  FEM_LAUNCH(k_vert_keys, grid_for(nvk, 256), 256, 0, s, ek, E, P->elem, d1, k3);
+  BP_RC(radix_sort_u64(k3, k4, nvk, s, &sorted));
+  int64_t VT = 0;
+  BP_TRY(cudaMallocAsync((void**)&vk, sizeof(uint64_t) * nvk, s));
+  BP_RC(unique_u64(sorted, nvk, vk, &VT, s));
+  cudaFreeAsync(k3, s);
+  cudaFreeAsync(k4, s);
+  BP_TRY(cudaMallocAsync((void**)&B.voff, sizeof(int32_t) * (B.nblocks + 1), s));
+  BP_RC(segment_starts(vk, VT, B.nblocks, B.voff, s));
+  // 4. element list, local vertex ids, vertex list
+  BP_TRY(cudaMallocAsync((void**)&B.elist, sizeof(int32_t) * E, s));
+  BP_TRY(cudaMallocAsync((void**)&B.lelem, sizeof(uint16_t) * E * d1, s));
+  BP_TRY(cudaMallocAsync((void**)&B.vlist, sizeof(int32_t) * VT, s));
+  FEM_LAUNCH(k_split_lists, grid_for(std::max(E, VT), 256), 256, 0, s, ek, E, vk, VT, P->elem, d1, B.voff, B.elist,
+             B.lelem, B.vlist, dev_int);
+  // 5. records of the owned rows
+  BP_TRY(cudaMallocAsync((void**)&deg, sizeof(int32_t) * N, s));
+  BP_TRY(cudaMallocAsync((void**)&B.rec_off, sizeof(int32_t) * (N + 1), s));
+  FEM_LAUNCH(k_sorted_degrees, grid_for(N, 256), 256, 0, s, B.order, P->inc_ptr, N, deg);
+  BP_RC(exclusive_scan(deg, B.rec_off, N, nullptr, s));
+  BP_TRY(cudaMallocAsync((void**)&B.own_local, sizeof(uint16_t) * N, s));
+  BP_TRY(cudaMallocAsync((void**)&B.dpos, sizeof(uint8_t) * N, s));
+  BP_TRY(cudaMallocAsync((void**)&B.rec, sizeof(uint32_t) * total, s));
+  FEM_LAUNCH(k_records, grid_for(N, 256), 256, 0, s, B.order, N, V, d1, NT, P->inc_ptr, P->inc, P->row_ptr, P->slot,
+             B.eoff, B.elist, B.voff, B.vlist, B.rec_off, B.own_local, B.dpos, B.rec, dev_int);
+  FEM_LAUNCH(k_block_maxima, grid_for(B.nblocks, 256), 256, 0, s, B.eoff, B.voff, B.order, P->row_ptr, N, V, B.nblocks,
+             dev_int + 1);
+  int hs[4] = {0, 0, 0, 0};
+  BP_TRY(cudaMemcpyAsync(hs, dev_int, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  BP_TRY(cudaStreamSynchronize(s));
+  B.E = E;
+  B.VT = VT;
+  B.max_e = hs[1];
+  B.max_v = hs[2];
+  B.max_acc = hs[3];
+  B.ok = (hs[0] == 0);
+  cleanup();
+#undef BP_TRY
+#undef BP_RC
+  *out = B;
+  return FEM_OK;
+}
+
+int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group, cudaStream_t s) {
+  free_block_plan(P->blk);
+  int V = (P->d == 2) ? 1024 : 512;
+  for (; V >= 32; V >>= 1) {
+    BlockPlan B;
+    int rc = build_block_plan(P, node_hint, group, V, &B, s);
+    if (rc) return rc;
+    // shared-memory need of the value kernel at the smallest sub-batch
+    const int W = (P->d1 * (P->d1 + 1)) / 2 + P->d1;
+    const int need = B.max_v * P->d * 8 + B.max_acc * 8 + V * (8 + 24) + 32 * W * 8 + 256;
+    if (B.ok && need <= 200 * 1024) {
+      P->blk = B;
+      return FEM_OK;
+    }
+    free_block_plan(B);
+  }
+  return FEM_OK;  // no feasible block size: the two-pass path serves this mesh
+}
+
+}  // namespace fem

@@ -64,6 +64,27 @@ inline int grid_for(int64_t n, int block, int max_blocks = 152 * 32) {
   return (int)g;
 }
 
+// ---- locality plan (owner-computes blocks), see blockplan.cu -----------------------------------------
+struct BlockPlan {
+  int V = 0, nblocks = 0;
+  int64_t E = 0, VT = 0;                  // listed elements / listed vertices over all blocks
+  int max_e = 0, max_v = 0, max_acc = 0;  // per-block maxima (shared-memory sizing)
+  bool ok = false;                        // the packed record limits hold for this mesh
+  int32_t* order = nullptr;               // [N] vertices in locality order; block b owns [b*V, b*V+V)
+  int32_t* rec_off = nullptr;             // [N+1] record offsets of the owned rows, locality order
+  uint16_t* own_local = nullptr;          // [N] local vertex id of each owned row in its block
+  uint8_t* dpos = nullptr;                // [N] in-row position of each owned row's diagonal
+  int32_t* eoff = nullptr;                // [nblocks+1] element-list offsets
+  int32_t* voff = nullptr;                // [nblocks+1] vertex-list offsets
+  int32_t* elist = nullptr;               // [E] caller element ids, ascending within a block
+  uint16_t* lelem = nullptr;              // [(d+1)][E] local vertex ids of the listed elements
+  int32_t* vlist = nullptr;               // [VT] global vertex ids, ascending within a block
+  uint32_t* rec = nullptr;                // [NT*(d+1)] packed incidence records
+};
+void free_block_plan(BlockPlan& B);
+int build_block_plan(const struct Pattern* P, const double* node_hint, const int32_t* group, int V, BlockPlan* out,
+                     cudaStream_t s);
+
 // ---- pattern object --------------------------------------------------------------------------------
 struct Pattern {
   int d = 0, d1 = 0;
@@ -77,7 +98,12 @@ struct Pattern {
   int32_t* inc = nullptr;      // [NT*(d+1)] entries t*(d+1)+i, ascending within a vertex
   double* scratch = nullptr;   // per-element values for the deterministic reduction
   int64_t scratch_elems = 0;   // doubles in scratch
+  BlockPlan blk;               // owner-computes locality plan (blk.ok == false: two-pass path only)
 };
+// (Re)build P->blk, halving the block size until the packed limits hold (blk.ok false if they never do).
+int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group, cudaStream_t s);
+int assemble_blocked(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg,
+                     double* val, double* b, cudaStream_t s);
 
 // scratch doubles per element: stiffness unique entries + rhs entries (+ gradient entries)
 inline int64_t scratch_per_elem(int d) { return d == 2 ? 9 : 14; }

@@ -62,6 +62,31 @@ def test_values_match_oracle(case, variant):
                 assert v[rp[r]:rp[r + 1]].tolist() == [0.0, -1.0, -1.0, 4.0, -1.0, -1.0, 0.0]
 
 
+@pytest.mark.parametrize("case", ["c1", "sq37p", "kuhn5", "kuhn7s", "delaunay2", "delaunay3"])
+def test_locality_plan_values_match_oracle(case):
+    """The owner-computes kernel with the geometric (Morton) block plan, and with the default plan."""
+    d, node, elem, k, f_kind = mesh_case(case)
+    N = node.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    rp, col, vo, so = oracle.assemble(d, node, elem, k)
+    bo = oracle.rhs(d, node, elem, f_kind)
+    kd = None if k is None else dev(k)
+    v_default, b_default = fa.assemble(p, dev(node), kd, f_kind, None, fa.FEM_DETERMINISTIC)
+    fa.fem_pattern_set_locality(p, dev(node))
+    val, b = fa.assemble(p, dev(node), kd, f_kind, None, fa.FEM_DETERMINISTIC)
+    fa.get_error()
+    for v_, b_ in ((val, b), (v_default, b_default)):
+        assert_close_scaled(host(v_), vo, so, what="stiffness")
+        assert_close_scaled(host(b_), bo, np.abs(bo), what="rhs")
+    # the geometric plan changes only which CTA owns a row, not the summation order of any entry
+    assert torch.equal(val, v_default) and torch.equal(b, b_default)
+    # and a plan built from other coordinates gives the same bits
+    rng = np.random.default_rng(3)
+    fa.fem_pattern_set_locality(p, dev(rng.normal(size=node.shape)))
+    v3, b3 = fa.assemble(p, dev(node), kd, f_kind, None, fa.FEM_DETERMINISTIC)
+    assert torch.equal(v3, val) and torch.equal(b3, b)
+
+
 def test_qp_values_rhs():
     d, node, elem, k, _ = mesh_case("sq37p")
     rng = np.random.default_rng(5)
@@ -297,6 +322,7 @@ def test_full_size_sampled_rows(cfg, variant):
     N, NT = node.shape[0], elem.shape[0]
     f_kind = oracle.F_SINPROD if m["f"] == "sinprod" else oracle.F_CONST
     p = fa.Pattern(dev(elem), N)
+    fa.fem_pattern_set_locality(p, dev(node))
     n = m["n"]
     exp_nnz = N + 2 * (3 * n * n + 2 * n) if d == 2 else N + 2 * (3 * n * (n + 1) ** 2 + 3 * n * n * (n + 1) + n ** 3)
     assert p.nnz == exp_nnz
