@@ -358,8 +358,9 @@ int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group
     if (rc) return rc;
     // shared-memory need of the value kernel at the smallest sub-batch
     const int W = (P->d1 * (P->d1 + 1)) / 2 + P->d1;
-    const int need = B.max_v * P->d * 8 + B.max_acc * 8 + V * (8 + 24) + 32 * W * 8 + 256;
-    if (B.ok && need <= 200 * 1024) {
+    // staged vertex: exact coordinate split (12 B per coordinate) + sin/cos pairs (32 B per 2-D vertex)
+    const int need = B.max_v * (P->d * 12 + (P->d == 2 ? 64 : 0)) + B.max_acc * 8 + V * (8 + 24) + 32 * W * 8 + 256;
+    if (B.ok && need <= 210 * 1024) {
       P->blk = B;
       return FEM_OK;
     }

@@ -1,0 +1,183 @@
+// Per-element local stiffness and load contributions in float-float arithmetic (see dfloat.cuh).
+//
+// Same formulas as element.cuh (Sec. 3.1.3, eq. (dlambda) and the a_ij formula below it; Sec. 3.2),
+// arranged for the FP32 pipe:
+//  * coordinates arrive as exact three-float splits, so every edge vector is formed to ~2^-47 of its
+//    own length (f3_diff);
+//  * 2-D: with ve_0 = x3 - x2, ve_1 = x1 - x3 (1-based vertices) and ve_2 = -(ve_0 + ve_1),
+//    2 area = ve_0 x ve_1, a_01 = s ve_0.ve_1, a_02 = -s (ve_0.ve_0 + ve_0.ve_1),
+//    a_12 = -s (ve_0.ve_1 + ve_1.ve_1), s = k / (2 |2 area|) (the paper's abs() of the area);
+//  * 3-D: with e_m = x_{m+1} - x_1, n_1 = e_2 x e_3, n_2 = e_3 x e_1, n_3 = e_1 x e_2 (the paper's faces
+//    [1 3 4], [1 4 2], [1 2 3]) and n_0 = -(n_1 + n_2 + n_3); volume = n_3 . e_3 / 6 (signed);
+//    a_ij = s n_i.n_j, s = k / (36 volume);
+//  * diagonals are minus the off-diagonal row sums (sum_i n_i = 0).
+#pragma once
+
+#include "dfloat.cuh"
+#include "element.cuh"
+
+namespace fem {
+
+// Staged vertex: exact splits of the coordinates, and for the sine-product load the values
+// sin(pi x/2), cos(pi x/2) of each coordinate (df).
+template <int D>
+struct VtxDF {
+  f3 x[D];
+};
+struct SC {
+  df2 s, c;
+};
+
+template <int D>
+struct LocalDF {
+  df2 a[(D + 1) * (D + 2) / 2];  // pidx order
+  df2 bt[D + 1];
+};
+
+// sin(pi x/2) and cos(pi x/2) from the exact split of x: x/2 = n + r with n = rint(a/2), r exact to
+// ~2^-47 of |r| (so values near the zeros of the sine keep their relative accuracy).
+__device__ __forceinline__ SC sincospi_half(const f3& x, const float4* __restrict__ tab) {
+  const float ah = 0.5f * x.a, bh = 0.5f * x.b, ch = 0.5f * x.c;
+  const float n = rintf(ah);
+  const df2 r0 = two_sum(__fsub_rn(ah, n), bh);
+  const df2 r = fast_two_sum(r0.h, __fadd_rn(r0.l, ch));
+  SC o;
+  df_sincospi_small(r, tab, o.s, o.c);
+  if (fmodf(fabsf(n), 2.0f) == 1.0f) {
+    o.s = df_neg(o.s);
+    o.c = df_neg(o.c);
+  }
+  return o;
+}
+
+// sin(pi (u + v)/2) = sin(pi u/2) cos(pi v/2) + cos(pi u/2) sin(pi v/2)
+__device__ __forceinline__ df2 sin_mid(const SC& u, const SC& v) { return df_add(df_mul(u.s, v.c), df_mul(u.c, v.s)); }
+
+__device__ __forceinline__ bool element_df2(const VtxDF<2>* const (&V)[3], const SC* const (&S)[3], df2 kt, bool want_a,
+                                            bool want_b, int f_kind, df2 fconst, const double* __restrict__ f_arg,
+                                            int64_t t, LocalDF<2>& L) {
+  df2 e0[2], e1[2];
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    e0[m] = f3_diff(V[2]->x[m], V[1]->x[m]);
+    e1[m] = f3_diff(V[0]->x[m], V[2]->x[m]);
+  }
+  const df2 a2 = df_sub(df_mul(e0[0], e1[1]), df_mul(e0[1], e1[0]));  // twice the signed area
+  const df2 a2abs = a2.h < 0.0f ? df_neg(a2) : a2;
+  const bool ok = a2abs.h > 0.0f && a2abs.h < INFINITY;
+  if (want_a) {
+    const df2 d00 = df_dot<2>(e0, e0), d11 = df_dot<2>(e1, e1), d01 = df_dot<2>(e0, e1);
+    const df2 s = df_mul(kt, df_recip(df_scale(a2abs, 2.0f)));
+    const df2 a01 = df_mul(s, d01);
+    const df2 a02 = df_neg(df_mul(s, df_add(d00, d01)));
+    const df2 a12 = df_neg(df_mul(s, df_add(d01, d11)));
+    L.a[3] = a01;
+    L.a[4] = a02;
+    L.a[5] = a12;
+    L.a[0] = df_neg(df_add(a01, a02));
+    L.a[1] = df_neg(df_add(a01, a12));
+    L.a[2] = df_neg(df_add(a02, a12));
+  }
+  if (want_b) {
+    const df2 meas = df_scale(a2abs, 0.5f);
+    df2 f[3];
+    if (f_kind == FEM_F_SINPROD) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int u = (q + 1) % 3, v = (q + 2) % 3;
+        f[q] = df_mul(sin_mid(S[u][0], S[v][0]), sin_mid(S[u][1], S[v][1]));
+      }
+    } else if (f_kind == FEM_F_QPVALUES) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) f[q] = df_from_double(__ldg(f_arg + t * 3 + q));
+    } else {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) f[q] = fconst;
+    }
+    const df2 w = df_mul(meas, df2{0.1666666716337204f, -4.9670538793e-09f});  // |tau| / 6
+#pragma unroll
+    for (int i = 0; i < 3; ++i) L.bt[i] = df_mul(w, df_add(f[(i + 1) % 3], f[(i + 2) % 3]));
+  }
+  return ok;
+}
+
+__device__ __forceinline__ void df_cross(const df2 (&u)[3], const df2 (&v)[3], df2 (&o)[3]) {
+  o[0] = df_sub(df_mul(u[1], v[2]), df_mul(u[2], v[1]));
+  o[1] = df_sub(df_mul(u[2], v[0]), df_mul(u[0], v[2]));
+  o[2] = df_sub(df_mul(u[0], v[1]), df_mul(u[1], v[0]));
+}
+
+__device__ __forceinline__ bool element_df3(const VtxDF<3>* const (&V)[4], df2 kt, bool want_a, bool want_b,
+                                            int f_kind, df2 fconst, const double* __restrict__ f_arg, int64_t t,
+                                            const float4* __restrict__ tab, LocalDF<3>& L) {
+  df2 e[3][3];  // e[m-1] = x_m - x_0
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) e[q][m] = f3_diff(V[q + 1]->x[m], V[0]->x[m]);
+  df2 n[4][3];
+  df_cross(e[1], e[2], n[1]);
+  df_cross(e[2], e[0], n[2]);
+  df_cross(e[0], e[1], n[3]);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) n[0][m] = df_neg(df_add(df_add(n[1][m], n[2][m]), n[3][m]));
+  const df2 vol6 = df_dot<3>(n[3], e[2]);  // 6 * signed volume
+  const bool ok = vol6.h > 0.0f && vol6.h < INFINITY;
+  if (want_a) {
+    const df2 s = df_mul(kt, df_recip(df_scale(vol6, 6.0f)));  // k / (36 vol)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) L.a[i] = df2{0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = i + 1; j < 4; ++j) {
+        const df2 aij = df_mul(s, df_dot<3>(n[i], n[j]));
+        L.a[pidx<3>(i, j)] = aij;
+        L.a[i] = df_sub(L.a[i], aij);
+        L.a[j] = df_sub(L.a[j], aij);
+      }
+  }
+  if (want_b) {
+    const df2 vol = df_mul(vol6, df2{0.1666666716337204f, -4.9670538793e-09f});
+    df2 f[4];
+    if (f_kind == FEM_F_SINPROD) {
+      // points x_q = sum_i lambda_i(q) x_i; per coordinate, shifted by an integer n near the element
+      // so that sin(pi x) keeps its relative accuracy next to integers
+      const df2 al = {0.58541017770767212f, 1.8917296174e-08f}, be = {0.13819660246372223f, -1.3387116971e-09f};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) f[q] = df_from(1.0f);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const float nn = rintf(V[0]->x[m].a);
+        df2 y[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const df2 ya = two_sum(V[i]->x[m].a, -nn);
+          y[i] = df_add(ya, fast_two_sum(V[i]->x[m].b, V[i]->x[m].c));
+        }
+        const df2 sy = df_add(df_add(y[0], y[1]), df_add(y[2], y[3]));
+        const float sgn = (fmodf(fabsf(nn), 2.0f) == 1.0f) ? -1.0f : 1.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const df2 xq = df_add(df_mul(be, sy), df_mul(df_sub(al, be), y[q]));
+          const df2 sv = df_sinpi(xq, tab);
+          f[q] = df_mul(f[q], df2{sv.h * sgn, sv.l * sgn});
+        }
+      }
+    } else if (f_kind == FEM_F_QPVALUES) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) f[q] = df_from_double(__ldg(f_arg + t * 4 + q));
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) f[q] = fconst;
+    }
+    const df2 al = {0.58541017770767212f, 1.8917296174e-08f}, be = {0.13819660246372223f, -1.3387116971e-09f};
+    const df2 fs = df_add(df_add(f[0], f[1]), df_add(f[2], f[3]));
+    const df2 w = df_scale(vol, 0.25f);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) L.bt[i] = df_mul(w, df_add(df_mul(be, fs), df_mul(df_sub(al, be), f[i])));
+  }
+  return ok;
+}
+
+}  // namespace fem

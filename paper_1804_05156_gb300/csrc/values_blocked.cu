@@ -1,22 +1,54 @@
-// Owner-computes value kernel: one CTA per block of rows (see blockplan.cu).
+// Owner-computes value kernel: one CTA per block of rows (see blockplan.cu), float-float arithmetic.
 //
-// 1. Stage the coordinates of every vertex the block's elements use in shared memory (each vertex is
-//    read from HBM once per block, coalesced through the block's vertex list).
-// 2. For sub-batches of the block's element list: compute the local stiffness and load entries of
-//    each element into shared memory, then let each owned row add the entries of its incidences in
-//    this sub-batch into its shared-memory accumulator, in ascending element order.
-// 3. Write every owned row once: val[row_ptr[R] + p] (coalesced along the row) and b[R].
-// No atomics; the summation order of every CSR entry is fixed by the plan (deterministic).
+// 1. Stage every vertex the block's elements use in shared memory, once per block: the exact
+//    three-float split of its coordinates and, for the sine-product load, sin/cos(pi x/2) of each
+//    coordinate (the edge midpoints then need only angle additions).
+// 2. For sub-batches of the block's element list: compute each element's local stiffness and load
+//    entries (element_df.cuh) into shared memory, then let each owned row add the entries of its
+//    incidences in this sub-batch into its shared-memory accumulator, in ascending element order.
+// 3. Write every owned row once: val[row_ptr[R] + p] (coalesced along the row) and b[R], converting
+//    float-float to double with integer operations.
+// No atomics and no FP64 instructions; the summation order of every CSR entry is fixed by the plan.
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <mutex>
+
 #include "common.cuh"
-#include "element.cuh"
+#include "element_df.cuh"
 
 namespace fem {
 
 namespace {
 
 constexpr int BT = 256;  // threads per CTA
+
+static __device__ float4 g_sincos_tab[kSinTabN + 1];
+std::mutex g_tab_mu;
+bool g_tab_ready[64] = {false};
+
+// sin(pi k/2048), cos(pi k/2048) for k = 0..1024, as float pairs, on the current device (once).
+int ensure_sincos_table() {
+  int dev = 0;
+  FEM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_error(FEM_ERR_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  if (g_tab_ready[dev]) return FEM_OK;
+  static float4 host[kSinTabN + 1];
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k <= kSinTabN; ++k) {
+    const double a = pi * (double)k / 2048.0;
+    const double s = std::sin(a), c = std::cos(a);
+    const float sh = (float)s, ch = (float)c;
+    host[k] = make_float4(sh, (float)(s - (double)sh), ch, (float)(c - (double)ch));
+  }
+  // exact values where they are known
+  host[0] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+  host[kSinTabN] = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+  FEM_CUDA(cudaMemcpyToSymbol(g_sincos_tab, host, sizeof(host)));
+  g_tab_ready[dev] = true;
+  return FEM_OK;
+}
 
 struct BlkArgs {
   int64_t N, NT, E;
@@ -31,7 +63,7 @@ struct BlkArgs {
   const int32_t* vlist;
   const uint32_t* rec;
   const int32_t* row_ptr;
-  int xs_bytes, ev_bytes, acc_bytes;  // shared-memory carve-up
+  int xs_bytes, sc_bytes, ev_bytes, acc_bytes;  // shared-memory carve-up
 };
 
 struct RowMeta {
@@ -39,17 +71,19 @@ struct RowMeta {
 };
 
 template <int D>
-__global__ void __launch_bounds__(BT) k_blocked(BlkArgs a, const double* __restrict__ node, const double* __restrict__ k,
-                                                int f_kind, const double* __restrict__ f_arg, double* __restrict__ val,
-                                                double* __restrict__ bvec, int* __restrict__ err) {
+__global__ void __launch_bounds__(BT) k_blocked_df(BlkArgs a, const double* __restrict__ node, const double* __restrict__ k,
+                                                   int f_kind, const double* __restrict__ f_arg, double* __restrict__ val,
+                                                   double* __restrict__ bvec, int* __restrict__ err) {
   constexpr int D1 = D + 1, U = D1 * (D1 + 1) / 2, W = U + D1;
   extern __shared__ __align__(16) unsigned char sm[];
-  double* xs = reinterpret_cast<double*>(sm);
-  double* ev = reinterpret_cast<double*>(sm + a.xs_bytes);
-  double* acc = reinterpret_cast<double*>(sm + a.xs_bytes + a.ev_bytes);
-  double* bacc = reinterpret_cast<double*>(sm + a.xs_bytes + a.ev_bytes + a.acc_bytes);
+  VtxDF<D>* xs = reinterpret_cast<VtxDF<D>*>(sm);
+  SC* scs = reinterpret_cast<SC*>(sm + a.xs_bytes);
+  df2* ev = reinterpret_cast<df2*>(sm + a.xs_bytes + a.sc_bytes);
+  df2* acc = reinterpret_cast<df2*>(sm + a.xs_bytes + a.sc_bytes + a.ev_bytes);
+  df2* bacc = reinterpret_cast<df2*>(sm + a.xs_bytes + a.sc_bytes + a.ev_bytes + a.acc_bytes);
   RowMeta* meta = reinterpret_cast<RowMeta*>(bacc + a.V);
   __shared__ int scan_tmp[BT];
+  const float4* tab = g_sincos_tab;
 
   const int blk = blockIdx.x;
   const int e0 = a.eoff[blk], ne = a.eoff[blk + 1] - e0;
@@ -57,11 +91,18 @@ __global__ void __launch_bounds__(BT) k_blocked(BlkArgs a, const double* __restr
   const int64_t p0 = (int64_t)blk * a.V;
   const int nown = (int)((a.N - p0) < a.V ? (a.N - p0) : a.V);
   const int tid = threadIdx.x;
+  const bool sinprod2 = (D == 2) && f_kind == FEM_F_SINPROD;
 
   for (int v = tid; v < nv; v += BT) {
     const int64_t R = a.vlist[v0 + v];
+    VtxDF<D> x;
 #pragma unroll
-    for (int m = 0; m < D; ++m) xs[v * D + m] = __ldg(node + R * D + m);
+    for (int m = 0; m < D; ++m) x.x[m] = split3(__ldg(node + R * D + m));
+    xs[v] = x;
+    if (sinprod2) {
+#pragma unroll
+      for (int m = 0; m < D; ++m) scs[v * D + m] = sincospi_half(x.x[m], tab);
+    }
   }
   // owned rows: contiguous chunk of rows per thread for the offset scan
   const int rpt = (nown + BT - 1) / BT;
@@ -92,26 +133,33 @@ __global__ void __launch_bounds__(BT) k_blocked(BlkArgs a, const double* __restr
     meta[r].off = off;
     off += meta[r].rl_dp & 0xff;
   }
-  for (int q = tid; q < total_acc; q += BT) acc[q] = 0.0;
-  for (int r = tid; r < nown; r += BT) bacc[r] = 0.0;
+  for (int q = tid; q < total_acc; q += BT) acc[q] = df2{0.0f, 0.0f};
+  for (int r = tid; r < nown; r += BT) bacc[r] = df2{0.0f, 0.0f};
   __syncthreads();
 
   const bool want_a = val != nullptr, want_b = bvec != nullptr;
+  const df2 fconst = (f_kind == FEM_F_CONST && f_arg) ? df_from_double(__ldg(f_arg)) : df2{1.0f, 0.0f};
   for (int sb = 0; sb < ne; sb += a.SB) {
     const int nb = (ne - sb < a.SB) ? ne - sb : a.SB;
     for (int e = tid; e < nb; e += BT) {
       const int64_t idx = e0 + sb + e;
       const int64_t t = a.elist[idx];
-      double x[D1][D];
+      int lv[D1];
 #pragma unroll
-      for (int i = 0; i < D1; ++i) {
-        const int lv = a.lelem[(int64_t)i * a.E + idx];
-#pragma unroll
-        for (int m = 0; m < D; ++m) x[i][m] = xs[lv * D + m];
+      for (int i = 0; i < D1; ++i) lv[i] = a.lelem[(int64_t)i * a.E + idx];
+      const df2 kt = k ? df_from_double(__ldg(k + t)) : df2{1.0f, 0.0f};
+      LocalDF<D> L;
+      bool ok;
+      if constexpr (D == 2) {
+        const VtxDF<2>* const V[3] = {&xs[lv[0]], &xs[lv[1]], &xs[lv[2]]};
+        const SC* const S[3] = {&scs[lv[0] * 2], &scs[lv[1] * 2], &scs[lv[2] * 2]};
+        ok = element_df2(V, S, kt, want_a, want_b, f_kind, fconst, f_arg, t, L);
+      } else {
+        const VtxDF<3>* const V[4] = {&xs[lv[0]], &xs[lv[1]], &xs[lv[2]], &xs[lv[3]]};
+        ok = element_df3(V, kt, want_a, want_b, f_kind, fconst, f_arg, t, tab, L);
       }
-      Local<D> L;
-      if (!element_local<D>(x, k ? __ldg(k + t) : 1.0, want_a, want_b, f_kind, f_arg, t, L)) report(err, FEM_ERR_DEGENERATE);
-      double* dst = ev + (int64_t)e * W;
+      if (!ok) report(err, FEM_ERR_DEGENERATE);
+      df2* dst = ev + (int64_t)e * W;
       if (want_a) {
 #pragma unroll
         for (int c = 0; c < U; ++c) dst[c] = L.a[c];
@@ -126,26 +174,26 @@ __global__ void __launch_bounds__(BT) k_blocked(BlkArgs a, const double* __restr
     for (int r = tid; r < nown; r += BT) {
       RowMeta m = meta[r];
       const int dp = m.rl_dp >> 8;
-      double ba = bacc[r];
+      df2 ba = bacc[r];
       int c = m.cur;
       for (; c < m.end; ++c) {
         const uint32_t rc = a.rec[c];
         const int e = (int)(rc & 0x7fff);
         if (e >= sb_end) break;
-        const double* src = ev + (int64_t)(e - sb) * W;
+        const df2* src = ev + (int64_t)(e - sb) * W;
         const int i = (rc >> 15) & 3;
         if (want_a) {
-          acc[m.off + dp] += src[pidx_rt<D>(i, i)];
+          acc[m.off + dp] = df_add(acc[m.off + dp], src[pidx_rt<D>(i, i)]);
           int sh = 17;
 #pragma unroll
           for (int j = 0; j < D1; ++j) {
             if (j == i) continue;
             const int pos = (rc >> sh) & 31;
-            acc[m.off + pos] += src[pidx_rt<D>(i, j)];
+            acc[m.off + pos] = df_add(acc[m.off + pos], src[pidx_rt<D>(i, j)]);
             sh += 5;
           }
         }
-        if (want_b) ba += src[U + i];
+        if (want_b) ba = df_add(ba, src[U + i]);
       }
       meta[r].cur = c;
       bacc[r] = ba;
@@ -161,11 +209,11 @@ __global__ void __launch_bounds__(BT) k_blocked(BlkArgs a, const double* __restr
         if (meta[mid].off <= q) lo = mid;
         else hi = mid - 1;
       }
-      val[meta[lo].rp + (q - meta[lo].off)] = acc[q];
+      val[meta[lo].rp + (q - meta[lo].off)] = df_to_double(acc[q]);
     }
   }
   if (want_b)
-    for (int r = tid; r < nown; r += BT) bvec[meta[r].R] = bacc[r];
+    for (int r = tid; r < nown; r += BT) bvec[meta[r].R] = df_to_double(bacc[r]);
 }
 
 }  // namespace
@@ -174,6 +222,8 @@ int assemble_blocked(const Pattern* P, const double* node, const double* k, int 
                      double* val, double* b, cudaStream_t s) {
   int* err = device_error_word();
   if (!err) return set_error(FEM_ERR_OOM, "cannot allocate the device error word");
+  int rc = ensure_sincos_table();
+  if (rc) return rc;
   const BlockPlan& B = P->blk;
   if (P->NT == 0 || B.nblocks == 0) {
     if (val && P->nnz > 0) FEM_CUDA(cudaMemsetAsync(val, 0, sizeof(double) * P->nnz, s));
@@ -196,22 +246,23 @@ int assemble_blocked(const Pattern* P, const double* node, const double* k, int 
   a.vlist = B.vlist;
   a.rec = B.rec;
   a.row_ptr = P->row_ptr;
-  const int budget = 200 * 1024;
-  a.xs_bytes = ((B.max_v * D * 8) + 15) / 16 * 16;
+  const int budget = 210 * 1024;
+  a.xs_bytes = ((B.max_v * D * (int)sizeof(f3)) + 15) / 16 * 16;
+  a.sc_bytes = (D == 2 && f_kind == FEM_F_SINPROD) ? ((B.max_v * D * (int)sizeof(SC)) + 15) / 16 * 16 : 0;
   a.acc_bytes = ((B.max_acc * 8) + 15) / 16 * 16;
-  const int fixed = a.xs_bytes + a.acc_bytes + B.V * 8 + B.V * (int)sizeof(RowMeta);
-  int sbmax = (budget - fixed) / (W * 8);
-  if (sbmax < 32) return set_error(FEM_ERR_STATE, "block too large for shared memory");
+  const int fixed = a.xs_bytes + a.sc_bytes + a.acc_bytes + B.V * 8 + B.V * (int)sizeof(RowMeta);
+  const int sbmax = (budget - fixed) / (W * 8);
+  if (sbmax < 32) return assemble_values(P, node, k, f_kind, f_arg, val, b, FEM_DETERMINISTIC, s);
   a.SB = sbmax < B.max_e ? (sbmax / 32) * 32 : B.max_e;
   if (a.SB < 1) a.SB = 1;
   a.ev_bytes = ((a.SB * W * 8) + 15) / 16 * 16;
   const int smem = fixed + a.ev_bytes;
   if (D == 2) {
-    FEM_CUDA(cudaFuncSetAttribute(k_blocked<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    FEM_LAUNCH(k_blocked<2>, B.nblocks, BT, smem, s, a, node, k, f_kind, f_arg, val, b, err);
+    FEM_CUDA(cudaFuncSetAttribute(k_blocked_df<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    FEM_LAUNCH(k_blocked_df<2>, B.nblocks, BT, smem, s, a, node, k, f_kind, f_arg, val, b, err);
   } else {
-    FEM_CUDA(cudaFuncSetAttribute(k_blocked<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    FEM_LAUNCH(k_blocked<3>, B.nblocks, BT, smem, s, a, node, k, f_kind, f_arg, val, b, err);
+    FEM_CUDA(cudaFuncSetAttribute(k_blocked_df<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    FEM_LAUNCH(k_blocked_df<3>, B.nblocks, BT, smem, s, a, node, k, f_kind, f_arg, val, b, err);
   }
   return FEM_OK;
 }
