@@ -65,7 +65,7 @@ __device__ __forceinline__ df2 df_mul_f(df2 a, float b) {
   e = __fmaf_rn(a.l, b, e);
   return fast_two_sum(p, e);
 }
-// exact scaling by a power of two
+// scaling by a power of two (exact; any other factor needs df_mul_f)
 __device__ __forceinline__ df2 df_scale(df2 a, float pow2) { return {__fmul_rn(a.h, pow2), __fmul_rn(a.l, pow2)}; }
 
 // 1/a: a float reciprocal refined by one Newton step carried in df (error ~2^-46 relative)

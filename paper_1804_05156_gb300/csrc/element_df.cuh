@@ -4,11 +4,11 @@
 // arranged for the FP32 pipe:
 //  * coordinates arrive as exact three-float splits, so every edge vector is formed to ~2^-47 of its
 //    own length (f3_diff);
-//  * 2-D: with ve_0 = x3 - x2, ve_1 = x1 - x3 (1-based vertices) and ve_2 = -(ve_0 + ve_1),
-//    2 area = ve_0 x ve_1, a_01 = s ve_0.ve_1, a_02 = -s (ve_0.ve_0 + ve_0.ve_1),
-//    a_12 = -s (ve_0.ve_1 + ve_1.ve_1), s = k / (2 |2 area|) (the paper's abs() of the area);
+//  * 2-D: ve_0 = x3 - x2, ve_1 = x1 - x3, ve_2 = x2 - x1 (1-based vertices), 2 area = ve_1 x ve_2,
+//    a_ij = s ve_i.ve_j, s = k / (2 |2 area|) (the paper's abs() of the area);
 //  * 3-D: with e_m = x_{m+1} - x_1, n_1 = e_2 x e_3, n_2 = e_3 x e_1, n_3 = e_1 x e_2 (the paper's faces
-//    [1 3 4], [1 4 2], [1 2 3]) and n_0 = -(n_1 + n_2 + n_3); volume = n_3 . e_3 / 6 (signed);
+//    [1 3 4], [1 4 2], [1 2 3]) and n_0 = (x_4 - x_2) x (x_3 - x_2) (face [2 4 3]); every edge is
+//    formed from its own endpoints, so each normal's rounding stays relative to its own face; volume = n_3 . e_3 / 6 (signed);
 //    a_ij = s n_i.n_j, s = k / (36 volume);
 //  * diagonals are minus the off-diagonal row sums (sum_i n_i = 0).
 #pragma once
@@ -56,21 +56,22 @@ __device__ __forceinline__ df2 sin_mid(const SC& u, const SC& v) { return df_add
 __device__ __forceinline__ bool element_df2(const VtxDF<2>* const (&V)[3], const SC* const (&S)[3], df2 kt, bool want_a,
                                             bool want_b, int f_kind, df2 fconst, const double* __restrict__ f_arg,
                                             int64_t t, LocalDF<2>& L) {
-  df2 e0[2], e1[2];
+  // side vectors ve_i (side opposite vertex i), each formed from its own endpoints
+  df2 e[3][2];
 #pragma unroll
   for (int m = 0; m < 2; ++m) {
-    e0[m] = f3_diff(V[2]->x[m], V[1]->x[m]);
-    e1[m] = f3_diff(V[0]->x[m], V[2]->x[m]);
+    e[0][m] = f3_diff(V[2]->x[m], V[1]->x[m]);
+    e[1][m] = f3_diff(V[0]->x[m], V[2]->x[m]);
+    e[2][m] = f3_diff(V[1]->x[m], V[0]->x[m]);
   }
-  const df2 a2 = df_sub(df_mul(e0[0], e1[1]), df_mul(e0[1], e1[0]));  // twice the signed area
+  const df2 a2 = df_sub(df_mul(e[1][0], e[2][1]), df_mul(e[1][1], e[2][0]));  // twice the signed area
   const df2 a2abs = a2.h < 0.0f ? df_neg(a2) : a2;
   const bool ok = a2abs.h > 0.0f && a2abs.h < INFINITY;
   if (want_a) {
-    const df2 d00 = df_dot<2>(e0, e0), d11 = df_dot<2>(e1, e1), d01 = df_dot<2>(e0, e1);
     const df2 s = df_mul(kt, df_recip(df_scale(a2abs, 2.0f)));
-    const df2 a01 = df_mul(s, d01);
-    const df2 a02 = df_neg(df_mul(s, df_add(d00, d01)));
-    const df2 a12 = df_neg(df_mul(s, df_add(d01, d11)));
+    const df2 a01 = df_mul(s, df_dot<2>(e[0], e[1]));
+    const df2 a02 = df_mul(s, df_dot<2>(e[0], e[2]));
+    const df2 a12 = df_mul(s, df_dot<2>(e[1], e[2]));
     L.a[3] = a01;
     L.a[4] = a02;
     L.a[5] = a12;
@@ -119,12 +120,19 @@ __device__ __forceinline__ bool element_df3(const VtxDF<3>* const (&V)[4], df2 k
   df_cross(e[1], e[2], n[1]);
   df_cross(e[2], e[0], n[2]);
   df_cross(e[0], e[1], n[3]);
+  {
+    df2 u[3], v[3];  // x_3 - x_1 and x_2 - x_1 (0-based), the edges of face [2 4 3]
 #pragma unroll
-  for (int m = 0; m < 3; ++m) n[0][m] = df_neg(df_add(df_add(n[1][m], n[2][m]), n[3][m]));
+    for (int m = 0; m < 3; ++m) {
+      u[m] = f3_diff(V[3]->x[m], V[1]->x[m]);
+      v[m] = f3_diff(V[2]->x[m], V[1]->x[m]);
+    }
+    df_cross(u, v, n[0]);
+  }
   const df2 vol6 = df_dot<3>(n[3], e[2]);  // 6 * signed volume
   const bool ok = vol6.h > 0.0f && vol6.h < INFINITY;
   if (want_a) {
-    const df2 s = df_mul(kt, df_recip(df_scale(vol6, 6.0f)));  // k / (36 vol)
+    const df2 s = df_mul(kt, df_recip(df_mul_f(vol6, 6.0f)));  // k / (36 vol)
 #pragma unroll
     for (int i = 0; i < 4; ++i) L.a[i] = df2{0.0f, 0.0f};
 #pragma unroll
