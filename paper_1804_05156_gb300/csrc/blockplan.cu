@@ -351,7 +351,7 @@ int build_block_plan(const Pattern* P, const double* node_hint, const int32_t* g
 
 int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group, cudaStream_t s) {
   free_block_plan(P->blk);
-  int V = (P->d == 2) ? 1024 : 512;
+  int V = 512;
   for (; V >= 32; V >>= 1) {
     BlockPlan B;
     int rc = build_block_plan(P, node_hint, group, V, &B, s);
@@ -359,8 +359,8 @@ int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group
     // shared-memory need of the value kernel at the smallest sub-batch
     const int W = (P->d1 * (P->d1 + 1)) / 2 + P->d1;
     // staged vertex: exact coordinate split (12 B per coordinate) + sin/cos pairs (32 B per 2-D vertex)
-    const int need = B.max_v * (P->d * 12 + (P->d == 2 ? 64 : 0)) + B.max_acc * 8 + V * (8 + 24) + 32 * W * 8 + 256;
-    if (B.ok && need <= 210 * 1024) {
+    const int need = B.max_v * (P->d * 12 + (P->d == 2 ? 64 : 0)) + B.max_acc * 10 + V * (8 + 24) + 32 * W * 8 + 256;
+    if (B.ok && need <= 220 * 1024) {
       P->blk = B;
       return FEM_OK;
     }

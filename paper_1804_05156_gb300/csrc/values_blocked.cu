@@ -21,8 +21,6 @@ namespace fem {
 
 namespace {
 
-constexpr int BT = 256;  // threads per CTA
-
 static __device__ float4 g_sincos_tab[kSinTabN + 1];
 std::mutex g_tab_mu;
 bool g_tab_ready[64] = {false};
@@ -70,7 +68,7 @@ struct RowMeta {
   int off, cur, end, rp, R, rl_dp;  // accumulator offset, record cursor/end, row_ptr, vertex, rowlen | dpos << 8
 };
 
-template <int D>
+template <int D, int BT>
 __global__ void __launch_bounds__(BT) k_blocked_df(BlkArgs a, const double* __restrict__ node, const double* __restrict__ k,
                                                    int f_kind, const double* __restrict__ f_arg, double* __restrict__ val,
                                                    double* __restrict__ bvec, int* __restrict__ err) {
@@ -82,6 +80,7 @@ __global__ void __launch_bounds__(BT) k_blocked_df(BlkArgs a, const double* __re
   df2* acc = reinterpret_cast<df2*>(sm + a.xs_bytes + a.sc_bytes + a.ev_bytes);
   df2* bacc = reinterpret_cast<df2*>(sm + a.xs_bytes + a.sc_bytes + a.ev_bytes + a.acc_bytes);
   RowMeta* meta = reinterpret_cast<RowMeta*>(bacc + a.V);
+  uint16_t* ridx = reinterpret_cast<uint16_t*>(meta + a.V);  // owning row of each accumulator entry
   __shared__ int scan_tmp[BT];
   const float4* tab = g_sincos_tab;
 
@@ -131,7 +130,9 @@ __global__ void __launch_bounds__(BT) k_blocked_df(BlkArgs a, const double* __re
   const int total_acc = scan_tmp[BT - 1];
   for (int r = r0; r < r1; ++r) {
     meta[r].off = off;
-    off += meta[r].rl_dp & 0xff;
+    const int rl = meta[r].rl_dp & 0xff;
+    for (int q = 0; q < rl; ++q) ridx[off + q] = (uint16_t)r;
+    off += rl;
   }
   for (int q = tid; q < total_acc; q += BT) acc[q] = df2{0.0f, 0.0f};
   for (int r = tid; r < nown; r += BT) bacc[r] = df2{0.0f, 0.0f};
@@ -203,13 +204,8 @@ __global__ void __launch_bounds__(BT) k_blocked_df(BlkArgs a, const double* __re
   // write-out: flattened over the block's accumulator entries, coalesced along each row
   if (want_a) {
     for (int q = tid; q < total_acc; q += BT) {
-      int lo = 0, hi = nown - 1;  // last row with off <= q
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (meta[mid].off <= q) lo = mid;
-        else hi = mid - 1;
-      }
-      val[meta[lo].rp + (q - meta[lo].off)] = df_to_double(acc[q]);
+      const int r = ridx[q];
+      val[meta[r].rp + (q - meta[r].off)] = df_to_double(acc[q]);
     }
   }
   if (want_b)
@@ -246,24 +242,36 @@ int assemble_blocked(const Pattern* P, const double* node, const double* k, int 
   a.vlist = B.vlist;
   a.rec = B.rec;
   a.row_ptr = P->row_ptr;
-  const int budget = 210 * 1024;
+  const int budget = 220 * 1024;
   a.xs_bytes = ((B.max_v * D * (int)sizeof(f3)) + 15) / 16 * 16;
   a.sc_bytes = (D == 2 && f_kind == FEM_F_SINPROD) ? ((B.max_v * D * (int)sizeof(SC)) + 15) / 16 * 16 : 0;
   a.acc_bytes = ((B.max_acc * 8) + 15) / 16 * 16;
-  const int fixed = a.xs_bytes + a.sc_bytes + a.acc_bytes + B.V * 8 + B.V * (int)sizeof(RowMeta);
+  const int fixed = a.xs_bytes + a.sc_bytes + a.acc_bytes + B.V * 8 + B.V * (int)sizeof(RowMeta) +
+                    ((B.max_acc * 2 + 15) / 16) * 16;
+  // threads per CTA: as many as the registers allow (2-D 1024, 3-D 512), and a sub-batch of at least
+  // one element per thread when shared memory allows it
+  int bt = (D == 2) ? 1024 : 512;
+  while (bt > 256 && (budget - fixed) / (W * 8) < bt) bt >>= 1;
   const int sbmax = (budget - fixed) / (W * 8);
   if (sbmax < 32) return assemble_values(P, node, k, f_kind, f_arg, val, b, FEM_DETERMINISTIC, s);
   a.SB = sbmax < B.max_e ? (sbmax / 32) * 32 : B.max_e;
   if (a.SB < 1) a.SB = 1;
   a.ev_bytes = ((a.SB * W * 8) + 15) / 16 * 16;
   const int smem = fixed + a.ev_bytes;
+#define FEM_BLK_LAUNCH(DD, TT)                                                                                \
+  do {                                                                                                        \
+    FEM_CUDA(cudaFuncSetAttribute(k_blocked_df<DD, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));   \
+    FEM_LAUNCH((k_blocked_df<DD, TT>), B.nblocks, TT, smem, s, a, node, k, f_kind, f_arg, val, b, err);        \
+  } while (0)
   if (D == 2) {
-    FEM_CUDA(cudaFuncSetAttribute(k_blocked_df<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    FEM_LAUNCH(k_blocked_df<2>, B.nblocks, BT, smem, s, a, node, k, f_kind, f_arg, val, b, err);
+    if (bt == 1024) FEM_BLK_LAUNCH(2, 1024);
+    else if (bt == 512) FEM_BLK_LAUNCH(2, 512);
+    else FEM_BLK_LAUNCH(2, 256);
   } else {
-    FEM_CUDA(cudaFuncSetAttribute(k_blocked_df<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    FEM_LAUNCH(k_blocked_df<3>, B.nblocks, BT, smem, s, a, node, k, f_kind, f_arg, val, b, err);
+    if (bt == 512) FEM_BLK_LAUNCH(3, 512);
+    else FEM_BLK_LAUNCH(3, 256);
   }
+#undef FEM_BLK_LAUNCH
   return FEM_OK;
 }
 
