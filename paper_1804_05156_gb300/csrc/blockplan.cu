@@ -351,7 +351,7 @@ int build_block_plan(const Pattern* P, const double* node_hint, const int32_t* g
 
 int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group, cudaStream_t s) {
   free_block_plan(P->blk);
-  int V = 512;
+  int V = (P->d == 2) ? 256 : 512;
   for (; V >= 32; V >>= 1) {
     BlockPlan B;
     int rc = build_block_plan(P, node_hint, group, V, &B, s);

@@ -68,8 +68,8 @@ struct RowMeta {
   int off, cur, end, rp, R, rl_dp;  // accumulator offset, record cursor/end, row_ptr, vertex, rowlen | dpos << 8
 };
 
-template <int D, int BT>
-__global__ void __launch_bounds__(BT) k_blocked_df(BlkArgs a, const double* __restrict__ node, const double* __restrict__ k,
+template <int D, int BT, int MINB>
+__global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double* __restrict__ node, const double* __restrict__ k,
                                                    int f_kind, const double* __restrict__ f_arg, double* __restrict__ val,
                                                    double* __restrict__ bvec, int* __restrict__ err) {
   constexpr int D1 = D + 1, U = D1 * (D1 + 1) / 2, W = U + D1;
@@ -184,17 +184,17 @@ __global__ void __launch_bounds__(BT) k_blocked_df(BlkArgs a, const double* __re
         const df2* src = ev + (int64_t)(e - sb) * W;
         const int i = (rc >> 15) & 3;
         if (want_a) {
-          acc[m.off + dp] = df_add(acc[m.off + dp], src[pidx_rt<D>(i, i)]);
+          acc[m.off + dp] = df_acc(acc[m.off + dp], src[pidx_rt<D>(i, i)]);
           int sh = 17;
 #pragma unroll
           for (int j = 0; j < D1; ++j) {
             if (j == i) continue;
             const int pos = (rc >> sh) & 31;
-            acc[m.off + pos] = df_add(acc[m.off + pos], src[pidx_rt<D>(i, j)]);
+            acc[m.off + pos] = df_acc(acc[m.off + pos], src[pidx_rt<D>(i, j)]);
             sh += 5;
           }
         }
-        if (want_b) ba = df_add(ba, src[U + i]);
+        if (want_b) ba = df_acc(ba, src[U + i]);
       }
       meta[r].cur = c;
       bacc[r] = ba;
@@ -242,35 +242,35 @@ int assemble_blocked(const Pattern* P, const double* node, const double* k, int 
   a.vlist = B.vlist;
   a.rec = B.rec;
   a.row_ptr = P->row_ptr;
-  const int budget = 220 * 1024;
+  // 2-D: 512 threads and at most ~110 KB of shared memory, so two CTAs share an SM and hide each
+  // other's barrier waits; 3-D: one 512-thread CTA with up to 220 KB.
+  const int budget = (D == 2) ? 110 * 1024 : 220 * 1024;
   a.xs_bytes = ((B.max_v * D * (int)sizeof(f3)) + 15) / 16 * 16;
   a.sc_bytes = (D == 2 && f_kind == FEM_F_SINPROD) ? ((B.max_v * D * (int)sizeof(SC)) + 15) / 16 * 16 : 0;
   a.acc_bytes = ((B.max_acc * 8) + 15) / 16 * 16;
   const int fixed = a.xs_bytes + a.sc_bytes + a.acc_bytes + B.V * 8 + B.V * (int)sizeof(RowMeta) +
                     ((B.max_acc * 2 + 15) / 16) * 16;
-  // threads per CTA: as many as the registers allow (2-D 1024, 3-D 512), and a sub-batch of at least
-  // one element per thread when shared memory allows it
-  int bt = (D == 2) ? 1024 : 512;
-  while (bt > 256 && (budget - fixed) / (W * 8) < bt) bt >>= 1;
-  const int sbmax = (budget - fixed) / (W * 8);
+  int sbmax = (budget - fixed) / (W * 8);
+  if (sbmax < 64) sbmax = (220 * 1024 - fixed) / (W * 8);  // fall back to one CTA per SM
   if (sbmax < 32) return assemble_values(P, node, k, f_kind, f_arg, val, b, FEM_DETERMINISTIC, s);
-  a.SB = sbmax < B.max_e ? (sbmax / 32) * 32 : B.max_e;
+  if (sbmax >= B.max_e) {
+    a.SB = B.max_e;
+  } else {  // equal sub-batches for the largest block
+    const int nsb = (B.max_e + sbmax - 1) / sbmax;
+    a.SB = (B.max_e + nsb - 1) / nsb;
+  }
   if (a.SB < 1) a.SB = 1;
   a.ev_bytes = ((a.SB * W * 8) + 15) / 16 * 16;
   const int smem = fixed + a.ev_bytes;
-#define FEM_BLK_LAUNCH(DD, TT)                                                                                \
-  do {                                                                                                        \
-    FEM_CUDA(cudaFuncSetAttribute(k_blocked_df<DD, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));   \
-    FEM_LAUNCH((k_blocked_df<DD, TT>), B.nblocks, TT, smem, s, a, node, k, f_kind, f_arg, val, b, err);        \
+  const int bt = 512;
+#define FEM_BLK_LAUNCH(DD, TT, MB)                                                                                \
+  do {                                                                                                            \
+    FEM_CUDA(cudaFuncSetAttribute(k_blocked_df<DD, TT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));   \
+    FEM_LAUNCH((k_blocked_df<DD, TT, MB>), B.nblocks, TT, smem, s, a, node, k, f_kind, f_arg, val, b, err);        \
   } while (0)
-  if (D == 2) {
-    if (bt == 1024) FEM_BLK_LAUNCH(2, 1024);
-    else if (bt == 512) FEM_BLK_LAUNCH(2, 512);
-    else FEM_BLK_LAUNCH(2, 256);
-  } else {
-    if (bt == 512) FEM_BLK_LAUNCH(3, 512);
-    else FEM_BLK_LAUNCH(3, 256);
-  }
+  (void)bt;
+  if (D == 2) FEM_BLK_LAUNCH(2, 512, 2);
+  else FEM_BLK_LAUNCH(3, 512, 1);
 #undef FEM_BLK_LAUNCH
   return FEM_OK;
 }
