@@ -159,7 +159,8 @@ __global__ void k_records(const int32_t* __restrict__ order, int64_t N, int V, i
                           const int32_t* __restrict__ eoff, const int32_t* __restrict__ elist,
                           const int32_t* __restrict__ voff, const int32_t* __restrict__ vlist,
                           const int32_t* __restrict__ rec_off, uint16_t* __restrict__ own_local,
-                          uint8_t* __restrict__ dpos, uint32_t* __restrict__ rec, int* __restrict__ bad) {
+                          int32_t* __restrict__ rowp, uint16_t* __restrict__ rldp, uint32_t* __restrict__ rec,
+                          int* __restrict__ bad) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
     const int R = order[p];
     const int b = (int)(p / V);
@@ -199,7 +200,8 @@ __global__ void k_records(const int32_t* __restrict__ order, int64_t N, int V, i
       }
       rec[w] = r;
     }
-    dpos[p] = dp;
+    rowp[p] = rp;
+    rldp[p] = (uint16_t)(((row_ptr[R + 1] - rp) & 0xff) | ((int)dp << 8));
   }
 }
 
@@ -222,7 +224,8 @@ void free_block_plan(BlockPlan& B) {
   cudaFree(B.order);
   cudaFree(B.rec_off);
   cudaFree(B.own_local);
-  cudaFree(B.dpos);
+  cudaFree(B.rowp);
+  cudaFree(B.rldp);
   cudaFree(B.eoff);
   cudaFree(B.voff);
   cudaFree(B.elist);
@@ -327,10 +330,11 @@ int build_block_plan(const Pattern* P, const double* node_hint, const int32_t* g
   FEM_LAUNCH(k_sorted_degrees, grid_for(N, 256), 256, 0, s, B.order, P->inc_ptr, N, deg);
   BP_RC(exclusive_scan(deg, B.rec_off, N, nullptr, s));
   BP_TRY(cudaMallocAsync((void**)&B.own_local, sizeof(uint16_t) * N, s));
-  BP_TRY(cudaMallocAsync((void**)&B.dpos, sizeof(uint8_t) * N, s));
+  BP_TRY(cudaMallocAsync((void**)&B.rowp, sizeof(int32_t) * N, s));
+  BP_TRY(cudaMallocAsync((void**)&B.rldp, sizeof(uint16_t) * N, s));
   BP_TRY(cudaMallocAsync((void**)&B.rec, sizeof(uint32_t) * total, s));
   FEM_LAUNCH(k_records, grid_for(N, 256), 256, 0, s, B.order, N, V, d1, NT, P->inc_ptr, P->inc, P->row_ptr, P->slot,
-             B.eoff, B.elist, B.voff, B.vlist, B.rec_off, B.own_local, B.dpos, B.rec, dev_int);
+             B.eoff, B.elist, B.voff, B.vlist, B.rec_off, B.own_local, B.rowp, B.rldp, B.rec, dev_int);
   FEM_LAUNCH(k_block_maxima, grid_for(B.nblocks, 256), 256, 0, s, B.eoff, B.voff, B.order, P->row_ptr, N, V, B.nblocks,
              dev_int + 1);
   int hs[4] = {0, 0, 0, 0};

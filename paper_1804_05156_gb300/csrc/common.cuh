@@ -73,7 +73,8 @@ struct BlockPlan {
   int32_t* order = nullptr;               // [N] vertices in locality order; block b owns [b*V, b*V+V)
   int32_t* rec_off = nullptr;             // [N+1] record offsets of the owned rows, locality order
   uint16_t* own_local = nullptr;          // [N] local vertex id of each owned row in its block
-  uint8_t* dpos = nullptr;                // [N] in-row position of each owned row's diagonal
+  int32_t* rowp = nullptr;                // [N] row_ptr of each owned row, locality order
+  uint16_t* rldp = nullptr;               // [N] row length | in-row position of the diagonal << 8
   int32_t* eoff = nullptr;                // [nblocks+1] element-list offsets
   int32_t* voff = nullptr;                // [nblocks+1] vertex-list offsets
   int32_t* elist = nullptr;               // [E] caller element ids, ascending within a block

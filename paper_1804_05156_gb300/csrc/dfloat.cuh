@@ -229,8 +229,7 @@ __device__ __forceinline__ df2 df_sinpi(df2 x, const float4* __restrict__ tab) {
   r = fast_two_sum(__fsub_rn(r.h, n2), r.l);
   df2 s, c;
   df_sincospi_small(r, tab, s, c);
-  const float odd = fmodf(fabsf(n) + fabsf(n2), 2.0f);
-  return odd == 1.0f ? df_neg(s) : s;
+  return ((__float2int_rn(n) + __float2int_rn(n2)) & 1) ? df_neg(s) : s;
 }
 
 }  // namespace fem

@@ -43,7 +43,7 @@ __device__ __forceinline__ SC sincospi_half(const f3& x, const float4* __restric
   const df2 r = fast_two_sum(r0.h, __fadd_rn(r0.l, ch));
   SC o;
   df_sincospi_small(r, tab, o.s, o.c);
-  if (fmodf(fabsf(n), 2.0f) == 1.0f) {
+  if (__float2int_rn(n) & 1) {
     o.s = df_neg(o.s);
     o.c = df_neg(o.c);
   }
@@ -55,7 +55,7 @@ __device__ __forceinline__ df2 sin_mid(const SC& u, const SC& v) { return df_add
 
 __device__ __forceinline__ bool element_df2(const VtxDF<2>* const (&V)[3], const SC* const (&S)[3], df2 kt, bool want_a,
                                             bool want_b, int f_kind, df2 fconst, const double* __restrict__ f_arg,
-                                            int64_t t, LocalDF<2>& L) {
+                                            int t, LocalDF<2>& L) {
   // side vectors ve_i (side opposite vertex i), each formed from its own endpoints
   df2 e[3][2];
 #pragma unroll
@@ -90,7 +90,7 @@ __device__ __forceinline__ bool element_df2(const VtxDF<2>* const (&V)[3], const
       }
     } else if (f_kind == FEM_F_QPVALUES) {
 #pragma unroll
-      for (int q = 0; q < 3; ++q) f[q] = df_from_double(__ldg(f_arg + t * 3 + q));
+      for (int q = 0; q < 3; ++q) f[q] = df_from_double(__ldg(f_arg + (size_t)t * 3 + q));
     } else {
 #pragma unroll
       for (int q = 0; q < 3; ++q) f[q] = fconst;
@@ -109,7 +109,7 @@ __device__ __forceinline__ void df_cross(const df2 (&u)[3], const df2 (&v)[3], d
 }
 
 __device__ __forceinline__ bool element_df3(const VtxDF<3>* const (&V)[4], df2 kt, bool want_a, bool want_b,
-                                            int f_kind, df2 fconst, const double* __restrict__ f_arg, int64_t t,
+                                            int f_kind, df2 fconst, const double* __restrict__ f_arg, int t,
                                             const float4* __restrict__ tab, LocalDF<3>& L) {
   df2 e[3][3];  // e[m-1] = x_m - x_0
 #pragma unroll
@@ -164,7 +164,7 @@ __device__ __forceinline__ bool element_df3(const VtxDF<3>* const (&V)[4], df2 k
           y[i] = df_add(ya, fast_two_sum(V[i]->x[m].b, V[i]->x[m].c));
         }
         const df2 sy = df_add(df_add(y[0], y[1]), df_add(y[2], y[3]));
-        const float sgn = (fmodf(fabsf(nn), 2.0f) == 1.0f) ? -1.0f : 1.0f;
+        const float sgn = (__float2int_rn(nn) & 1) ? -1.0f : 1.0f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const df2 xq = df_add(df_mul(be, sy), df_mul(df_sub(al, be), y[q]));
@@ -174,7 +174,7 @@ __device__ __forceinline__ bool element_df3(const VtxDF<3>* const (&V)[4], df2 k
       }
     } else if (f_kind == FEM_F_QPVALUES) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) f[q] = df_from_double(__ldg(f_arg + t * 4 + q));
+      for (int q = 0; q < 4; ++q) f[q] = df_from_double(__ldg(f_arg + (size_t)t * 4 + q));
     } else {
 #pragma unroll
       for (int q = 0; q < 4; ++q) f[q] = fconst;

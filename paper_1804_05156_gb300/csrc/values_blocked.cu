@@ -49,11 +49,12 @@ int ensure_sincos_table() {
 }
 
 struct BlkArgs {
-  int64_t N, NT, E;
+  int N, NT, E;
   int V, SB;
   const int32_t* order;
   const int32_t* rec_off;
-  const uint8_t* dpos;
+  const int32_t* rowp;    // row_ptr of each owned row, locality order
+  const uint16_t* rldp;   // row length | diagonal position << 8, locality order
   const int32_t* eoff;
   const int32_t* voff;
   const int32_t* elist;
@@ -81,22 +82,22 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
   df2* bacc = reinterpret_cast<df2*>(sm + a.xs_bytes + a.sc_bytes + a.ev_bytes + a.acc_bytes);
   RowMeta* meta = reinterpret_cast<RowMeta*>(bacc + a.V);
   uint16_t* ridx = reinterpret_cast<uint16_t*>(meta + a.V);  // owning row of each accumulator entry
-  __shared__ int scan_tmp[BT];
+  __shared__ int warp_tot[BT / 32];
   const float4* tab = g_sincos_tab;
 
   const int blk = blockIdx.x;
   const int e0 = a.eoff[blk], ne = a.eoff[blk + 1] - e0;
   const int v0 = a.voff[blk], nv = a.voff[blk + 1] - v0;
-  const int64_t p0 = (int64_t)blk * a.V;
-  const int nown = (int)((a.N - p0) < a.V ? (a.N - p0) : a.V);
+  const int p0 = blk * a.V;
+  const int nown = (a.N - p0) < a.V ? (a.N - p0) : a.V;
   const int tid = threadIdx.x;
   const bool sinprod2 = (D == 2) && f_kind == FEM_F_SINPROD;
 
   for (int v = tid; v < nv; v += BT) {
-    const int64_t R = a.vlist[v0 + v];
+    const int R = a.vlist[v0 + v];
     VtxDF<D> x;
 #pragma unroll
-    for (int m = 0; m < D; ++m) x.x[m] = split3(__ldg(node + R * D + m));
+    for (int m = 0; m < D; ++m) x.x[m] = split3(__ldg(node + (size_t)R * D + m));
     xs[v] = x;
     if (sinprod2) {
 #pragma unroll
@@ -108,32 +109,44 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
   const int r0 = tid * rpt, r1 = (r0 + rpt < nown) ? r0 + rpt : nown;
   int mysum = 0;
   for (int r = r0; r < r1; ++r) {
-    const int R = a.order[p0 + r];
-    const int rp = a.row_ptr[R];
-    const int rl = a.row_ptr[R + 1] - rp;
+    const int rl_dp = a.rldp[p0 + r];
     meta[r].cur = a.rec_off[p0 + r];
     meta[r].end = a.rec_off[p0 + r + 1];
-    meta[r].rp = rp;
-    meta[r].R = R;
-    meta[r].rl_dp = rl | ((int)a.dpos[p0 + r] << 8);
-    mysum += rl;
+    meta[r].rp = a.rowp[p0 + r];
+    meta[r].R = a.order[p0 + r];
+    meta[r].rl_dp = rl_dp;
+    mysum += rl_dp & 0xff;
   }
-  scan_tmp[tid] = mysum;
+  // block-wide exclusive scan of the row lengths (warp shuffles, then the warp totals)
+  const int lane = tid & 31, wid = tid >> 5;
+  int inc = mysum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) warp_tot[wid] = inc;
   __syncthreads();
-  for (int o = 1; o < BT; o <<= 1) {
-    const int v = (tid >= o) ? scan_tmp[tid - o] : 0;
-    __syncthreads();
-    scan_tmp[tid] += v;
-    __syncthreads();
+  if (wid == 0) {
+    int w = (lane < BT / 32) ? warp_tot[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += v;
+    }
+    if (lane < BT / 32) warp_tot[lane] = wi - w;
   }
-  int off = scan_tmp[tid] - mysum;
-  const int total_acc = scan_tmp[BT - 1];
+  __syncthreads();
+  int off = warp_tot[wid] + inc - mysum;
   for (int r = r0; r < r1; ++r) {
     meta[r].off = off;
     const int rl = meta[r].rl_dp & 0xff;
     for (int q = 0; q < rl; ++q) ridx[off + q] = (uint16_t)r;
     off += rl;
   }
+  __syncthreads();
+  const int total_acc = meta[nown - 1].off + (meta[nown - 1].rl_dp & 0xff);
   for (int q = tid; q < total_acc; q += BT) acc[q] = df2{0.0f, 0.0f};
   for (int r = tid; r < nown; r += BT) bacc[r] = df2{0.0f, 0.0f};
   __syncthreads();
@@ -143,12 +156,12 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
   for (int sb = 0; sb < ne; sb += a.SB) {
     const int nb = (ne - sb < a.SB) ? ne - sb : a.SB;
     for (int e = tid; e < nb; e += BT) {
-      const int64_t idx = e0 + sb + e;
-      const int64_t t = a.elist[idx];
+      const int idx = e0 + sb + e;
+      const int t = a.elist[idx];
       int lv[D1];
 #pragma unroll
-      for (int i = 0; i < D1; ++i) lv[i] = a.lelem[(int64_t)i * a.E + idx];
-      const df2 kt = k ? df_from_double(__ldg(k + t)) : df2{1.0f, 0.0f};
+      for (int i = 0; i < D1; ++i) lv[i] = a.lelem[i * a.E + idx];
+      const df2 kt = (k && want_a) ? df_from_double(__ldg(k + t)) : df2{1.0f, 0.0f};
       LocalDF<D> L;
       bool ok;
       if constexpr (D == 2) {
@@ -160,7 +173,7 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
         ok = element_df3(V, kt, want_a, want_b, f_kind, fconst, f_arg, t, tab, L);
       }
       if (!ok) report(err, FEM_ERR_DEGENERATE);
-      df2* dst = ev + (int64_t)e * W;
+      df2* dst = ev + e * W;
       if (want_a) {
 #pragma unroll
         for (int c = 0; c < U; ++c) dst[c] = L.a[c];
@@ -181,7 +194,7 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
         const uint32_t rc = a.rec[c];
         const int e = (int)(rc & 0x7fff);
         if (e >= sb_end) break;
-        const df2* src = ev + (int64_t)(e - sb) * W;
+        const df2* src = ev + (e - sb) * W;
         const int i = (rc >> 15) & 3;
         if (want_a) {
           acc[m.off + dp] = df_acc(acc[m.off + dp], src[pidx_rt<D>(i, i)]);
@@ -228,13 +241,14 @@ int assemble_blocked(const Pattern* P, const double* node, const double* k, int 
   }
   const int D = P->d, D1 = D + 1, W = D1 * (D1 + 1) / 2 + D1;
   BlkArgs a;
-  a.N = P->N;
-  a.NT = P->NT;
-  a.E = B.E;
+  a.N = (int)P->N;
+  a.NT = (int)P->NT;
+  a.E = (int)B.E;
   a.V = B.V;
   a.order = B.order;
   a.rec_off = B.rec_off;
-  a.dpos = B.dpos;
+  a.rowp = B.rowp;
+  a.rldp = B.rldp;
   a.eoff = B.eoff;
   a.voff = B.voff;
   a.elist = B.elist;
