@@ -206,8 +206,9 @@ __global__ void k_records(const int32_t* __restrict__ order, int64_t N, int V, i
 }
 
 __global__ void k_block_maxima(const int32_t* __restrict__ eoff, const int32_t* __restrict__ voff,
-                               const int32_t* __restrict__ order, const int32_t* __restrict__ row_ptr, int64_t N, int V,
-                               int nblocks, int* __restrict__ mx) {
+                               const int32_t* __restrict__ order, const int32_t* __restrict__ row_ptr,
+                               const int32_t* __restrict__ rec_off, int64_t N, int V, int nblocks,
+                               int* __restrict__ mx) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblocks; b += gridDim.x * blockDim.x) {
     atomicMax(mx + 0, eoff[b + 1] - eoff[b]);
     atomicMax(mx + 1, voff[b + 1] - voff[b]);
@@ -215,6 +216,7 @@ __global__ void k_block_maxima(const int32_t* __restrict__ eoff, const int32_t* 
     const int64_t p1 = ((int64_t)(b + 1) * V < N) ? (int64_t)(b + 1) * V : N;
     for (int64_t p = (int64_t)b * V; p < p1; ++p) s += row_ptr[order[p] + 1] - row_ptr[order[p]];
     atomicMax(mx + 2, s);
+    atomicMax(mx + 3, rec_off[p1] - rec_off[(int64_t)b * V]);
   }
 }
 
@@ -249,7 +251,7 @@ int build_block_plan(const Pattern* P, const double* node_hint, const int32_t* g
   int rc = FEM_OK;
   uint64_t *k1 = nullptr, *k2 = nullptr, *sorted = nullptr, *ek = nullptr, *vk = nullptr;
   int32_t *vblock = nullptr, *deg = nullptr;
-  int* dev_int = nullptr;  // [0] bad flag, [1..3] maxima
+  int* dev_int = nullptr;  // [0] bad flag, [1..4] maxima
   unsigned long long* bbox = nullptr;
   auto cleanup = [&]() {
     cudaFreeAsync(k1, s);
@@ -283,10 +285,10 @@ int build_block_plan(const Pattern* P, const double* node_hint, const int32_t* g
   BP_TRY(cudaMallocAsync((void**)&k1, sizeof(uint64_t) * big, s));
   BP_TRY(cudaMallocAsync((void**)&k2, sizeof(uint64_t) * big, s));
   BP_TRY(cudaMallocAsync((void**)&vblock, sizeof(int32_t) * N, s));
-  BP_TRY(cudaMallocAsync((void**)&dev_int, sizeof(int) * 4, s));
+  BP_TRY(cudaMallocAsync((void**)&dev_int, sizeof(int) * 5, s));
   BP_TRY(cudaMallocAsync((void**)&bbox, sizeof(unsigned long long) * 6, s));
   BP_TRY(cudaMallocAsync((void**)&B.order, sizeof(int32_t) * N, s));
-  BP_TRY(cudaMemsetAsync(dev_int, 0, sizeof(int) * 4, s));
+  BP_TRY(cudaMemsetAsync(dev_int, 0, sizeof(int) * 5, s));
   // 1. locality order of the vertices
   if (node_hint) {
     unsigned long long init[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
@@ -335,9 +337,9 @@ int build_block_plan(const Pattern* P, const double* node_hint, const int32_t* g
   BP_TRY(cudaMallocAsync((void**)&B.rec, sizeof(uint32_t) * total, s));
   FEM_LAUNCH(k_records, grid_for(N, 256), 256, 0, s, B.order, N, V, d1, NT, P->inc_ptr, P->inc, P->row_ptr, P->slot,
              B.eoff, B.elist, B.voff, B.vlist, B.rec_off, B.own_local, B.rowp, B.rldp, B.rec, dev_int);
-  FEM_LAUNCH(k_block_maxima, grid_for(B.nblocks, 256), 256, 0, s, B.eoff, B.voff, B.order, P->row_ptr, N, V, B.nblocks,
-             dev_int + 1);
-  int hs[4] = {0, 0, 0, 0};
+  FEM_LAUNCH(k_block_maxima, grid_for(B.nblocks, 256), 256, 0, s, B.eoff, B.voff, B.order, P->row_ptr, B.rec_off, N,
+             V, B.nblocks, dev_int + 1);
+  int hs[5] = {0, 0, 0, 0, 0};
   BP_TRY(cudaMemcpyAsync(hs, dev_int, sizeof(hs), cudaMemcpyDeviceToHost, s));
   BP_TRY(cudaStreamSynchronize(s));
   B.E = E;
@@ -345,6 +347,7 @@ int build_block_plan(const Pattern* P, const double* node_hint, const int32_t* g
   B.max_e = hs[1];
   B.max_v = hs[2];
   B.max_acc = hs[3];
+  B.max_rec = hs[4];
   B.ok = (hs[0] == 0);
   cleanup();
 #undef BP_TRY
@@ -363,7 +366,8 @@ int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group
     // shared-memory need of the value kernel at the smallest sub-batch
     const int W = (P->d1 * (P->d1 + 1)) / 2 + P->d1;
     // staged vertex: exact coordinate split (12 B per coordinate) + sin/cos pairs (32 B per 2-D vertex)
-    const int need = B.max_v * (P->d * 12 + (P->d == 2 ? 64 : 0)) + B.max_acc * 10 + V * (8 + 24) + 32 * W * 8 + 256;
+    const int need = B.max_v * (P->d * 12 + (P->d == 2 ? 64 : 0)) + B.max_acc * 10 + V * (8 + 24) + 32 * W * 8 +
+                     B.max_rec * 4 + B.max_e * 20 + 256;
     if (B.ok && need <= 220 * 1024) {
       P->blk = B;
       return FEM_OK;

@@ -69,6 +69,7 @@ struct BlockPlan {
   int V = 0, nblocks = 0;
   int64_t E = 0, VT = 0;                  // listed elements / listed vertices over all blocks
   int max_e = 0, max_v = 0, max_acc = 0;  // per-block maxima (shared-memory sizing)
+  int max_rec = 0;                        // most records in one block
   bool ok = false;                        // the packed record limits hold for this mesh
   int32_t* order = nullptr;               // [N] vertices in locality order; block b owns [b*V, b*V+V)
   int32_t* rec_off = nullptr;             // [N+1] record offsets of the owned rows, locality order

@@ -63,6 +63,7 @@ struct BlkArgs {
   const uint32_t* rec;
   const int32_t* row_ptr;
   int xs_bytes, sc_bytes, ev_bytes, acc_bytes;  // shared-memory carve-up
+  int rec_bytes, el_bytes, max_e;                // block records; per-element coefficient, id, local vertices
 };
 
 struct RowMeta {
@@ -81,7 +82,12 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
   df2* acc = reinterpret_cast<df2*>(sm + a.xs_bytes + a.sc_bytes + a.ev_bytes);
   df2* bacc = reinterpret_cast<df2*>(sm + a.xs_bytes + a.sc_bytes + a.ev_bytes + a.acc_bytes);
   RowMeta* meta = reinterpret_cast<RowMeta*>(bacc + a.V);
-  uint16_t* ridx = reinterpret_cast<uint16_t*>(meta + a.V);  // owning row of each accumulator entry
+  unsigned char* tail = reinterpret_cast<unsigned char*>(meta + a.V);
+  uint32_t* srec = reinterpret_cast<uint32_t*>(tail);                            // the block's records
+  double* sk = reinterpret_cast<double*>(tail + a.rec_bytes);                  // k of each listed element
+  int* st = reinterpret_cast<int*>(tail + a.rec_bytes + a.max_e * 8);          // element ids
+  uint16_t* slv = reinterpret_cast<uint16_t*>(tail + a.rec_bytes + a.max_e * 12);  // local vertex ids
+  uint16_t* ridx = reinterpret_cast<uint16_t*>(tail + a.rec_bytes + a.el_bytes);  // row of each acc entry
   __shared__ int warp_tot[BT / 32];
   const float4* tab = g_sincos_tab;
 
@@ -103,6 +109,18 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
 #pragma unroll
       for (int m = 0; m < D; ++m) scs[v * D + m] = sincospi_half(x.x[m], tab);
     }
+  }
+  // the block's records and element data, loaded once, coalesced (their latency overlaps the staging)
+  const int rbase = a.rec_off[p0];
+  const int nrec = a.rec_off[p0 + nown] - rbase;
+  for (int q = tid; q < nrec; q += BT) srec[q] = __ldg(a.rec + rbase + q);
+  const bool want_k = (k != nullptr) && (val != nullptr);
+  for (int e = tid; e < ne; e += BT) {
+    const int t = __ldg(a.elist + e0 + e);
+    st[e] = t;
+#pragma unroll
+    for (int i = 0; i < D1; ++i) slv[e * D1 + i] = __ldg(a.lelem + i * a.E + e0 + e);
+    if (want_k) sk[e] = __ldg(k + t);
   }
   // owned rows: contiguous chunk of rows per thread for the offset scan
   const int rpt = (nown + BT - 1) / BT;
@@ -156,12 +174,12 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
   for (int sb = 0; sb < ne; sb += a.SB) {
     const int nb = (ne - sb < a.SB) ? ne - sb : a.SB;
     for (int e = tid; e < nb; e += BT) {
-      const int idx = e0 + sb + e;
-      const int t = a.elist[idx];
+      const int el = sb + e;
+      const int t = st[el];
       int lv[D1];
 #pragma unroll
-      for (int i = 0; i < D1; ++i) lv[i] = a.lelem[i * a.E + idx];
-      const df2 kt = (k && want_a) ? df_from_double(__ldg(k + t)) : df2{1.0f, 0.0f};
+      for (int i = 0; i < D1; ++i) lv[i] = slv[el * D1 + i];
+      const df2 kt = want_k ? df_from_double(sk[el]) : df2{1.0f, 0.0f};
       LocalDF<D> L;
       bool ok;
       if constexpr (D == 2) {
@@ -191,7 +209,7 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
       df2 ba = bacc[r];
       int c = m.cur;
       for (; c < m.end; ++c) {
-        const uint32_t rc = a.rec[c];
+        const uint32_t rc = srec[c - rbase];
         const int e = (int)(rc & 0x7fff);
         if (e >= sb_end) break;
         const df2* src = ev + (e - sb) * W;
@@ -262,8 +280,11 @@ int assemble_blocked(const Pattern* P, const double* node, const double* k, int 
   a.xs_bytes = ((B.max_v * D * (int)sizeof(f3)) + 15) / 16 * 16;
   a.sc_bytes = (D == 2 && f_kind == FEM_F_SINPROD) ? ((B.max_v * D * (int)sizeof(SC)) + 15) / 16 * 16 : 0;
   a.acc_bytes = ((B.max_acc * 8) + 15) / 16 * 16;
-  const int fixed = a.xs_bytes + a.sc_bytes + a.acc_bytes + B.V * 8 + B.V * (int)sizeof(RowMeta) +
-                    ((B.max_acc * 2 + 15) / 16) * 16;
+  a.rec_bytes = ((B.max_rec * 4) + 15) / 16 * 16;
+  a.max_e = B.max_e;
+  a.el_bytes = ((B.max_e * 20) + 15) / 16 * 16;  // 8 B k + 4 B id + up to 4 x 2 B local vertices
+  const int fixed = a.xs_bytes + a.sc_bytes + a.acc_bytes + B.V * 8 + B.V * (int)sizeof(RowMeta) + a.rec_bytes +
+                    a.el_bytes + ((B.max_acc * 2 + 15) / 16) * 16;
   int sbmax = (budget - fixed) / (W * 8);
   if (sbmax < 64) sbmax = (220 * 1024 - fixed) / (W * 8);  // fall back to one CTA per SM
   if (sbmax < 32) return assemble_values(P, node, k, f_kind, f_arg, val, b, FEM_DETERMINISTIC, s);
