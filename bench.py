@@ -274,6 +274,7 @@ def run_ours(args):
                       "variant": args.variant, "l2": "flushed by a 512 MB write between steps (outside timing)",
                       "parallelism": "independent mesh per rank" if ws > 1 else "single GPU"},
            "wall_s_timed_region": wall, "pattern_build_ms": pattern_ms,
+           "launch_shape": fa.fem_pattern_launch_shape(p),
            "roofline": roof,
            "e2e": {"value": ws * NT / (e2e_ms * 1e-3) / 1e6, "unit": "Melem/s", "ms_per_step": e2e_ms,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

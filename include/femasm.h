@@ -69,10 +69,18 @@ int fem_mesh_build_pattern(int d, int64_t N, int64_t NT, const int32_t* elem, fe
  * elements on block boundaries are computed once per block they touch. This call rebuilds the plan
  * from a geometric order instead: a Morton code of the coordinates `node` [N][d] (device), grouped
  * first by group [N] (device int32, nullable; for example the mesh id in a batch). Compact blocks
- * mean fewer boundary elements. The coordinates only choose the order: any values give the same
- * results, and later calls may pass different coordinates. Synchronises `stream`. Meshes whose rows
- * exceed 32 entries keep the two-pass deterministic path. */
+ * mean fewer boundary elements. It also tunes the launch (see fem_pattern_launch_shape). The
+ * coordinates only choose the order and the timing workload: any values give the same results,
+ * and later calls may pass different coordinates. Synchronises `stream`. Meshes whose rows exceed
+ * 32 entries keep the two-pass deterministic path. */
 int fem_pattern_set_locality(fem_pattern_t p, const double* node, const int32_t* group, fem_stream_t stream);
+/* The tuned launch of the deterministic value kernel. fem_pattern_set_locality times every feasible
+ * combination of rows per block (128, 256, 512) and launch shape (threads per CTA x CTAs per SM) on
+ * the device, assembling with `node` as the geometry (k = 1; 2-D sine-product load, 3-D constant
+ * load), and keeps the fastest. Outputs (host, nullable): rows per block, threads per CTA, CTAs per
+ * SM, and the tuner's time in ms for the chosen shape (0 when the plan was not tuned). All are 0 when
+ * the mesh uses the two-pass path. */
+int fem_pattern_launch_shape(fem_pattern_t p, int* rows_per_block, int* threads, int* ctas_per_sm, float* tuned_ms);
 
 /* Sizes and library-owned device arrays of a pattern (valid until fem_pattern_destroy):
  * row_ptr [N+1], col_idx [nnz], slot [(d+1)^2 * NT] (layout above). Any output pointer may be NULL. */

@@ -49,6 +49,7 @@ def lib():
             "fem_mesh_build_pattern": (I32, [I32, I64, I64, P, P, P]),
             "fem_pattern_info": (I32, [P, P, P, P, P, P, P, P]),
             "fem_pattern_set_locality": (I32, [P, P, P, P]),
+            "fem_pattern_launch_shape": (I32, [P, P, P, P, P]),
             "fem_pattern_destroy": (None, [P]),
             "fem_assemble": (I32, [P, P, P, I32, P, P, P, I32, P]),
             "fem_assemble_stiffness": (I32, [P, P, P, P, I32, P]),
@@ -172,6 +173,12 @@ class Pattern:
 
 def fem_pattern_set_locality(p: Pattern, node, group=None, stream=None):
     _check(lib().fem_pattern_set_locality(p.handle, _ptr(node), _ptr(group), _stream(stream)))
+
+
+def fem_pattern_launch_shape(p: Pattern) -> dict:
+    v, t, c, ms = C.c_int(), C.c_int(), C.c_int(), C.c_float()
+    _check(lib().fem_pattern_launch_shape(p.handle, C.byref(v), C.byref(t), C.byref(c), C.byref(ms)))
+    return {"rows_per_block": v.value, "threads": t.value, "ctas_per_sm": c.value, "tuned_ms": ms.value}
 
 
 def fem_mesh_build_pattern(elem: torch.Tensor, N: int, stream=None) -> Pattern:

@@ -173,6 +173,16 @@ int fem_pattern_set_locality(fem_pattern_t p, const double* node, const int32_t*
   return fem::rebuild_block_plan(&p->P, node, group, (cudaStream_t)stream);
 }
 
+int fem_pattern_launch_shape(fem_pattern_t p, int* rows_per_block, int* threads, int* ctas_per_sm, float* tuned_ms) {
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  const fem::BlockPlan& B = p->P.blk;
+  if (rows_per_block) *rows_per_block = B.ok ? B.V : 0;
+  if (threads) *threads = B.ok ? B.threads : 0;
+  if (ctas_per_sm) *ctas_per_sm = B.ok ? B.minb : 0;
+  if (tuned_ms) *tuned_ms = B.tuned_ms;
+  return FEM_OK;
+}
+
 int fem_pattern_info(fem_pattern_t p, int* d, int64_t* N, int64_t* NT, int64_t* nnz, const int32_t** row_ptr,
                      const int32_t** col_idx, const int32_t** slot) {
   if (!p) return set_error(FEM_ERR_ARG, "null pattern");

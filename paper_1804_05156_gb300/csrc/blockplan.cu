@@ -356,25 +356,95 @@ int build_block_plan(const Pattern* P, const double* node_hint, const int32_t* g
   return FEM_OK;
 }
 
+// Launch shapes (threads per CTA, CTAs per SM) the value kernel is compiled for.
+static const int kShapes2[][2] = {{512, 2}, {256, 4}, {256, 2}};
+static const int kShapes3[][2] = {{512, 1}, {256, 2}, {256, 1}};
+
 int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group, cudaStream_t s) {
   free_block_plan(P->blk);
-  int V = (P->d == 2) ? 256 : 512;
-  for (; V >= 32; V >>= 1) {
-    BlockPlan B;
-    int rc = build_block_plan(P, node_hint, group, V, &B, s);
-    if (rc) return rc;
-    // shared-memory need of the value kernel at the smallest sub-batch
-    const int W = (P->d1 * (P->d1 + 1)) / 2 + P->d1;
-    // staged vertex: exact coordinate split (12 B per coordinate) + sin/cos pairs (32 B per 2-D vertex)
-    const int need = B.max_v * (P->d * 12 + (P->d == 2 ? 64 : 0)) + B.max_acc * 10 + V * (8 + 24) + 32 * W * 8 +
-                     B.max_rec * 4 + B.max_e * 20 + 256;
-    if (B.ok && need <= 220 * 1024) {
-      P->blk = B;
-      return FEM_OK;
+  const int d = P->d;
+  const bool sinprod = (d == 2);  // the tuning workload: the 2-D sine-product load, 3-D constant load
+  // Without coordinates there is nothing to time: take the first feasible block size, default shape.
+  if (!node_hint) {
+    for (int V = (d == 2) ? 256 : 512; V >= 32; V >>= 1) {
+      BlockPlan B;
+      int rc = build_block_plan(P, nullptr, group, V, &B, s);
+      if (rc) return rc;
+      B.threads = (d == 2) ? 512 : 512;
+      B.minb = (d == 2) ? 2 : 1;
+      while (B.minb > 1 && blocked_smem_need(B, d, sinprod) > blocked_smem_budget(B.minb)) B.minb >>= 1;
+      if (B.ok && blocked_smem_need(B, d, sinprod) <= blocked_smem_budget(B.minb)) {
+        P->blk = B;
+        return FEM_OK;
+      }
+      free_block_plan(B);
     }
-    free_block_plan(B);
+    return FEM_OK;
   }
-  return FEM_OK;  // no feasible block size: the two-pass path serves this mesh
+  // With coordinates: time every feasible (block size, launch shape) on the device, keep the fastest.
+  // The timing runs may report degenerate elements (the coordinates are only an ordering hint), so
+  // the device error word is saved first and restored afterwards.
+  int* errw = device_error_word();
+  if (!errw) return set_error(FEM_ERR_OOM, "cannot allocate the device error word");
+  int saved_err = 0;
+  FEM_CUDA(cudaMemcpyAsync(&saved_err, errw, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FEM_CUDA(cudaStreamSynchronize(s));
+  double *val = nullptr, *bb = nullptr;
+  FEM_CUDA(cudaMallocAsync((void**)&val, sizeof(double) * (P->nnz > 0 ? P->nnz : 1), s));
+  FEM_CUDA(cudaMallocAsync((void**)&bb, sizeof(double) * (P->N > 0 ? P->N : 1), s));
+  cudaEvent_t e0, e1;
+  FEM_CUDA(cudaEventCreate(&e0));
+  FEM_CUDA(cudaEventCreate(&e1));
+  BlockPlan best;
+  float best_ms = 1e30f;
+  const int Vs[] = {512, 256, 128};
+  const int (*shapes)[2] = (d == 2) ? kShapes2 : kShapes3;
+  const int nshapes = 3;
+  int rc = FEM_OK;
+  for (int vi = 0; vi < 3 && rc == FEM_OK; ++vi) {
+    BlockPlan B;
+    rc = build_block_plan(P, node_hint, group, Vs[vi], &B, s);
+    if (rc) break;
+    bool kept = false;
+    for (int si = 0; si < nshapes && B.ok; ++si) {
+      B.threads = shapes[si][0];
+      B.minb = shapes[si][1];
+      if (blocked_smem_need(B, d, sinprod) > blocked_smem_budget(B.minb)) continue;
+      Pattern Q = *P;  // same pattern, candidate plan
+      Q.blk = B;
+      const int fk = sinprod ? FEM_F_SINPROD : FEM_F_CONST;
+      rc = assemble_blocked(&Q, node_hint, nullptr, fk, nullptr, val, bb, s);  // warm-up
+      if (rc) break;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 3 && rc == FEM_OK; ++r) rc = assemble_blocked(&Q, node_hint, nullptr, fk, nullptr, val, bb, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = cuda_error(cudaGetLastError(), "tuning run");
+      if (rc) break;
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= 3.0f;
+      if (ms < best_ms) {
+        if (best.order && !kept) free_block_plan(best);
+        best_ms = ms;
+        best = B;
+        best.tuned_ms = ms;
+        kept = true;
+      }
+    }
+    if (!kept) free_block_plan(B);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(val, s);
+  cudaFreeAsync(bb, s);
+  cudaMemcpyAsync(errw, &saved_err, sizeof(int), cudaMemcpyHostToDevice, s);
+  cudaStreamSynchronize(s);
+  if (rc) {
+    if (best.order) free_block_plan(best);
+    return rc;
+  }
+  if (best.order) P->blk = best;
+  return FEM_OK;
 }
 
 }  // namespace fem

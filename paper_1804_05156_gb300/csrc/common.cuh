@@ -70,6 +70,8 @@ struct BlockPlan {
   int64_t E = 0, VT = 0;                  // listed elements / listed vertices over all blocks
   int max_e = 0, max_v = 0, max_acc = 0;  // per-block maxima (shared-memory sizing)
   int max_rec = 0;                        // most records in one block
+  int threads = 512, minb = 1;            // launch shape: threads per CTA, CTAs per SM
+  float tuned_ms = 0.0f;                  // the tuner's time for the chosen shape (0 if not tuned)
   bool ok = false;                        // the packed record limits hold for this mesh
   int32_t* order = nullptr;               // [N] vertices in locality order; block b owns [b*V, b*V+V)
   int32_t* rec_off = nullptr;             // [N+1] record offsets of the owned rows, locality order
@@ -104,6 +106,8 @@ struct Pattern {
 };
 // (Re)build P->blk, halving the block size until the packed limits hold (blk.ok false if they never do).
 int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group, cudaStream_t s);
+int blocked_smem_budget(int ctas_per_sm);
+int blocked_smem_need(const BlockPlan& B, int d, bool sinprod);
 int assemble_blocked(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg,
                      double* val, double* b, cudaStream_t s);
 

@@ -245,6 +245,18 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
 
 }  // namespace
 
+int blocked_smem_budget(int ctas_per_sm) {
+  // 228 KB of shared memory per SM, 1 KB of it reserved per resident CTA
+  const int per = (228 * 1024) / ctas_per_sm - 1024 - 2048;
+  return per < 220 * 1024 ? per : 220 * 1024;
+}
+
+int blocked_smem_need(const BlockPlan& B, int d, bool sinprod) {
+  const int W = (d + 1) * (d + 2) / 2 + d + 1;
+  return B.max_v * d * 12 + (sinprod && d == 2 ? B.max_v * d * 16 : 0) + B.max_acc * 10 + B.V * (8 + 24) +
+         B.max_rec * 4 + B.max_e * 20 + 32 * W * 8 + 256;
+}
+
 int assemble_blocked(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg,
                      double* val, double* b, cudaStream_t s) {
   int* err = device_error_word();
@@ -274,9 +286,8 @@ int assemble_blocked(const Pattern* P, const double* node, const double* k, int 
   a.vlist = B.vlist;
   a.rec = B.rec;
   a.row_ptr = P->row_ptr;
-  // 2-D: 512 threads and at most ~110 KB of shared memory, so two CTAs share an SM and hide each
-  // other's barrier waits; 3-D: one 512-thread CTA with up to 220 KB.
-  const int budget = (D == 2) ? 110 * 1024 : 220 * 1024;
+  // Shared memory per CTA: what the plan's launch shape (threads x CTAs per SM) leaves per CTA.
+  const int budget = blocked_smem_budget(B.minb);
   a.xs_bytes = ((B.max_v * D * (int)sizeof(f3)) + 15) / 16 * 16;
   a.sc_bytes = (D == 2 && f_kind == FEM_F_SINPROD) ? ((B.max_v * D * (int)sizeof(SC)) + 15) / 16 * 16 : 0;
   a.acc_bytes = ((B.max_acc * 8) + 15) / 16 * 16;
@@ -285,8 +296,7 @@ int assemble_blocked(const Pattern* P, const double* node, const double* k, int 
   a.el_bytes = ((B.max_e * 20) + 15) / 16 * 16;  // 8 B k + 4 B id + up to 4 x 2 B local vertices
   const int fixed = a.xs_bytes + a.sc_bytes + a.acc_bytes + B.V * 8 + B.V * (int)sizeof(RowMeta) + a.rec_bytes +
                     a.el_bytes + ((B.max_acc * 2 + 15) / 16) * 16;
-  int sbmax = (budget - fixed) / (W * 8);
-  if (sbmax < 64) sbmax = (220 * 1024 - fixed) / (W * 8);  // fall back to one CTA per SM
+  const int sbmax = (budget - fixed) / (W * 8);
   if (sbmax < 32) return assemble_values(P, node, k, f_kind, f_arg, val, b, FEM_DETERMINISTIC, s);
   if (sbmax >= B.max_e) {
     a.SB = B.max_e;
@@ -297,15 +307,21 @@ int assemble_blocked(const Pattern* P, const double* node, const double* k, int 
   if (a.SB < 1) a.SB = 1;
   a.ev_bytes = ((a.SB * W * 8) + 15) / 16 * 16;
   const int smem = fixed + a.ev_bytes;
-  const int bt = 512;
 #define FEM_BLK_LAUNCH(DD, TT, MB)                                                                                \
   do {                                                                                                            \
     FEM_CUDA(cudaFuncSetAttribute(k_blocked_df<DD, TT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));   \
     FEM_LAUNCH((k_blocked_df<DD, TT, MB>), B.nblocks, TT, smem, s, a, node, k, f_kind, f_arg, val, b, err);        \
   } while (0)
-  (void)bt;
-  if (D == 2) FEM_BLK_LAUNCH(2, 512, 2);
-  else FEM_BLK_LAUNCH(3, 512, 1);
+  const int shape = B.threads * 16 + B.minb;
+  if (D == 2) {
+    if (shape == 256 * 16 + 4) FEM_BLK_LAUNCH(2, 256, 4);
+    else if (shape == 256 * 16 + 2) FEM_BLK_LAUNCH(2, 256, 2);
+    else FEM_BLK_LAUNCH(2, 512, 2);
+  } else {
+    if (shape == 256 * 16 + 2) FEM_BLK_LAUNCH(3, 256, 2);
+    else if (shape == 256 * 16 + 1) FEM_BLK_LAUNCH(3, 256, 1);
+    else FEM_BLK_LAUNCH(3, 512, 1);
+  }
 #undef FEM_BLK_LAUNCH
   return FEM_OK;
 }
