@@ -10,7 +10,7 @@
 // Rounded intrinsics (__fadd_rn, __fmul_rn) keep the compiler from contracting them into FMAs.
 //
 // Doubles enter through an exact split into three floats done with integer operations only (see
-// split3), and leave through an integer reassembly of hi + lo into IEEE double bits (df_to_double).
+// split3), and leave as one correctly rounded FP64 add of the two parts (df_to_double).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -140,53 +140,25 @@ __device__ __forceinline__ df2 f3_diff(const f3& xj, const f3& xi) {
 
 // ---- doubles out ----------------------------------------------------------------------------------
 
-// hi + lo rounded to a double (error <= 1 ulp), with 32-bit integer operations and one float->int32
-// conversion; no FP64 instruction.
-__device__ __forceinline__ double df_to_double(df2 v) {
-  v = fast_two_sum(v.h, v.l);
-  const uint32_t hb = __float_as_uint(v.h);
-  const int eh = (int)((hb >> 23) & 0xff);
-  if (eh == 0 || eh == 255) {  // zero, float subnormal or non-finite hi: hi alone decides
-    if (eh == 255) {
-      const uint32_t m = hb & 0x7fffffu;
-      return __hiloint2double((int)((hb & 0x80000000u) | 0x7ff00000u | (m ? 0x80000u : 0u)), 0);
-    }
-    // subnormal or zero float: exact as a double through the bits
-    if ((hb & 0x7fffffffu) == 0) return __hiloint2double((int)(hb & 0x80000000u), 0);
-    const uint32_t m = hb & 0x7fffffu;
-    const int lz = __clz(m) - 8;                       // shift to bring the leading 1 to bit 23
-    const uint32_t mm = (m << lz) & 0x7fffffu;
-    const int E = 1023 - 126 - lz;
-    return __hiloint2double((int)((hb & 0x80000000u) | ((uint32_t)E << 20) | (mm >> 3)), (int)(mm << 29));
-  }
-  // mantissa of hi as a 53-bit integer: (1.m23) << 29; unit = 2^(eh - 127 - 52)
-  uint32_t mhi = ((hb & 0x7fffffu) | 0x800000u) >> 3;  // top 21 bits -> bits 0..20 of the high word
-  uint32_t mlo = (hb & 7u) << 29;
-  // lo in the same units: |lo| <= 2^-24 |hi| -> |L| < 2^29
-  const int k = 179 - eh;  // lo * 2^k is in those units
-  float lf = v.l;
-  int kk = k;
-  // apply 2^k in two steps so each factor stays a normal float
-  const int k1 = kk / 2, k2 = kk - k1;
-  lf = __fmul_rn(__fmul_rn(lf, pow2f(k1)), pow2f(k2));
-  const int L = __float2int_rn(lf);
-  const bool neg = (hb & 0x80000000u) != 0;
-  // magnitude M = mant(hi) + (neg ? -L : L) as a 64-bit value in two 32-bit words
-  const int Ls = neg ? -L : L;
-  uint64_t M = ((uint64_t)mhi << 32) | mlo;
-  M = (uint64_t)((int64_t)M + (int64_t)Ls);
-  int E = eh - 127 + 1023;
-  if (M >> 53) {  // carried into bit 53: renormalise with round-half-even
-    const uint64_t odd = M & 1u;
-    M = (M >> 1) + (odd & ((M >> 1) & 1u));
-    E += 1;
-  } else if (!(M >> 52)) {  // borrowed below bit 52
-    M <<= 1;
-    E -= 1;
-  }
-  const uint64_t bits = ((uint64_t)(neg ? 1u : 0u) << 63) | ((uint64_t)E << 52) | (M & 0xfffffffffffffull);
-  return __longlong_as_double((long long)bits);
+// The exact double of a float, assembled from its bits with 32-bit integer operations (no conversion
+// instruction). Zero and float subnormals give a signed zero (they only ever appear as the low part
+// of a float-float, below any result's precision); infinities and NaNs keep their class.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint32_t sg = u & 0x80000000u;
+  const uint32_t m = u & 0x7fffffu;
+  uint32_t hi = sg | ((e + 896u) << 20) | (m >> 3);
+  uint32_t lo = m << 29;
+  hi = (e == 0u) ? sg : hi;
+  lo = (e == 0u) ? 0u : lo;
+  hi = (e == 255u) ? (sg | 0x7ff00000u | (m ? 0x80000u : 0u)) : hi;
+  return __hiloint2double((int)hi, (int)lo);
 }
+
+// hi + lo rounded to the nearest double: both parts are exact doubles, so one FP64 add rounds their
+// sum correctly. The FP64 unit is otherwise idle in these kernels.
+__device__ __forceinline__ double df_to_double(df2 v) { return __dadd_rn(f2d_bits(v.h), f2d_bits(v.l)); }
 
 // ---- sin(pi r), cos(pi r) ---------------------------------------------------------------------------
 
