@@ -22,9 +22,18 @@ __host__ __device__ constexpr int pidx(int i, int j) {
                                    : (i < j ? i : j) == 1 ? ((i > j ? i : j) + 1)
                                                           : 5));
 }
+// Same map for run-time (i, j): the (d+1)^2 results packed 4 bits each in one 64-bit constant.
+template <int D>
+__host__ __device__ constexpr uint64_t pidx_table() {
+  uint64_t t = 0;
+  for (int i = 0; i < D + 1; ++i)
+    for (int j = 0; j < D + 1; ++j) t |= (uint64_t)pidx<D>(i, j) << (4 * (i * (D + 1) + j));
+  return t;
+}
 template <int D>
 __device__ __forceinline__ int pidx_rt(int i, int j) {
-  return pidx<D>(i, j);
+  constexpr uint64_t T = pidx_table<D>();
+  return (int)((T >> (4 * (i * (D + 1) + j))) & 15u);
 }
 
 template <int D>

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
   double* sk = reinterpret_cast<double*>(tail + a.rec_bytes);                  // k of each listed element
   int* st = reinterpret_cast<int*>(tail + a.rec_bytes + a.max_e * 8);          // element ids
   uint16_t* slv = reinterpret_cast<uint16_t*>(tail + a.rec_bytes + a.max_e * 12);  // local vertex ids
-  uint16_t* ridx = reinterpret_cast<uint16_t*>(tail + a.rec_bytes + a.el_bytes);  // row of each acc entry
+  int* gidx = reinterpret_cast<int*>(tail + a.rec_bytes + a.el_bytes);  // CSR position of each acc entry
   __shared__ int warp_tot[BT / 32];
   const float4* tab = g_sincos_tab;
 
@@ -160,7 +160,8 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
   for (int r = r0; r < r1; ++r) {
     meta[r].off = off;
     const int rl = meta[r].rl_dp & 0xff;
-    for (int q = 0; q < rl; ++q) ridx[off + q] = (uint16_t)r;
+    const int rp = meta[r].rp;
+    for (int q = 0; q < rl; ++q) gidx[off + q] = rp + q;
     off += rl;
   }
   __syncthreads();
@@ -234,10 +235,7 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
   }
   // write-out: flattened over the block's accumulator entries, coalesced along each row
   if (want_a) {
-    for (int q = tid; q < total_acc; q += BT) {
-      const int r = ridx[q];
-      val[meta[r].rp + (q - meta[r].off)] = df_to_double(acc[q]);
-    }
+    for (int q = tid; q < total_acc; q += BT) val[gidx[q]] = df_to_double(acc[q]);
   }
   if (want_b)
     for (int r = tid; r < nown; r += BT) bvec[meta[r].R] = df_to_double(bacc[r]);
@@ -253,7 +251,7 @@ int blocked_smem_budget(int ctas_per_sm) {
 
 int blocked_smem_need(const BlockPlan& B, int d, bool sinprod) {
   const int W = (d + 1) * (d + 2) / 2 + d + 1;
-  return B.max_v * d * 12 + (sinprod && d == 2 ? B.max_v * d * 16 : 0) + B.max_acc * 10 + B.V * (8 + 24) +
+  return B.max_v * d * 12 + (sinprod && d == 2 ? B.max_v * d * 16 : 0) + B.max_acc * 12 + B.V * (8 + 24) +
          B.max_rec * 4 + B.max_e * 20 + 32 * W * 8 + 256;
 }
 
@@ -295,7 +293,7 @@ int assemble_blocked(const Pattern* P, const double* node, const double* k, int 
   a.max_e = B.max_e;
   a.el_bytes = ((B.max_e * 20) + 15) / 16 * 16;  // 8 B k + 4 B id + up to 4 x 2 B local vertices
   const int fixed = a.xs_bytes + a.sc_bytes + a.acc_bytes + B.V * 8 + B.V * (int)sizeof(RowMeta) + a.rec_bytes +
-                    a.el_bytes + ((B.max_acc * 2 + 15) / 16) * 16;
+                    a.el_bytes + ((B.max_acc * 4 + 15) / 16) * 16;
   const int sbmax = (budget - fixed) / (W * 8);
   if (sbmax < 32) return assemble_values(P, node, k, f_kind, f_arg, val, b, FEM_DETERMINISTIC, s);
   if (sbmax >= B.max_e) {
