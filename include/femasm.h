@@ -75,12 +75,19 @@ int fem_mesh_build_pattern(int d, int64_t N, int64_t NT, const int32_t* elem, fe
  * 32 entries keep the two-pass deterministic path. */
 int fem_pattern_set_locality(fem_pattern_t p, const double* node, const int32_t* group, fem_stream_t stream);
 /* The tuned launch of the deterministic value kernel. fem_pattern_set_locality times every feasible
- * combination of rows per block (128, 256, 512) and launch shape (threads per CTA x CTAs per SM) on
- * the device, assembling with `node` as the geometry (k = 1; 2-D sine-product load, 3-D constant
- * load), and keeps the fastest. Outputs (host, nullable): rows per block, threads per CTA, CTAs per
- * SM, and the tuner's time in ms for the chosen shape (0 when the plan was not tuned). All are 0 when
- * the mesh uses the two-pass path. */
-int fem_pattern_launch_shape(fem_pattern_t p, int* rows_per_block, int* threads, int* ctas_per_sm, float* tuned_ms);
+ * combination of rows per block (128, 256, 512), launch shape (threads per CTA x CTAs per SM) and
+ * launch mode (one CTA per block, or a persistent wave drawing blocks from a device counter) on the
+ * device, assembling with `node` as the geometry (k = 1; 2-D sine-product load, 3-D constant load),
+ * and keeps the fastest. Outputs (host, nullable): rows per block, threads per CTA, CTAs per SM,
+ * persistent (0/1), and the tuner's time in ms for the chosen launch (0 when not tuned). All are 0
+ * when the mesh uses the two-pass path. */
+int fem_pattern_launch_shape(fem_pattern_t p, int* rows_per_block, int* threads, int* ctas_per_sm, int* persistent,
+                             float* tuned_ms);
+/* Override the launch of the deterministic value kernel (the plan's rows per block are kept).
+ * Supported shapes: 2-D 512x2, 256x4, 256x2; 3-D 512x1, 256x2, 256x1 (threads x CTAs per SM);
+ * persistent 0/1. Every launch gives the same bits. FEM_ERR_ARG if the shape is not supported or the
+ * plan does not fit it; FEM_ERR_STATE if the mesh has no blocked plan. */
+int fem_pattern_force_launch(fem_pattern_t p, int threads, int ctas_per_sm, int persistent);
 
 /* Sizes and library-owned device arrays of a pattern (valid until fem_pattern_destroy):
  * row_ptr [N+1], col_idx [nnz], slot [(d+1)^2 * NT] (layout above). Any output pointer may be NULL. */
@@ -146,6 +153,10 @@ int fem_batch_plan(int d, int B, const int64_t* N, const int64_t* NT, const int3
                    fem_stream_t stream);
 int fem_batch_info(fem_batch_t bt, int* B, const int64_t** node_off, const int64_t** elem_off,
                    const int64_t** nnz_off, fem_pattern_t* pattern);
+/* Locality plan and launch tuning for the batch (fem_pattern_set_locality on the block-diagonal
+ * pattern, with the vertices grouped by mesh): node_cat [sum N][d] (device) orders and times the
+ * plan. Synchronises. */
+int fem_batch_set_locality(fem_batch_t bt, const double* node_cat, fem_stream_t stream);
 /* One persistent launch over all meshes' elements (work tiles taken from a device counter), plus
  * the per-slot reduction: node_cat [sum N][d], k_cat [sum NT] (nullable), val_cat [sum nnz],
  * b_cat [sum N] (either output nullable). No allocation and no host synchronisation, so the call

@@ -49,7 +49,8 @@ def lib():
             "fem_mesh_build_pattern": (I32, [I32, I64, I64, P, P, P]),
             "fem_pattern_info": (I32, [P, P, P, P, P, P, P, P]),
             "fem_pattern_set_locality": (I32, [P, P, P, P]),
-            "fem_pattern_launch_shape": (I32, [P, P, P, P, P]),
+            "fem_pattern_launch_shape": (I32, [P, P, P, P, P, P]),
+            "fem_pattern_force_launch": (I32, [P, I32, I32, I32]),
             "fem_pattern_destroy": (None, [P]),
             "fem_assemble": (I32, [P, P, P, I32, P, P, P, I32, P]),
             "fem_assemble_stiffness": (I32, [P, P, P, P, I32, P]),
@@ -59,6 +60,7 @@ def lib():
             "fem_assemble_backward": (I32, [P, P, P, I32, P, P, P, P, P, P]),
             "fem_batch_plan": (I32, [I32, I32, P, P, P, P, P]),
             "fem_batch_info": (I32, [P, P, P, P, P, P]),
+            "fem_batch_set_locality": (I32, [P, P, P]),
             "fem_batch_assemble": (I32, [P, P, P, I32, P, P, P, I32, P]),
             "fem_batch_assemble_graph": (I32, [P, P, P, I32, P, P, P, I32, P]),
             "fem_batch_destroy": (None, [P]),
@@ -176,9 +178,14 @@ def fem_pattern_set_locality(p: Pattern, node, group=None, stream=None):
 
 
 def fem_pattern_launch_shape(p: Pattern) -> dict:
-    v, t, c, ms = C.c_int(), C.c_int(), C.c_int(), C.c_float()
-    _check(lib().fem_pattern_launch_shape(p.handle, C.byref(v), C.byref(t), C.byref(c), C.byref(ms)))
-    return {"rows_per_block": v.value, "threads": t.value, "ctas_per_sm": c.value, "tuned_ms": ms.value}
+    v, t, c, pe, ms = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_float()
+    _check(lib().fem_pattern_launch_shape(p.handle, C.byref(v), C.byref(t), C.byref(c), C.byref(pe), C.byref(ms)))
+    return {"rows_per_block": v.value, "threads": t.value, "ctas_per_sm": c.value, "persistent": bool(pe.value),
+            "tuned_ms": ms.value}
+
+
+def fem_pattern_force_launch(p: Pattern, threads: int, ctas_per_sm: int, persistent: bool):
+    _check(lib().fem_pattern_force_launch(p.handle, threads, ctas_per_sm, 1 if persistent else 0))
 
 
 def fem_mesh_build_pattern(elem: torch.Tensor, N: int, stream=None) -> Pattern:
@@ -240,6 +247,9 @@ class Batch:
         self.nnz_off = [zo[i] for i in range(B + 1)]
         self.pattern = Pattern(None, 0, _handle=ph)
         self.pattern._owned = False  # owned by the batch
+
+    def set_locality(self, node_cat, stream=None):
+        _check(lib().fem_batch_set_locality(self._h, _ptr(node_cat), _stream(stream)))
 
     def assemble(self, node_cat, k_cat, f_kind, f_arg, val_cat, b_cat, variant=FEM_DETERMINISTIC, graph=False,
                  stream=None):

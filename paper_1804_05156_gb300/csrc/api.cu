@@ -105,6 +105,7 @@ void free_pattern(Pattern& P) {
   cudaFree(P.inc_ptr);
   cudaFree(P.inc);
   cudaFree(P.scratch);
+  cudaFree(P.work_counter);
   P = Pattern();
 }
 
@@ -147,6 +148,11 @@ int fem_mesh_build_pattern(int d, int64_t N, int64_t NT, const int32_t* elem, fe
     return set_error(FEM_ERR_OOM, "cannot allocate the device error word");
   }
   int rc = fem::build_pattern(&P, elem, s);
+  if (rc == FEM_OK && cudaMalloc((void**)&P.work_counter, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    P.work_counter = nullptr;
+    rc = set_error(FEM_ERR_OOM, "work counter allocation failed");
+  }
   if (rc == FEM_OK && NT > 0) {
     P.scratch_elems = fem::scratch_per_elem(d) * NT;
     if (cudaMallocAsync((void**)&P.scratch, sizeof(double) * (size_t)P.scratch_elems, s) != cudaSuccess) {
@@ -173,13 +179,31 @@ int fem_pattern_set_locality(fem_pattern_t p, const double* node, const int32_t*
   return fem::rebuild_block_plan(&p->P, node, group, (cudaStream_t)stream);
 }
 
-int fem_pattern_launch_shape(fem_pattern_t p, int* rows_per_block, int* threads, int* ctas_per_sm, float* tuned_ms) {
+int fem_pattern_launch_shape(fem_pattern_t p, int* rows_per_block, int* threads, int* ctas_per_sm, int* persistent,
+                             float* tuned_ms) {
   if (!p) return set_error(FEM_ERR_ARG, "null pattern");
   const fem::BlockPlan& B = p->P.blk;
   if (rows_per_block) *rows_per_block = B.ok ? B.V : 0;
   if (threads) *threads = B.ok ? B.threads : 0;
   if (ctas_per_sm) *ctas_per_sm = B.ok ? B.minb : 0;
   if (tuned_ms) *tuned_ms = B.tuned_ms;
+  if (persistent) *persistent = B.ok && B.persistent ? 1 : 0;
+  return FEM_OK;
+}
+
+int fem_pattern_force_launch(fem_pattern_t p, int threads, int ctas_per_sm, int persistent) {
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  fem::BlockPlan& B = p->P.blk;
+  if (!B.ok) return set_error(FEM_ERR_STATE, "this mesh has no blocked plan");
+  const bool ok2 = (threads == 512 && ctas_per_sm == 2) || (threads == 256 && (ctas_per_sm == 4 || ctas_per_sm == 2));
+  const bool ok3 = (threads == 512 && ctas_per_sm == 1) || (threads == 256 && (ctas_per_sm == 2 || ctas_per_sm == 1));
+  if (!(p->P.d == 2 ? ok2 : ok3)) return set_error(FEM_ERR_ARG, "unsupported launch shape %d x %d", threads, ctas_per_sm);
+  if (fem::blocked_smem_need(B, p->P.d, p->P.d == 2) > fem::blocked_smem_budget(ctas_per_sm))
+    return set_error(FEM_ERR_ARG, "launch shape %d x %d does not fit this plan in shared memory", threads, ctas_per_sm);
+  B.threads = threads;
+  B.minb = ctas_per_sm;
+  B.persistent = persistent != 0;
+  B.tuned_ms = 0.0f;
   return FEM_OK;
 }
 

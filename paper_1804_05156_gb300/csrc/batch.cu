@@ -40,9 +40,51 @@ __global__ void k_offset_elem(const int32_t* __restrict__ in, int32_t* __restric
   }
 }
 
+// group id of every vertex: the mesh it belongs to (binary search over the vertex offsets)
+__global__ void k_vertex_group(const int64_t* __restrict__ node_off, int B, int64_t N, int32_t* __restrict__ group) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (node_off[mid] <= v) lo = mid;
+      else hi = mid - 1;
+    }
+    group[v] = lo;
+  }
+}
+
 }  // namespace
 
 extern "C" {
+
+int fem_batch_set_locality(fem_batch_t bt, const double* node_cat, fem_stream_t stream) {
+  if (!bt) return set_error(FEM_ERR_ARG, "null batch");
+  if (((uintptr_t)node_cat) % 8 != 0) return set_error(FEM_ERR_ARG, "misaligned node_cat");
+  const int64_t N = bt->node_off[bt->B];
+  if (N == 0) return FEM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t* doff = nullptr;
+  int32_t* group = nullptr;
+  if (cudaMallocAsync((void**)&doff, sizeof(int64_t) * (bt->B + 1), s) != cudaSuccess ||
+      cudaMallocAsync((void**)&group, sizeof(int32_t) * N, s) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(FEM_ERR_OOM, "batch locality allocation failed");
+  }
+  cudaMemcpyAsync(doff, bt->node_off.data(), sizeof(int64_t) * (bt->B + 1), cudaMemcpyHostToDevice, s);
+  k_vertex_group<<<fem::grid_for(N, 256), 256, 0, s>>>(doff, bt->B, N, group);
+  fem::g_launches.fetch_add(1);
+  int rc = fem_pattern_set_locality(bt->pat, node_cat, group, stream);
+  cudaStreamSynchronize(s);
+  cudaFree(doff);
+  cudaFree(group);
+  // a re-planned batch invalidates any captured graph
+  if (bt->exec) cudaGraphExecDestroy(bt->exec);
+  if (bt->graph) cudaGraphDestroy(bt->graph);
+  bt->exec = nullptr;
+  bt->graph = nullptr;
+  return rc;
+}
+
 
 int fem_batch_plan(int d, int B, const int64_t* N, const int64_t* NT, const int32_t* elem_cat, fem_batch_t* out,
                    fem_stream_t stream) {

@@ -406,9 +406,10 @@ int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group
     rc = build_block_plan(P, node_hint, group, Vs[vi], &B, s);
     if (rc) break;
     bool kept = false;
-    for (int si = 0; si < nshapes && B.ok; ++si) {
-      B.threads = shapes[si][0];
-      B.minb = shapes[si][1];
+    for (int si = 0; si < 2 * nshapes && B.ok; ++si) {
+      B.threads = shapes[si % nshapes][0];
+      B.minb = shapes[si % nshapes][1];
+      B.persistent = si >= nshapes;
       if (blocked_smem_need(B, d, sinprod) > blocked_smem_budget(B.minb)) continue;
       Pattern Q = *P;  // same pattern, candidate plan
       Q.blk = B;

@@ -71,6 +71,7 @@ struct BlockPlan {
   int max_e = 0, max_v = 0, max_acc = 0;  // per-block maxima (shared-memory sizing)
   int max_rec = 0;                        // most records in one block
   int threads = 512, minb = 1;            // launch shape: threads per CTA, CTAs per SM
+  bool persistent = false;                // one resident wave drawing blocks from a counter
   float tuned_ms = 0.0f;                  // the tuner's time for the chosen shape (0 if not tuned)
   bool ok = false;                        // the packed record limits hold for this mesh
   int32_t* order = nullptr;               // [N] vertices in locality order; block b owns [b*V, b*V+V)
@@ -103,6 +104,7 @@ struct Pattern {
   double* scratch = nullptr;   // per-element values for the deterministic reduction
   int64_t scratch_elems = 0;   // doubles in scratch
   BlockPlan blk;               // owner-computes locality plan (blk.ok == false: two-pass path only)
+  int* work_counter = nullptr; // device counter of the persistent launch
 };
 // (Re)build P->blk, halving the block size until the packed limits hold (blk.ok false if they never do).
 int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group, cudaStream_t s);

@@ -50,7 +50,7 @@ int ensure_sincos_table() {
 
 struct BlkArgs {
   int N, NT, E;
-  int V, SB;
+  int V, SB, nblocks;
   const int32_t* order;
   const int32_t* rec_off;
   const int32_t* rowp;    // row_ptr of each owned row, locality order
@@ -73,7 +73,8 @@ struct RowMeta {
 template <int D, int BT, int MINB>
 __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double* __restrict__ node, const double* __restrict__ k,
                                                    int f_kind, const double* __restrict__ f_arg, double* __restrict__ val,
-                                                   double* __restrict__ bvec, int* __restrict__ err) {
+                                                   double* __restrict__ bvec, int* __restrict__ err,
+                                                   int* __restrict__ work) {
   constexpr int D1 = D + 1, U = D1 * (D1 + 1) / 2, W = U + D1;
   extern __shared__ __align__(16) unsigned char sm[];
   VtxDF<D>* xs = reinterpret_cast<VtxDF<D>*>(sm);
@@ -90,8 +91,19 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
   int* gidx = reinterpret_cast<int*>(tail + a.rec_bytes + a.el_bytes);  // CSR position of each acc entry
   __shared__ int warp_tot[BT / 32];
   const float4* tab = g_sincos_tab;
-
-  const int blk = blockIdx.x;
+  __shared__ int s_blk;
+  // One block per CTA, or (work != nullptr) a persistent CTA that takes blocks from a device counter
+  // until none are left: CTAs that draw small blocks take more of them.
+  for (int it = 0;; ++it) {
+  if (work) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_blk = atomicAdd(work, 1);
+    __syncthreads();
+  } else if (it > 0) {
+    break;
+  }
+  const int blk = work ? s_blk : (int)blockIdx.x;
+  if (blk >= a.nblocks) break;
   const int e0 = a.eoff[blk], ne = a.eoff[blk + 1] - e0;
   const int v0 = a.voff[blk], nv = a.voff[blk + 1] - v0;
   const int p0 = blk * a.V;
@@ -239,6 +251,7 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
   }
   if (want_b)
     for (int r = tid; r < nown; r += BT) bvec[meta[r].R] = df_to_double(bacc[r]);
+  }  // blocks
 }
 
 }  // namespace
@@ -271,6 +284,7 @@ int assemble_blocked(const Pattern* P, const double* node, const double* k, int 
   BlkArgs a;
   a.N = (int)P->N;
   a.NT = (int)P->NT;
+  a.nblocks = B.nblocks;
   a.E = (int)B.E;
   a.V = B.V;
   a.order = B.order;
@@ -305,10 +319,22 @@ int assemble_blocked(const Pattern* P, const double* node, const double* k, int 
   if (a.SB < 1) a.SB = 1;
   a.ev_bytes = ((a.SB * W * 8) + 15) / 16 * 16;
   const int smem = fixed + a.ev_bytes;
+  // persistent launch: one resident wave of CTAs drawing blocks from a counter reset in-stream
+  int* work = nullptr;
+  int grid = B.nblocks;
+  if (B.persistent) {
+    work = P->work_counter;
+    if (!work) return set_error(FEM_ERR_STATE, "pattern has no work counter");
+    FEM_CUDA(cudaMemsetAsync(work, 0, sizeof(int), s));
+    int nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    grid = nsm * B.minb < B.nblocks ? nsm * B.minb : B.nblocks;
+  }
 #define FEM_BLK_LAUNCH(DD, TT, MB)                                                                                \
   do {                                                                                                            \
     FEM_CUDA(cudaFuncSetAttribute(k_blocked_df<DD, TT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));   \
-    FEM_LAUNCH((k_blocked_df<DD, TT, MB>), B.nblocks, TT, smem, s, a, node, k, f_kind, f_arg, val, b, err);        \
+    FEM_LAUNCH((k_blocked_df<DD, TT, MB>), grid, TT, smem, s, a, node, k, f_kind, f_arg, val, b, err, work);        \
   } while (0)
   const int shape = B.threads * 16 + B.minb;
   if (D == 2) {

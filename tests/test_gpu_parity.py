@@ -87,6 +87,30 @@ def test_locality_plan_values_match_oracle(case):
     assert torch.equal(v3, val) and torch.equal(b3, b)
 
 
+@pytest.mark.parametrize("case", ["sq37p", "kuhn5", "delaunay2"])
+def test_every_launch_shape_gives_the_same_bits(case):
+    """Deterministic means independent of the launch: all shapes, one CTA per block or persistent."""
+    d, node, elem, k, f_kind = mesh_case(case)
+    p = fa.Pattern(dev(elem), node.shape[0])
+    fa.fem_pattern_set_locality(p, dev(node))
+    ref = None
+    shapes = [(512, 2), (256, 4), (256, 2)] if d == 2 else [(512, 1), (256, 2), (256, 1)]
+    for thr, cta in shapes:
+        for pers in (False, True):
+            try:
+                fa.fem_pattern_force_launch(p, thr, cta, pers)
+            except fa.FemError as e:
+                assert e.code == fa.FEM_ERR_ARG  # this plan does not fit the shape
+                continue
+            v, b = fa.assemble(p, dev(node), dev(k), f_kind, None, fa.FEM_DETERMINISTIC)
+            if ref is None:
+                ref = (v, b)
+                _, _, vo, so = oracle.assemble(d, node, elem, k)
+                assert_close_scaled(host(v), vo, so)
+            else:
+                assert torch.equal(v, ref[0]) and torch.equal(b, ref[1]), (thr, cta, pers)
+
+
 def test_qp_values_rhs():
     d, node, elem, k, _ = mesh_case("sq37p")
     rng = np.random.default_rng(5)
@@ -250,6 +274,7 @@ def test_batched_matches_per_mesh_oracle():
     node_cat = np.concatenate([m["node"] for m in meshes])
     k_cat = np.concatenate(ks)
     bt = fa.Batch(2, [m["node"].shape[0] for m in meshes], [m["elem"].shape[0] for m in meshes], dev(elem_cat))
+    bt.set_locality(dev(node_cat))
     val = torch.empty(bt.nnz_off[-1], dtype=torch.float64, device="cuda")
     b = torch.empty(bt.node_off[-1], dtype=torch.float64, device="cuda")
     bt.assemble(dev(node_cat), dev(k_cat), fa.FEM_F_SINPROD, None, val, b, fa.FEM_DETERMINISTIC)
