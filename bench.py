@@ -166,6 +166,98 @@ def workload_name(cfg):
             "c3": "3-D unit cube 128^3 Kuhn tets, jittered 0.1h, k~LN(0,1), f=1"}[cfg]
 
 
+def _time_steps(fn, steps, flush, s):
+    """Mean ms of `fn` over `steps` calls, CUDA events on stream s, L2 flushed between calls."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        evs[i][0].record(s)
+        fn()
+        evs[i][1].record(s)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+
+def extras(fa, args, flush, plain_melem):
+    """Secondary rows of the metric: 3-D, atomic variant, Dirichlet, batched (C4), fwd+bwd (C5)."""
+    import torch
+    s = torch.cuda.current_stream()
+    out = {}
+    steps = max(3, min(args.steps, 10))
+    # 3-D 128^3 Kuhn (C3)
+    m = meshgen.make_config("c3")
+    nd, kd = torch.as_tensor(m["node"]).cuda(), torch.as_tensor(m["coef"]).cuda()
+    t0 = time.perf_counter()
+    p = fa.Pattern(torch.as_tensor(m["elem"]).cuda(), m["node"].shape[0])
+    fa.fem_pattern_set_locality(p, nd)
+    torch.cuda.synchronize()
+    pms = 1e3 * (time.perf_counter() - t0)
+    val = torch.empty(p.nnz, dtype=torch.float64, device="cuda")
+    b = torch.empty(p.N, dtype=torch.float64, device="cuda")
+    f = lambda: fa.fem_assemble(p, nd, kd, fa.FEM_F_CONST, None, val, b, fa.FEM_DETERMINISTIC)
+    for _ in range(3):
+        f()
+    ms = _time_steps(f, steps, flush, s)
+    NT = m["elem"].shape[0]
+    out["c3_3d_128cube"] = {"ms": ms, "Melem_s": NT / (ms * 1e-3) / 1e6, "NT": NT, "nnz": p.nnz,
+                            "pattern_build_ms": pms, "launch": fa.fem_pattern_launch_shape(p),
+                            "algorithmic_GBs": algorithmic_bytes(3, p.N, NT, p.nnz) / (ms * 1e-3) / 1e9}
+    del p, val, b, nd, kd, m
+    torch.cuda.empty_cache()
+    # batched: 256 squares, n ~ U{16..512}, one persistent launch replayed from a CUDA graph (C4)
+    c4 = meshgen.make_config("c4")
+    ms_ = c4["meshes"]
+    elem_cat = np.concatenate([x["elem"] for x in ms_])
+    node_cat = torch.as_tensor(np.concatenate([x["node"] for x in ms_])).cuda()
+    k_cat = torch.as_tensor(np.concatenate([x["coef"] for x in ms_])).cuda()
+    t0 = time.perf_counter()
+    bt = fa.Batch(2, [x["node"].shape[0] for x in ms_], [x["elem"].shape[0] for x in ms_],
+                  torch.as_tensor(elem_cat).cuda())
+    bt.set_locality(node_cat)
+    torch.cuda.synchronize()
+    bpms = 1e3 * (time.perf_counter() - t0)
+    val = torch.empty(bt.nnz_off[-1], dtype=torch.float64, device="cuda")
+    b = torch.empty(bt.node_off[-1], dtype=torch.float64, device="cuda")
+    f = lambda: bt.assemble(node_cat, k_cat, fa.FEM_F_SINPROD, None, val, b, fa.FEM_DETERMINISTIC, graph=True)
+    for _ in range(3):
+        f()
+    ms = _time_steps(f, steps, flush, s)
+    NT = elem_cat.shape[0]
+    bm = NT / (ms * 1e-3) / 1e6
+    out["c4_batched_256"] = {"ms": ms, "Melem_s": bm, "NT": NT, "meshes": len(ms_), "nnz": bt.nnz_off[-1],
+                             "plan_ms": bpms, "launch": fa.fem_pattern_launch_shape(bt.pattern),
+                             "graph": True, "vs_plain_fwd": bm / plain_melem}
+    del bt, val, b, node_cat, k_cat, elem_cat, c4, ms_
+    torch.cuda.empty_cache()
+    # differentiable: 64^3 Kuhn, forward then backward of L = w.A + r.b (C5)
+    m = meshgen.make_config("c5")
+    nd, kd = torch.as_tensor(m["node"]).cuda(), torch.as_tensor(m["coef"]).cuda()
+    p = fa.Pattern(torch.as_tensor(m["elem"]).cuda(), m["node"].shape[0])
+    fa.fem_pattern_set_locality(p, nd)
+    w = torch.as_tensor(meshgen.normal(m["loss_seed"], meshgen.TAG_W, p.nnz)).cuda()
+    r = torch.as_tensor(meshgen.normal(m["loss_seed"], meshgen.TAG_R, p.N)).cuda()
+    val = torch.empty(p.nnz, dtype=torch.float64, device="cuda")
+    b = torch.empty(p.N, dtype=torch.float64, device="cuda")
+    gn = torch.empty((p.N, 3), dtype=torch.float64, device="cuda")
+    gk = torch.empty(p.NT, dtype=torch.float64, device="cuda")
+    fwd = lambda: fa.fem_assemble(p, nd, kd, fa.FEM_F_SINPROD, None, val, b, fa.FEM_DETERMINISTIC)
+
+    def fwdbwd():
+        fwd()
+        fa.fem_assemble_backward(p, nd, kd, fa.FEM_F_SINPROD, None, w, r, gn, gk)
+    for _ in range(3):
+        fwdbwd()
+    ms_f = _time_steps(fwd, steps, flush, s)
+    ms_fb = _time_steps(fwdbwd, steps, flush, s)
+    NT = m["elem"].shape[0]
+    out["c5_fwd_bwd_64cube"] = {"fwd_ms": ms_f, "fwd_bwd_ms": ms_fb, "NT": NT,
+                                "fwd_Melem_s": NT / (ms_f * 1e-3) / 1e6, "fwd_bwd_Melem_s": NT / (ms_fb * 1e-3) / 1e6,
+                                "fwd_bwd_vs_plain_fwd": ms_f / ms_fb}
+    fa.get_error()
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_1804_05156_gb300 as fa
@@ -280,6 +372,22 @@ def run_ours(args):
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
            "gpu_launches": launches,
            "clocks": clk.summary()}
+    # secondary timings on the same mesh: atomic variant, boundary + Dirichlet elimination
+    fa.fem_assemble(p, node_d, k_d, f_kind, None, val, b, fa.FEM_ATOMIC)
+    ms_at = _time_steps(lambda: fa.fem_assemble(p, node_d, k_d, f_kind, None, val, b, fa.FEM_ATOMIC),
+                        max(3, min(args.steps, 10)), flush, s)
+    isbd = torch.empty(N, dtype=torch.uint8, device="cuda")
+    free = torch.empty(N, dtype=torch.int32, device="cuda")
+
+    def dirich():
+        fa.fem_boundary_nodes(p, None, isbd)
+        fa.fem_apply_dirichlet(p, isbd, None, val, b, free, want_count=False)
+    dirich()
+    ms_di = _time_steps(dirich, max(3, min(args.steps, 10)), flush, s)
+    out["atomic_variant"] = {"ms": ms_at, "Melem_s": NT / (ms_at * 1e-3) / 1e6}
+    out["dirichlet_ms"] = ms_di
+    if not args.no_extras and ws == 1:
+        out["extras"] = extras(fa, args, flush, value)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(mesh, 1 if mesh["f"] == "sinprod" else 0, args.cpu_seconds)
     if rank == 0:
@@ -298,6 +406,7 @@ def main():
     ap.add_argument("--config", choices=["c1", "c2", "c3"], default="c2")
     ap.add_argument("--variant", choices=["deterministic", "atomic"], default="deterministic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the 3-D, batched and fwd+bwd rows")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-sample", type=int, default=400_000)
     args = ap.parse_args()
