@@ -35,14 +35,28 @@ __device__ __forceinline__ double from_ordered(unsigned long long u) {
   return __longlong_as_double((long long)((u >> 63) ? (u & 0x7fffffffffffffffull) : ~u));
 }
 
+// Bounding box of the coordinates: per-thread, then per-warp min/max, then one atomic per warp and
+// coordinate on the order-preserving bit pattern.
 __global__ void k_bbox(const double* __restrict__ node, int64_t N, int d, unsigned long long* __restrict__ lo,
                        unsigned long long* __restrict__ hi) {
+  unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x)
     for (int m = 0; m < d; ++m) {
       const unsigned long long u = ordered_bits(node[v * d + m]);
-      atomicMin(lo + m, u);
-      atomicMax(hi + m, u);
+      mn[m] = u < mn[m] ? u : mn[m];
+      mx[m] = u > mx[m] ? u : mx[m];
     }
+  for (int m = 0; m < d; ++m) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long a = __shfl_xor_sync(0xffffffffu, mn[m], o), b = __shfl_xor_sync(0xffffffffu, mx[m], o);
+      mn[m] = a < mn[m] ? a : mn[m];
+      mx[m] = b > mx[m] ? b : mx[m];
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(lo + m, mn[m]);
+      atomicMax(hi + m, mx[m]);
+    }
+  }
 }
 
 __device__ __forceinline__ uint32_t spread2(uint32_t x) {  // 12 bits -> every other bit
