@@ -139,7 +139,10 @@ int fem_apply_dirichlet(fem_pattern_t p, const uint8_t* is_bd, const double* gD,
  * recomputed from node, not stored. Derivatives follow from eq. (dlambda): d|tau|/dx_m = |tau| g_m
  * and dg_i/dx_m = -g_m g_i^T with g_i = grad lambda_i. f_kind FEM_F_QPVALUES contributes only
  * through |tau| and the point weights (the values are inputs). Node gradients are summed over the
- * incident elements in ascending element order (deterministic). */
+ * incident elements in ascending element order (deterministic). The gradient of |tau| needs the
+ * orientation: a 2-D element must be counter-clockwise and a 3-D element positively oriented, else
+ * FEM_ERR_DEGENERATE. Arithmetic is float-float (about 2^-44 relative per operation); each output
+ * is rounded to double once. */
 int fem_assemble_backward(fem_pattern_t p, const double* node, const double* k, int f_kind, const double* f_arg,
                           const double* w, const double* r, double* gnode, double* gk, fem_stream_t stream);
 

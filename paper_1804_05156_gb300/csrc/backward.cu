@@ -1,233 +1,290 @@
 // Backward of the assembly: gradients of L = w . val + r . b with respect to the node coordinates and
-// the per-element coefficients. The basis gradients are recomputed from the coordinates.
+// the per-element coefficients, in float-float arithmetic (dfloat.cuh).
 //
-// With g_i = grad lambda_i = n_i / (d! |tau|) (eq. (dlambda)), a^tau = k |tau| G G^T, and the
-// identities d|tau|/dx_m = |tau| g_m, dg_i/dx_m = -g_m g_i^T:
-//   dL/dk_t   = |tau| S,                               S = sum_ij W_ij g_i . g_j
-//   dL_A/dx_m = k |tau| (S g_m - sum_i Q_im g_i),     Q = (W + W^T) P, P_ij = g_i . g_j
-//   dL_b/dx_m = |tau| g_m sum_i r_i c_i + |tau| sum_q w_q lambda_m(q) grad f(x_q) sum_i r_i lambda_i(q)
-// where W_ij = w[slot(t, i, j)], c_i = sum_q w_q f(x_q) lambda_i(q) and (w_q, lambda(q)) is the
-// element's quadrature rule. Node gradients are gathered per vertex over its incidence list
-// (ascending element order), so the result is deterministic.
+// With g_i = grad lambda_i = n_i / (d! |tau|) (eq. (dlambda)), a^tau = k |tau| G G^T, the identities
+// d|tau|/dx_m = |tau| g_m and dg_i/dx_m = -g_m g_i^T, W_ij = w[slot(t, i, j)] and P_ij = g_i . g_j:
+//   dL/dk_t   = |tau| S,                           S = sum_ij W_ij P_ij
+//   dL_A/dx_m = k |tau| (S g_m - sum_i Q_im g_i),  Q = (W + W^T) P
+//   dL_b/dx_m = |tau| g_m sum_q w_q f_q rl_q + |tau| sum_q w_q lambda_m(q) grad f(x_q) rl_q,
+//               rl_q = sum_i r_i lambda_i(q)
+// One thread per element writes gk[t] and its (d+1) x d vertex contributions (float pairs) to the
+// pattern's scratch; a second kernel sums each vertex's contributions over its incidence list in
+// ascending element order (deterministic) and writes gnode. No FP64 arithmetic except the final
+// rounding of each output (one FP64 add).
 #include <cuda_runtime.h>
 
 #include "common.cuh"
-#include "element.cuh"
+#include "element_df.cuh"
 
 namespace fem {
+
+const float4* sincos_table_device();  // values_blocked.cu
 
 namespace {
 
 template <int D>
-__device__ __forceinline__ void grad_f(int f_kind, const double (&p)[D], double (&g)[D]) {
-#pragma unroll
-  for (int c = 0; c < D; ++c) g[c] = 0.0;
-  if (f_kind != FEM_F_SINPROD) return;
-  double sp[D], cp[D];
-#pragma unroll
-  for (int m = 0; m < D; ++m) sincospi(p[m], &sp[m], &cp[m]);
-#pragma unroll
-  for (int c = 0; c < D; ++c) {
-    double v = 3.14159265358979323846 * cp[c];
-#pragma unroll
-    for (int m = 0; m < D; ++m)
-      if (m != c) v *= sp[m];
-    g[c] = v;
-  }
-}
-
-template <int D>
-__global__ void __launch_bounds__(256) k_backward_elem(const int32_t* __restrict__ elem, int64_t NT,
-                                                       const double* __restrict__ node, const double* __restrict__ k,
-                                                       int f_kind, const double* __restrict__ f_arg,
-                                                       const int32_t* __restrict__ slot, const double* __restrict__ w,
-                                                       const double* __restrict__ r, double* __restrict__ gk,
-                                                       double* __restrict__ scratch, int* __restrict__ err) {
+__global__ void __launch_bounds__(256) k_backward_df(const int32_t* __restrict__ elem, int NT,
+                                                     const double* __restrict__ node, const double* __restrict__ k,
+                                                     int f_kind, const double* __restrict__ f_arg,
+                                                     const int32_t* __restrict__ slot, const double* __restrict__ w,
+                                                     const double* __restrict__ r, double* __restrict__ gk,
+                                                     float2* __restrict__ scratch, const float4* __restrict__ tab,
+                                                     int* __restrict__ err) {
   constexpr int D1 = D + 1;
-  constexpr double DF = (D == 2) ? 2.0 : 6.0;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < NT; t += (int64_t)gridDim.x * blockDim.x) {
-    int e[D1];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= NT) return;
+  int e[D1];
 #pragma unroll
-    for (int i = 0; i < D1; ++i) e[i] = elem[t * D1 + i];
-    double x[D1][D];
-    load_coords<D>(node, e, x);
-    double n[D1][D], meas;
-    bool ok;
+  for (int i = 0; i < D1; ++i) e[i] = __ldg(elem + (size_t)t * D1 + i);
+  VtxDF<D> V[D1];
+#pragma unroll
+  for (int i = 0; i < D1; ++i)
+#pragma unroll
+    for (int m = 0; m < D; ++m) V[i].x[m] = split3(__ldg(node + (size_t)e[i] * D + m));
+  // scaled inward normals n_i and the positive measure |tau| (d! |tau| = signed 2-D area x 2, 3-D vol x 6)
+  df2 n[D1][D];
+  df2 dmeas;  // d! |tau|
+  if constexpr (D == 2) {
+    df2 ev[3][2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      ev[0][m] = f3_diff(V[2].x[m], V[1].x[m]);
+      ev[1][m] = f3_diff(V[0].x[m], V[2].x[m]);
+      ev[2][m] = f3_diff(V[1].x[m], V[0].x[m]);
+    }
+    dmeas = df_sub(df_mul(ev[1][0], ev[2][1]), df_mul(ev[1][1], ev[2][0]));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      n[i][0] = df_neg(ev[i][1]);
+      n[i][1] = ev[i][0];
+    }
+  } else {
+    df2 ed[3][3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) ed[q][m] = f3_diff(V[q + 1].x[m], V[0].x[m]);
+    df_cross(ed[1], ed[2], n[1]);
+    df_cross(ed[2], ed[0], n[2]);
+    df_cross(ed[0], ed[1], n[3]);
+    df2 u[3], v[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      u[m] = f3_diff(V[3].x[m], V[1].x[m]);
+      v[m] = f3_diff(V[2].x[m], V[1].x[m]);
+    }
+    df_cross(u, v, n[0]);
+    dmeas = df_dot<3>(n[3], ed[2]);
+  }
+  if (!(dmeas.h > 0.0f && dmeas.h < INFINITY)) report(err, FEM_ERR_DEGENERATE);
+  const df2 inv = df_recip(dmeas);
+  const df2 meas = (D == 2) ? df_scale(dmeas, 0.5f) : df_mul(dmeas, df2{0.1666666716337204f, -4.9670538793e-09f});
+  df2 g[D1][D];
+#pragma unroll
+  for (int i = 0; i < D1; ++i)
+#pragma unroll
+    for (int c = 0; c < D; ++c) g[i][c] = df_mul(n[i][c], inv);
+  df2 out[D1][D];
+#pragma unroll
+  for (int i = 0; i < D1; ++i)
+#pragma unroll
+    for (int c = 0; c < D; ++c) out[i][c] = df2{0.0f, 0.0f};
+  if (w) {
+    df2 P[D1][D1];
+#pragma unroll
+    for (int i = 0; i < D1; ++i)
+#pragma unroll
+      for (int j = i; j < D1; ++j) {
+        P[i][j] = df_dot<D>(g[i], g[j]);
+        P[j][i] = P[i][j];
+      }
+    df2 W[D1][D1];
+#pragma unroll
+    for (int i = 0; i < D1; ++i)
+#pragma unroll
+      for (int j = 0; j < D1; ++j) W[i][j] = df_from_double_fast(__ldg(w + __ldg(slot + (size_t)(i * D1 + j) * NT + t)));
+    df2 S = df2{0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < D1; ++i)
+#pragma unroll
+      for (int j = 0; j < D1; ++j) S = df_add(S, df_mul(W[i][j], P[i][j]));
+    if (gk) gk[t] = df_to_double(df_mul(meas, S));
+    const df2 kt = k ? df_from_double_fast(__ldg(k + t)) : df2{1.0f, 0.0f};
+    const df2 km = df_mul(kt, meas);
+#pragma unroll
+    for (int m = 0; m < D1; ++m) {
+      df2 acc[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) acc[c] = df_mul(S, g[m][c]);
+#pragma unroll
+      for (int i = 0; i < D1; ++i) {
+        df2 q = df2{0.0f, 0.0f};
+#pragma unroll
+        for (int j = 0; j < D1; ++j) q = df_add(q, df_mul(df_add(W[i][j], W[j][i]), P[j][m]));
+#pragma unroll
+        for (int c = 0; c < D; ++c) acc[c] = df_sub(acc[c], df_mul(q, g[i][c]));
+      }
+#pragma unroll
+      for (int c = 0; c < D; ++c) out[m][c] = df_mul(km, acc[c]);
+    }
+  } else if (gk) {
+    gk[t] = 0.0;
+  }
+  if (r) {
+    df2 rv[D1];
+#pragma unroll
+    for (int i = 0; i < D1; ++i) rv[i] = df_from_double_fast(__ldg(r + e[i]));
+    // quadrature points: f, grad f and barycentric weights lambda_i(q)
+    df2 fq[D1], gf[D1][D];
+    float lam_self, lam_other, wq;
     if constexpr (D == 2) {
-      ok = normals2(x, n, meas);
-      // the backward needs the signed area: reject inverted triangles
-      const double a2 = (x[1][0] - x[0][0]) * (x[2][1] - x[0][1]) - (x[1][1] - x[0][1]) * (x[2][0] - x[0][0]);
-      ok = ok && a2 > 0.0;
+      lam_self = 0.0f;
+      lam_other = 0.5f;
+      wq = 1.0f / 3.0f;
     } else {
-      ok = normals3(x, n, meas);
+      lam_self = 0.5854101777f;
+      lam_other = 0.1381966025f;
+      wq = 0.25f;
     }
-    if (!ok) report(err, FEM_ERR_DEGENERATE);
-    double g[D1][D];
-    const double inv = 1.0 / (DF * meas);
 #pragma unroll
-    for (int i = 0; i < D1; ++i)
+    for (int q = 0; q < D1; ++q)
 #pragma unroll
-      for (int c = 0; c < D; ++c) g[i][c] = n[i][c] * inv;
-    double P[D1][D1];
-#pragma unroll
-    for (int i = 0; i < D1; ++i)
-#pragma unroll
-      for (int j = 0; j < D1; ++j) {
-        double s = 0.0;
-#pragma unroll
-        for (int c = 0; c < D; ++c) s += g[i][c] * g[j][c];
-        P[i][j] = s;
-      }
-    const double kt = k ? k[t] : 1.0;
-    double out[D1][D];
-#pragma unroll
-    for (int m = 0; m < D1; ++m)
-#pragma unroll
-      for (int c = 0; c < D; ++c) out[m][c] = 0.0;
-    if (w) {
-      double W[D1][D1];
-#pragma unroll
-      for (int i = 0; i < D1; ++i)
-#pragma unroll
-        for (int j = 0; j < D1; ++j) W[i][j] = __ldg(w + slot[(int64_t)(i * D1 + j) * NT + t]);
-      double S = 0.0;
-#pragma unroll
-      for (int i = 0; i < D1; ++i)
-#pragma unroll
-        for (int j = 0; j < D1; ++j) S += W[i][j] * P[i][j];
-      if (gk) gk[t] = meas * S;
-#pragma unroll
-      for (int m = 0; m < D1; ++m) {
-        double acc[D];
-#pragma unroll
-        for (int c = 0; c < D; ++c) acc[c] = S * g[m][c];
-#pragma unroll
-        for (int i = 0; i < D1; ++i) {
-          double q = 0.0;
-#pragma unroll
-          for (int j = 0; j < D1; ++j) q += (W[i][j] + W[j][i]) * P[j][m];
-#pragma unroll
-          for (int c = 0; c < D; ++c) acc[c] -= q * g[i][c];
-        }
-#pragma unroll
-        for (int c = 0; c < D; ++c) out[m][c] = kt * meas * acc[c];
-      }
-    } else if (gk) {
-      gk[t] = 0.0;
-    }
-    if (r) {
-      double rv[D1];
-#pragma unroll
-      for (int i = 0; i < D1; ++i) rv[i] = __ldg(r + e[i]);
-      double fq[D1];
-      f_at_points<D>(x, f_kind, f_arg, t, fq);
-      // rule: 2-D midpoints (w_q = 1/3, lambda_i(q) = 1/2 for i != q, 0 for i == q);
-      //       3-D (w_q = 1/4, lambda_i(q) = alpha if i == q else beta)
-      double lam[D1][D1];
-      double wq;
-      double pts[D1][D];
+      for (int c = 0; c < D; ++c) gf[q][c] = df2{0.0f, 0.0f};
+    if (f_kind == FEM_F_SINPROD) {
+      df2 sn[D1][D], cs[D1][D];  // sin(pi x_q,m), cos(pi x_q,m)
       if constexpr (D == 2) {
-        wq = 1.0 / 3.0;
+        SC sc[3][2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int m = 0; m < 2; ++m) sc[i][m] = sincospi_half(V[i].x[m], tab);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
+          const int u = (q + 1) % 3, v = (q + 2) % 3;
 #pragma unroll
-          for (int i = 0; i < 3; ++i) lam[q][i] = (i == q) ? 0.0 : 0.5;
-#pragma unroll
-          for (int c = 0; c < 2; ++c) pts[q][c] = (x[(q + 1) % 3][c] + x[(q + 2) % 3][c]) * 0.5;
+          for (int m = 0; m < 2; ++m) {
+            sn[q][m] = sin_mid(sc[u][m], sc[v][m]);
+            cs[q][m] = df_sub(df_mul(sc[u][m].c, sc[v][m].c), df_mul(sc[u][m].s, sc[v][m].s));
+          }
         }
       } else {
-        wq = 0.25;
-        const double s5 = 2.23606797749978969641;
-        const double alpha = (5.0 + 3.0 * s5) / 20.0, beta = (5.0 - s5) / 20.0;
+        const df2 al = {0.58541017770767212f, 1.8917296174e-08f}, be = {0.13819660246372223f, -1.3387116971e-09f};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int m = 0; m < 3; ++m) {
+          const float nn = rintf(V[0].x[m].a);
+          df2 y[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) lam[q][i] = (i == q) ? alpha : beta;
+          for (int i = 0; i < 4; ++i) y[i] = df_add(two_sum(V[i].x[m].a, -nn), fast_two_sum(V[i].x[m].b, V[i].x[m].c));
+          const df2 sy = df_add(df_add(y[0], y[1]), df_add(y[2], y[3]));
+          const float sgn = (__float2int_rn(nn) & 1) ? -1.0f : 1.0f;
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            double s = 0.0;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) s += lam[q][i] * x[i][c];
-            pts[q][c] = s;
+          for (int q = 0; q < 4; ++q) {
+            df_sincospi(df_add(df_mul(be, sy), df_mul(df_sub(al, be), y[q])), tab, sn[q][m], cs[q][m]);
+            sn[q][m] = df2{sn[q][m].h * sgn, sn[q][m].l * sgn};
+            cs[q][m] = df2{cs[q][m].h * sgn, cs[q][m].l * sgn};
           }
         }
       }
-      double Rb = 0.0;
-#pragma unroll
-      for (int i = 0; i < D1; ++i) {
-        double ci = 0.0;
-#pragma unroll
-        for (int q = 0; q < D1; ++q) ci += wq * fq[q] * lam[q][i];
-        Rb += rv[i] * ci;
-      }
-      double gf[D1][D], rl[D1];
+      const df2 PI = {3.14159274101257324f, -8.74227765734758577e-8f};
 #pragma unroll
       for (int q = 0; q < D1; ++q) {
-        grad_f<D>(f_kind, pts[q], gf[q]);
-        double s = 0.0;
+        df2 f = sn[q][0];
 #pragma unroll
-        for (int i = 0; i < D1; ++i) s += rv[i] * lam[q][i];
-        rl[q] = s;
-      }
-#pragma unroll
-      for (int m = 0; m < D1; ++m)
+        for (int m = 1; m < D; ++m) f = df_mul(f, sn[q][m]);
+        fq[q] = f;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-          double s2 = 0.0;
+          df2 gv = df_mul(PI, cs[q][c]);
 #pragma unroll
-          for (int q = 0; q < D1; ++q) s2 += wq * lam[q][m] * gf[q][c] * rl[q];
-          out[m][c] += meas * g[m][c] * Rb + meas * s2;
+          for (int m = 0; m < D; ++m)
+            if (m != c) gv = df_mul(gv, sn[q][m]);
+          gf[q][c] = gv;
         }
+      }
+    } else if (f_kind == FEM_F_QPVALUES) {
+#pragma unroll
+      for (int q = 0; q < D1; ++q) fq[q] = df_from_double_fast(__ldg(f_arg + (size_t)t * D1 + q));
+    } else {
+      const df2 c0 = f_arg ? df_from_double_fast(__ldg(f_arg)) : df2{1.0f, 0.0f};
+#pragma unroll
+      for (int q = 0; q < D1; ++q) fq[q] = c0;
     }
+    // rl_q = sum_i r_i lambda_i(q) = lam_other * sum_i r_i + (lam_self - lam_other) r_q
+    df2 rs = rv[0];
+#pragma unroll
+    for (int i = 1; i < D1; ++i) rs = df_add(rs, rv[i]);
+    df2 rl[D1];
+    df2 Rb = df2{0.0f, 0.0f};
+#pragma unroll
+    for (int q = 0; q < D1; ++q) {
+      rl[q] = df_add(df_mul_f(rs, lam_other), df_mul_f(rv[q], lam_self - lam_other));
+      Rb = df_add(Rb, df_mul(fq[q], rl[q]));
+    }
+    Rb = df_mul_f(Rb, wq);
 #pragma unroll
     for (int m = 0; m < D1; ++m)
 #pragma unroll
-      for (int c = 0; c < D; ++c) scratch[(int64_t)(m * D + c) * NT + t] = out[m][c];
+      for (int c = 0; c < D; ++c) {
+        df2 s2 = df2{0.0f, 0.0f};
+        if (f_kind == FEM_F_SINPROD) {
+#pragma unroll
+          for (int q = 0; q < D1; ++q)
+            s2 = df_add(s2, df_mul_f(df_mul(gf[q][c], rl[q]), wq * (q == m ? lam_self : lam_other)));
+        }
+        out[m][c] = df_add(out[m][c], df_mul(meas, df_add(df_mul(g[m][c], Rb), s2)));
+      }
   }
+#pragma unroll
+  for (int m = 0; m < D1; ++m)
+#pragma unroll
+    for (int c = 0; c < D; ++c) scratch[(size_t)(m * D + c) * NT + t] = make_float2(out[m][c].h, out[m][c].l);
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) k_backward_gather(const int32_t* __restrict__ inc_ptr,
-                                                         const int32_t* __restrict__ inc, int64_t N, int64_t NT,
-                                                         const double* __restrict__ scratch, double* __restrict__ gnode) {
+__global__ void __launch_bounds__(256) k_backward_gather_df(const int32_t* __restrict__ inc_ptr,
+                                                            const int32_t* __restrict__ inc, int N, int NT,
+                                                            const float2* __restrict__ scratch, double* __restrict__ gnode) {
   constexpr int D1 = D + 1;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
-    double acc[D];
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= N) return;
+  df2 acc[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) acc[c] = 0.0;
-    for (int q = inc_ptr[v]; q < inc_ptr[v + 1]; ++q) {
-      const int p = inc[q];
-      const int64_t t = p / D1;
-      const int m = p - (int)t * D1;
+  for (int c = 0; c < D; ++c) acc[c] = df2{0.0f, 0.0f};
+  for (int q = inc_ptr[v]; q < inc_ptr[v + 1]; ++q) {
+    const int p = inc[q];
+    const int t = p / D1, m = p - t * D1;
 #pragma unroll
-      for (int c = 0; c < D; ++c) acc[c] = acc[c] + scratch[(int64_t)(m * D + c) * NT + t];
+    for (int c = 0; c < D; ++c) {
+      const float2 x = __ldg(scratch + (size_t)(m * D + c) * NT + t);
+      acc[c] = df_acc(acc[c], df2{x.x, x.y});
     }
-#pragma unroll
-    for (int c = 0; c < D; ++c) gnode[v * D + c] = acc[c];
   }
+#pragma unroll
+  for (int c = 0; c < D; ++c) gnode[(size_t)v * D + c] = df_to_double(acc[c]);
 }
 
 }  // namespace
 
 int assemble_backward(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg,
-                      const double* w, const double* r, double* gnode, double* gk, cudaStream_t s) {
+                         const double* w, const double* r, double* gnode, double* gk, cudaStream_t s) {
   int* err = device_error_word();
   if (!err) return set_error(FEM_ERR_OOM, "cannot allocate the device error word");
   if (!P->scratch) return set_error(FEM_ERR_STATE, "pattern has no scratch for the backward gather");
-  const int64_t NT = P->NT, N = P->N;
+  const float4* tab = sincos_table_device();
+  if (!tab) return set_error(FEM_ERR_CUDA, "sin/cos table unavailable");
+  const int NT = (int)P->NT, N = (int)P->N;
   if (NT == 0) {
     if (gnode && N > 0) FEM_CUDA(cudaMemsetAsync(gnode, 0, sizeof(double) * N * P->d, s));
     return FEM_OK;
   }
-  const int grid = grid_for(NT, 256, 152 * 16);
+  float2* scr = reinterpret_cast<float2*>(P->scratch);
+  const int g1 = (NT + 255) / 256, g2 = (N + 255) / 256;
   if (P->d == 2) {
-    FEM_LAUNCH(k_backward_elem<2>, grid, 256, 0, s, P->elem, NT, node, k, f_kind, f_arg, P->slot, w, r, gk, P->scratch,
-               err);
-    if (gnode) FEM_LAUNCH(k_backward_gather<2>, grid_for(N, 256), 256, 0, s, P->inc_ptr, P->inc, N, NT, P->scratch, gnode);
+    FEM_LAUNCH(k_backward_df<2>, g1, 256, 0, s, P->elem, NT, node, k, f_kind, f_arg, P->slot, w, r, gk, scr, tab, err);
+    if (gnode) FEM_LAUNCH(k_backward_gather_df<2>, g2, 256, 0, s, P->inc_ptr, P->inc, N, NT, scr, gnode);
   } else {
-    FEM_LAUNCH(k_backward_elem<3>, grid, 256, 0, s, P->elem, NT, node, k, f_kind, f_arg, P->slot, w, r, gk, P->scratch,
-               err);
-    if (gnode) FEM_LAUNCH(k_backward_gather<3>, grid_for(N, 256), 256, 0, s, P->inc_ptr, P->inc, N, NT, P->scratch, gnode);
+    FEM_LAUNCH(k_backward_df<3>, g1, 256, 0, s, P->elem, NT, node, k, f_kind, f_arg, P->slot, w, r, gk, scr, tab, err);
+    if (gnode) FEM_LAUNCH(k_backward_gather_df<3>, g2, 256, 0, s, P->inc_ptr, P->inc, N, NT, scr, gnode);
   }
   return FEM_OK;
 }

@@ -127,6 +127,19 @@ __device__ __forceinline__ df2 df_from_double(double x) {
   return fast_two_sum(s.a, __fadd_rn(s.b, s.c));
 }
 
+// df approximation of a double that need not be exact (relative error ~2^-47): the leading 24 bits
+// from the IEEE bits, the remaining 29 bits through one int32->float conversion.
+__device__ __forceinline__ df2 df_from_double_fast(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const int E = (int)((hi >> 20) & 0x7ff);
+  if (E < 897 || E > 1150) return df2{(float)0.0f, 0.0f};
+  const uint32_t sign = hi & 0x80000000u;
+  const float a = __uint_as_float(sign | ((uint32_t)(E - 896) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+  const int e0 = E - 1075;
+  const float r = (e0 >= -126) ? __fmul_rn(__uint2float_rn(lo & 0x1fffffffu), pow2f(e0)) : 0.0f;
+  return fast_two_sum(a, sign ? -r : r);
+}
+
 // xj - xi as df, from exact three-float splits: the difference of the leading parts and of the
 // middle parts are formed exactly with two-sum, so the result is accurate to ~2^-47 of |xj - xi|
 // however close xi and xj are.
@@ -190,6 +203,19 @@ __device__ __forceinline__ void df_sincospi_small(df2 r, const float4* __restric
   if (k < 0) Sk = df_neg(Sk);
   s = df_add(df_mul(Sk, cs), df_mul(Ck, sn));
   c = df_sub(df_mul(Ck, cs), df_mul(Sk, sn));
+}
+
+// sin(pi x) and cos(pi x) for a df x of any size (reduction as in df_sinpi below).
+__device__ __forceinline__ void df_sincospi(df2 x, const float4* __restrict__ tab, df2& s, df2& c) {
+  const float n = rintf(x.h);
+  df2 r = fast_two_sum(__fsub_rn(x.h, n), x.l);
+  const float n2 = rintf(r.h);
+  r = fast_two_sum(__fsub_rn(r.h, n2), r.l);
+  df_sincospi_small(r, tab, s, c);
+  if ((__float2int_rn(n) + __float2int_rn(n2)) & 1) {
+    s = df_neg(s);
+    c = df_neg(c);
+  }
 }
 
 // sin(pi x) for a df x of any size: x = n + r exactly with n = rint(x.h), then the parity of n.

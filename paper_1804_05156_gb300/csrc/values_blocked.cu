@@ -48,6 +48,18 @@ int ensure_sincos_table() {
   return FEM_OK;
 }
 
+}  // namespace
+
+// Device address of the sin/cos table on the current device (filled on first use); nullptr on failure.
+const float4* sincos_table_device() {
+  if (ensure_sincos_table() != FEM_OK) return nullptr;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_sincos_tab) != cudaSuccess) return nullptr;
+  return static_cast<const float4*>(p);
+}
+
+namespace {
+
 struct BlkArgs {
   int N, NT, E;
   int V, SB, nblocks;
