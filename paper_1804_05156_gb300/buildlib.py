@@ -3,6 +3,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import glob
+import hashlib
 import os
 import subprocess
 import sys
@@ -33,6 +34,20 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
+def source_digest() -> str:
+    """sha256 over the kernel sources and the ABI header (names and contents, sorted by name): ties a
+    profile's counters to the code they were taken from."""
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cuh")))
+    files.append(os.path.join(ROOT, "include", "femasm.h"))
+    for f in files:
+        h.update(os.path.basename(f).encode() + b"\0")
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+        h.update(b"\0")
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     deps = srcs + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "femasm.h"), __file__]
@@ -54,5 +69,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
 
 if __name__ == "__main__":
+    if "--digest" in sys.argv:
+        print(source_digest())
+        sys.exit(0)
     build(force="--force" in sys.argv, verbose=True,
           extra=["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else None)
