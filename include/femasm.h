@@ -64,15 +64,16 @@ typedef void* fem_stream_t; /* cudaStream_t */
 int fem_mesh_build_pattern(int d, int64_t N, int64_t NT, const int32_t* elem, fem_pattern_t* out,
                            fem_stream_t stream);
 
-/* Locality plan of the deterministic value kernel. The pattern build makes one from the vertex
- * numbering. Vertices are cut into blocks of consecutive ids, and one CTA owns each block's rows;
- * elements on block boundaries are computed once per block they touch. This call rebuilds the plan
- * from a geometric order instead: a Morton code of the coordinates `node` [N][d] (device), grouped
- * first by group [N] (device int32, nullable; for example the mesh id in a batch). Compact blocks
- * mean fewer boundary elements. It also tunes the launch (see fem_pattern_launch_shape). The
- * coordinates only choose the order and the timing workload: any values give the same results,
- * and later calls may pass different coordinates. Synchronises `stream`. Meshes whose rows exceed
- * 32 entries keep the two-pass deterministic path. */
+/* Locality plans of the deterministic value paths (see FEM_PATH_* below). The pattern build makes
+ * them from the vertex numbering: the owner-computes plan cuts the vertices into blocks of
+ * consecutive ids, one CTA per block's rows; the tile plan orders the elements by their earliest
+ * vertex and cuts them into tiles. This call rebuilds both from a geometric order instead: a Morton
+ * code of the coordinates `node` [N][d] (device), grouped first by group [N] (device int32,
+ * nullable; for example the mesh id in a batch). It also tunes the launch (see
+ * fem_pattern_launch_shape and fem_pattern_value_path). The coordinates only choose the order and
+ * the timing workload: any values give the same results, and later calls may pass different
+ * coordinates. Synchronises `stream`. Rows of more than 32 entries rule out the owner-computes
+ * plan, rows of more than 256 entries the tile plan; a mesh with neither takes the two-pass path. */
 int fem_pattern_set_locality(fem_pattern_t p, const double* node, const int32_t* group, fem_stream_t stream);
 /* The tuned launch of the deterministic value kernel. fem_pattern_set_locality times every feasible
  * combination of rows per block (128, 256, 512), launch shape (threads per CTA x CTAs per SM) and
@@ -88,6 +89,29 @@ int fem_pattern_launch_shape(fem_pattern_t p, int* rows_per_block, int* threads,
  * persistent 0/1. Every launch gives the same bits. FEM_ERR_ARG if the shape is not supported or the
  * plan does not fit it; FEM_ERR_STATE if the mesh has no blocked plan. */
 int fem_pattern_force_launch(fem_pattern_t p, int threads, int ctas_per_sm, int persistent);
+
+/* ---- deterministic value paths --------------------------------------------------------------------
+ * All three give every CSR entry as the sum of its element contributions in ascending element order;
+ * they differ in where the sums are formed:
+ *   FEM_PATH_TILES    elements computed once per tile of 128 or 256 elements in locality order, each
+ *                     row's local entries written as packets to the row's incidence slots, then one
+ *                     thread per row sums its packets (two launches; float-float arithmetic);
+ *   FEM_PATH_BLOCKED  owner-computes blocks of rows, elements on block boundaries computed by every
+ *                     block they touch, sums formed in shared memory (one launch; float-float);
+ *   FEM_PATH_TWO_PASS per-element FP64 values to scratch, then a per-slot FP64 reduction.
+ * TILES and BLOCKED give identical bits. fem_pattern_set_locality times TILES (both tile sizes)
+ * against the best BLOCKED launch and keeps the faster; without coordinates TILES (256) is used. */
+#define FEM_PATH_TWO_PASS 0
+#define FEM_PATH_BLOCKED 1
+#define FEM_PATH_TILES 2
+/* The path fem_assemble(FEM_DETERMINISTIC) takes, the tile size (0 unless TILES) and the tuner's time
+ * for it in ms (0 when not tuned). Outputs are host pointers, nullable. */
+int fem_pattern_value_path(fem_pattern_t p, int* path, int* tile_elems, float* tuned_ms);
+/* Select the path: TWO_PASS drops both plans; BLOCKED needs the blocked plan (FEM_ERR_STATE if the
+ * mesh has none); TILES builds the tile plan for tile_elems (128 or 256) if it is not the current one
+ * (synchronises `stream`; FEM_ERR_STATE if a row has more than 256 entries). fem_pattern_force_launch
+ * selects BLOCKED. */
+int fem_pattern_force_path(fem_pattern_t p, int path, int tile_elems, fem_stream_t stream);
 
 /* Sizes and library-owned device arrays of a pattern (valid until fem_pattern_destroy):
  * row_ptr [N+1], col_idx [nnz], slot [(d+1)^2 * NT] (layout above). Any output pointer may be NULL. */

@@ -21,6 +21,7 @@ FEM_ERR_ARG, FEM_ERR_INDEX, FEM_ERR_DEGENERATE, FEM_ERR_CUDA, FEM_ERR_OOM, FEM_E
     -1, -2, -3, -4, -5, -6, -7)
 FEM_DETERMINISTIC, FEM_ATOMIC = 0, 1
 FEM_F_CONST, FEM_F_SINPROD, FEM_F_QPVALUES = 0, 1, 2
+FEM_PATH_TWO_PASS, FEM_PATH_BLOCKED, FEM_PATH_TILES = 0, 1, 2
 
 _lib = None
 
@@ -51,6 +52,8 @@ def lib():
             "fem_pattern_set_locality": (I32, [P, P, P, P]),
             "fem_pattern_launch_shape": (I32, [P, P, P, P, P, P]),
             "fem_pattern_force_launch": (I32, [P, I32, I32, I32]),
+            "fem_pattern_value_path": (I32, [P, P, P, P]),
+            "fem_pattern_force_path": (I32, [P, I32, I32, P]),
             "fem_pattern_destroy": (None, [P]),
             "fem_assemble": (I32, [P, P, P, I32, P, P, P, I32, P]),
             "fem_assemble_stiffness": (I32, [P, P, P, P, I32, P]),
@@ -186,6 +189,18 @@ def fem_pattern_launch_shape(p: Pattern) -> dict:
 
 def fem_pattern_force_launch(p: Pattern, threads: int, ctas_per_sm: int, persistent: bool):
     _check(lib().fem_pattern_force_launch(p.handle, threads, ctas_per_sm, 1 if persistent else 0))
+
+
+def fem_pattern_value_path(p: Pattern) -> dict:
+    """The deterministic value path of the pattern: {"path": "tiles"|"blocked"|"two_pass", "tile_elems", "tuned_ms"}."""
+    pa, te, ms = C.c_int(), C.c_int(), C.c_float()
+    _check(lib().fem_pattern_value_path(p.handle, C.byref(pa), C.byref(te), C.byref(ms)))
+    names = {FEM_PATH_TWO_PASS: "two_pass", FEM_PATH_BLOCKED: "blocked", FEM_PATH_TILES: "tiles"}
+    return {"path": names[pa.value], "tile_elems": te.value, "tuned_ms": ms.value}
+
+
+def fem_pattern_force_path(p: Pattern, path: int, tile_elems: int = 256, stream=None):
+    _check(lib().fem_pattern_force_path(p.handle, path, tile_elems, _stream(stream)))
 
 
 def fem_mesh_build_pattern(elem: torch.Tensor, N: int, stream=None) -> Pattern:

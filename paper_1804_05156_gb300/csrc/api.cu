@@ -98,6 +98,7 @@ bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 void free_pattern(Pattern& P) {
   fem::free_block_plan(P.blk);
+  fem::free_tile_plan(P.tile);
   cudaFree(P.elem);
   cudaFree(P.row_ptr);
   cudaFree(P.col_idx);
@@ -204,6 +205,52 @@ int fem_pattern_force_launch(fem_pattern_t p, int threads, int ctas_per_sm, int 
   B.minb = ctas_per_sm;
   B.persistent = persistent != 0;
   B.tuned_ms = 0.0f;
+  p->P.use_tiles = false;
+  return FEM_OK;
+}
+
+int fem_pattern_value_path(fem_pattern_t p, int* path, int* tile_elems, float* tuned_ms) {
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  const Pattern& P = p->P;
+  const int pth = P.use_tiles ? FEM_PATH_TILES : (P.blk.ok ? FEM_PATH_BLOCKED : FEM_PATH_TWO_PASS);
+  if (path) *path = pth;
+  if (tile_elems) *tile_elems = P.use_tiles ? P.tile.TE : 0;
+  if (tuned_ms) {
+    *tuned_ms = 0.0f;
+    if (pth == FEM_PATH_TILES && P.tile.tuned_ms < 1e29f) *tuned_ms = P.tile.tuned_ms;
+    if (pth == FEM_PATH_BLOCKED) *tuned_ms = P.blk.tuned_ms;
+  }
+  return FEM_OK;
+}
+
+int fem_pattern_force_path(fem_pattern_t p, int path, int tile_elems, fem_stream_t stream) {
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  Pattern& P = p->P;
+  if (path == FEM_PATH_TWO_PASS) {
+    fem::free_block_plan(P.blk);
+    fem::free_tile_plan(P.tile);
+    P.use_tiles = false;
+    return FEM_OK;
+  }
+  if (path == FEM_PATH_BLOCKED) {
+    if (!P.blk.ok) return set_error(FEM_ERR_STATE, "this mesh has no blocked plan");
+    P.use_tiles = false;
+    return FEM_OK;
+  }
+  if (path != FEM_PATH_TILES) return set_error(FEM_ERR_ARG, "unknown value path %d", path);
+  if (tile_elems != 128 && tile_elems != 256) return set_error(FEM_ERR_ARG, "tile size must be 128 or 256");
+  if (!(P.tile.ok && P.tile.TE == tile_elems)) {
+    fem::TilePlan T;
+    int rc = fem::build_tile_plan(&P, P.blk.order, tile_elems, &T, (cudaStream_t)stream);
+    if (rc) return rc;
+    if (!T.ok) {
+      fem::free_tile_plan(T);
+      return set_error(FEM_ERR_STATE, "this mesh has no tile plan (a row longer than 256 entries)");
+    }
+    fem::free_tile_plan(P.tile);
+    P.tile = T;
+  }
+  P.use_tiles = true;
   return FEM_OK;
 }
 
@@ -237,6 +284,8 @@ int fem_assemble(fem_pattern_t p, const double* node, const double* k, int f_kin
   if (rc) return rc;
   if (!aligned(val, 8) || !aligned(b, 8)) return set_error(FEM_ERR_ARG, "misaligned output array");
   if (!val && !b) return FEM_OK;
+  if (variant == FEM_DETERMINISTIC && p->P.use_tiles)
+    return fem::assemble_tiles(&p->P, node, k, f_kind, f_arg, val, b, (cudaStream_t)stream);
   if (variant == FEM_DETERMINISTIC && p->P.blk.ok)
     return fem::assemble_blocked(&p->P, node, k, f_kind, f_arg, val, b, (cudaStream_t)stream);
   return fem::assemble_values(&p->P, node, k, f_kind, f_arg, val, b, variant, (cudaStream_t)stream);

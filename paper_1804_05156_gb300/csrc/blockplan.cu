@@ -376,6 +376,8 @@ static const int kShapes3[][2] = {{512, 1}, {256, 2}, {256, 1}};
 
 int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group, cudaStream_t s) {
   free_block_plan(P->blk);
+  free_tile_plan(P->tile);
+  P->use_tiles = false;
   const int d = P->d;
   const bool sinprod = (d == 2);  // the tuning workload: the 2-D sine-product load, 3-D constant load
   // Without coordinates there is nothing to time: take the first feasible block size, default shape.
@@ -389,9 +391,19 @@ int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group
       while (B.minb > 1 && blocked_smem_need(B, d, sinprod) > blocked_smem_budget(B.minb)) B.minb >>= 1;
       if (B.ok && blocked_smem_need(B, d, sinprod) <= blocked_smem_budget(B.minb)) {
         P->blk = B;
-        return FEM_OK;
+        break;
       }
       free_block_plan(B);
+    }
+    // the two-phase path on the same vertex order (identity order if no blocked plan was feasible)
+    TilePlan T;
+    int rc = build_tile_plan(P, P->blk.order, 256, &T, s);
+    if (rc) return rc;
+    if (T.ok) {
+      P->tile = T;
+      P->use_tiles = true;
+    } else {
+      free_tile_plan(T);
     }
     return FEM_OK;
   }
@@ -448,6 +460,41 @@ int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group
     }
     if (!kept) free_block_plan(B);
   }
+  // The two-phase path on the chosen vertex order: time each tile size, keep the fastest if it beats
+  // the blocked plan.
+  TilePlan bestT;
+  for (int ti = 0; ti < 2 && rc == FEM_OK; ++ti) {
+    const int TEs[] = {256, 128};
+    TilePlan T;
+    rc = build_tile_plan(P, best.order, TEs[ti], &T, s);
+    if (rc) break;
+    if (!T.ok) {
+      free_tile_plan(T);
+      continue;
+    }
+    Pattern Q = *P;
+    Q.tile = T;
+    const int fk = sinprod ? FEM_F_SINPROD : FEM_F_CONST;
+    rc = assemble_tiles(&Q, node_hint, nullptr, fk, nullptr, val, bb, s);  // warm-up
+    if (rc == FEM_OK) {
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 3 && rc == FEM_OK; ++r) rc = assemble_tiles(&Q, node_hint, nullptr, fk, nullptr, val, bb, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = cuda_error(cudaGetLastError(), "tuning run");
+    }
+    float ms = 1e30f;
+    if (rc == FEM_OK) {
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= 3.0f;
+    }
+    if (rc == FEM_OK && ms < bestT.tuned_ms) {
+      free_tile_plan(bestT);
+      bestT = T;
+      bestT.tuned_ms = ms;
+    } else {
+      free_tile_plan(T);
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFreeAsync(val, s);
@@ -456,9 +503,16 @@ int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group
   cudaStreamSynchronize(s);
   if (rc) {
     if (best.order) free_block_plan(best);
+    free_tile_plan(bestT);
     return rc;
   }
   if (best.order) P->blk = best;
+  if (bestT.ok && (!best.order || bestT.tuned_ms < best_ms)) {
+    P->tile = bestT;
+    P->use_tiles = true;
+  } else {
+    free_tile_plan(bestT);
+  }
   return FEM_OK;
 }
 

@@ -90,6 +90,26 @@ void free_block_plan(BlockPlan& B);
 int build_block_plan(const struct Pattern* P, const double* node_hint, const int32_t* group, int V, BlockPlan* out,
                      cudaStream_t s);
 
+// ---- tile plan of the two-phase value path, see tileplan.cu -----------------------------------------
+struct TilePlan {
+  int TE = 0, ntiles = 0;      // elements per tile, tiles
+  int64_t VT = 0;              // listed vertices over all tiles
+  int max_v = 0, max_row = 0;  // most vertices of one tile; longest row
+  bool ok = false;             // local ids fit 16 bits and rows have <= 256 entries
+  float tuned_ms = 1e30f;      // the tuner's time for this plan (1e30 if not timed)
+  int32_t* elist = nullptr;    // [NT] caller element ids in tile order
+  uint16_t* lelem = nullptr;   // [(d+1)][NT] local vertex ids, tile order
+  int32_t* voff = nullptr;     // [ntiles+1] vertex-list offsets
+  int32_t* vlist = nullptr;    // [VT] global vertex ids, ascending within a tile
+  int32_t* ipos = nullptr;     // [(d+1)][NT] packet (incidence) index of (elist[j], i)
+  void* pw = nullptr;          // [NT*(d+1)] per incidence: other columns' in-row positions (uint16 2-D, uint32 3-D)
+  uint8_t* rdp = nullptr;      // [N] in-row position of the diagonal
+  float4* pk = nullptr;        // [NT*(d+1)][2] packets of float pairs
+  float2* pb = nullptr;        // [NT*(d+1)] 3-D load terms
+};
+void free_tile_plan(TilePlan& T);
+int build_tile_plan(const struct Pattern* P, const int32_t* order, int TE, TilePlan* out, cudaStream_t s);
+
 // ---- pattern object --------------------------------------------------------------------------------
 struct Pattern {
   int d = 0, d1 = 0;
@@ -104,6 +124,8 @@ struct Pattern {
   double* scratch = nullptr;   // per-element values for the deterministic reduction
   int64_t scratch_elems = 0;   // doubles in scratch
   BlockPlan blk;               // owner-computes locality plan (blk.ok == false: two-pass path only)
+  TilePlan tile;               // two-phase plan (tile.ok == false: not available)
+  bool use_tiles = false;      // the deterministic value path runs the two-phase kernels
   int* work_counter = nullptr; // device counter of the persistent launch
 };
 // (Re)build P->blk, halving the block size until the packed limits hold (blk.ok false if they never do).
@@ -112,6 +134,8 @@ int blocked_smem_budget(int ctas_per_sm);
 int blocked_smem_need(const BlockPlan& B, int d, bool sinprod);
 int assemble_blocked(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg,
                      double* val, double* b, cudaStream_t s);
+int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg, double* val,
+                   double* b, cudaStream_t s);
 
 // scratch doubles per element: stiffness unique entries + rhs entries (+ gradient entries)
 inline int64_t scratch_per_elem(int d) { return d == 2 ? 9 : 14; }

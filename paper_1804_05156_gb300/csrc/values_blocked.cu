@@ -52,9 +52,14 @@ int ensure_sincos_table() {
 
 // Device address of the sin/cos table on the current device (filled on first use); nullptr on failure.
 const float4* sincos_table_device() {
+  static std::atomic<const float4*> addr[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (const float4* p = addr[dev].load(std::memory_order_acquire)) return p;
   if (ensure_sincos_table() != FEM_OK) return nullptr;
   void* p = nullptr;
   if (cudaGetSymbolAddress(&p, g_sincos_tab) != cudaSuccess) return nullptr;
+  addr[dev].store(static_cast<const float4*>(p), std::memory_order_release);
   return static_cast<const float4*>(p);
 }
 

@@ -1,0 +1,240 @@
+// Two-phase value path in float-float arithmetic: every element is computed exactly once, and every
+// row sums its incidences in ascending element order.
+//
+// Phase 1 (k_tile_elements): one CTA per tile of TE elements in locality order (tileplan.cu). The
+//   tile's vertices are staged in shared memory once (exact three-float splits; for the 2-D
+//   sine-product load also sin/cos(pi x/2) per coordinate), then each thread computes one element's
+//   local stiffness and load entries (element_df.cuh: Sec. 3.1.3, eq. (dlambda), Sec. 3.2) and writes,
+//   for each local row i, one packet of float pairs to the slot of incidence (t, i):
+//     2-D: (a_ii, a_ij, a_ik, b_i);  3-D: (a_ii, a_ij, a_ik, a_il), b_i separately,
+//   with j < k < l the other local indices.
+// Phase 2 (k_row_gather): one thread per row. Its packets are contiguous (the incidence lists are
+//   sorted by element), so it reads them in order, adds the diagonal and load terms in registers and
+//   the off-diagonal terms in a per-warp shared-memory copy of the warp's 32 rows (CSR order), then
+//   the warp converts and writes its rows' values with coalesced stores.
+// Every CSR entry is the float-float sum of its element contributions in ascending element order,
+// rounded to double once, whatever the tile size: the same bits as the owner-computes kernel.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "element_df.cuh"
+
+namespace fem {
+
+const float4* sincos_table_device();  // values_blocked.cu
+
+namespace {
+
+struct TileArgs {
+  int64_t NT;
+  const int32_t* elist;
+  const uint16_t* lelem;
+  const int32_t* voff;
+  const int32_t* vlist;
+  const int32_t* ipos;
+  float4* pk;
+  float2* pb;
+  int xs_bytes;
+};
+
+template <int D, int TE>
+__global__ void __launch_bounds__(TE) k_tile_elements(TileArgs a, const double* __restrict__ node,
+                                                      const double* __restrict__ k, int f_kind,
+                                                      const double* __restrict__ f_arg, int want_a, int want_b,
+                                                      const float4* __restrict__ tab, int* __restrict__ err) {
+  constexpr int D1 = D + 1;
+  extern __shared__ __align__(16) unsigned char sm[];
+  VtxDF<D>* xs = reinterpret_cast<VtxDF<D>*>(sm);
+  SC* scs = reinterpret_cast<SC*>(sm + a.xs_bytes);
+  const int tile = blockIdx.x;
+  const int v0 = __ldg(a.voff + tile), nv = __ldg(a.voff + tile + 1) - v0;
+  const bool sinprod2 = (D == 2) && f_kind == FEM_F_SINPROD && want_b;
+  // element data first: its loads are in flight during the vertex staging
+  const int64_t j = (int64_t)tile * TE + threadIdx.x;
+  const bool act = j < a.NT;
+  int t = 0;
+  int lv[D1];
+  double kd = 1.0;
+  if (act) {
+    t = __ldg(a.elist + j);
+#pragma unroll
+    for (int i = 0; i < D1; ++i) lv[i] = __ldg(a.lelem + (int64_t)i * a.NT + j);
+    if (k && want_a) kd = __ldg(k + t);
+  }
+  for (int v = threadIdx.x; v < nv; v += TE) {
+    const int R = __ldg(a.vlist + v0 + v);
+    VtxDF<D> x;
+#pragma unroll
+    for (int m = 0; m < D; ++m) x.x[m] = split3(__ldg(node + (size_t)R * D + m));
+    xs[v] = x;
+    if (sinprod2) {
+#pragma unroll
+      for (int m = 0; m < D; ++m) scs[v * D + m] = sincospi_half(x.x[m], tab);
+    }
+  }
+  __syncthreads();
+  if (!act) return;
+  const df2 kt = (k && want_a) ? df_from_double(kd) : df2{1.0f, 0.0f};
+  const df2 fconst = (f_kind == FEM_F_CONST && f_arg) ? df_from_double(__ldg(f_arg)) : df2{1.0f, 0.0f};
+  LocalDF<D> L;
+#pragma unroll
+  for (int c = 0; c < D1 * (D1 + 1) / 2; ++c) L.a[c] = df2{0.0f, 0.0f};
+#pragma unroll
+  for (int i = 0; i < D1; ++i) L.bt[i] = df2{0.0f, 0.0f};
+  bool ok;
+  if constexpr (D == 2) {
+    const VtxDF<2>* const V[3] = {&xs[lv[0]], &xs[lv[1]], &xs[lv[2]]};
+    const SC* const S[3] = {&scs[lv[0] * 2], &scs[lv[1] * 2], &scs[lv[2] * 2]};
+    ok = element_df2(V, S, kt, want_a, want_b, f_kind, fconst, f_arg, t, L);
+  } else {
+    const VtxDF<3>* const V[4] = {&xs[lv[0]], &xs[lv[1]], &xs[lv[2]], &xs[lv[3]]};
+    ok = element_df3(V, kt, want_a, want_b, f_kind, fconst, f_arg, t, tab, L);
+  }
+  if (!ok) report(err, FEM_ERR_DEGENERATE);
+#pragma unroll
+  for (int i = 0; i < D1; ++i) {
+    const int64_t q = __ldg(a.ipos + (int64_t)i * a.NT + j);
+    df2 o[D1];  // a_ii, then a_ij for j != i ascending
+    o[0] = L.a[pidx<D>(i, i)];
+    int c = 1;
+#pragma unroll
+    for (int jj = 0; jj < D1; ++jj)
+      if (jj != i) o[c++] = L.a[pidx<D>(i, jj)];
+    float4* dst = a.pk + 2 * q;
+    dst[0] = make_float4(o[0].h, o[0].l, o[1].h, o[1].l);
+    if constexpr (D == 2) {
+      dst[1] = make_float4(o[2].h, o[2].l, L.bt[i].h, L.bt[i].l);
+    } else {
+      dst[1] = make_float4(o[2].h, o[2].l, o[3].h, o[3].l);
+      a.pb[q] = make_float2(L.bt[i].h, L.bt[i].l);
+    }
+  }
+}
+
+template <int D, typename PW>
+__global__ void __launch_bounds__(256) k_row_gather(int64_t N, int max_row, const int32_t* __restrict__ row_ptr,
+                                                    const int32_t* __restrict__ inc_ptr, const PW* __restrict__ pw,
+                                                    const uint8_t* __restrict__ rdp, const float4* __restrict__ pk,
+                                                    const float2* __restrict__ pb, double* __restrict__ val,
+                                                    double* __restrict__ bvec) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  df2* acc = reinterpret_cast<df2*>(sm) + (size_t)wid * 32 * max_row;
+  const int64_t R0 = (int64_t)blockIdx.x * blockDim.x + wid * 32;
+  if (R0 >= N) return;  // whole warp
+  const int64_t R = R0 + lane;
+  const bool act = R < N;
+  const int64_t Rend = (R0 + 32 < N) ? R0 + 32 : N;
+  const int base = __ldg(row_ptr + R0);
+  const int region = __ldg(row_ptr + Rend) - base;
+  if (val)
+    for (int x = lane; x < region; x += 32) acc[x] = df2{0.0f, 0.0f};
+  __syncwarp();
+  if (act) {
+    const int rp = __ldg(row_ptr + R), rl = __ldg(row_ptr + R + 1) - rp;
+    const int o = rp - base;
+    df2 dacc = {0.0f, 0.0f}, bacc = {0.0f, 0.0f};
+    const int q1 = __ldg(inc_ptr + R + 1);
+    for (int q = __ldg(inc_ptr + R); q < q1; ++q) {
+      const float4 p1 = __ldg(pk + 2 * (size_t)q + 1);
+      if (val) {
+        const float4 p0 = __ldg(pk + 2 * (size_t)q);
+        const uint32_t w = (uint32_t)__ldg(pw + q);
+        dacc = df_acc(dacc, df2{p0.x, p0.y});
+        const int c0 = o + (int)(w & 0xffu), c1 = o + (int)((w >> 8) & 0xffu);
+        acc[c0] = df_acc(acc[c0], df2{p0.z, p0.w});
+        acc[c1] = df_acc(acc[c1], df2{p1.x, p1.y});
+        if constexpr (D == 3) {
+          const int c2 = o + (int)((w >> 16) & 0xffu);
+          acc[c2] = df_acc(acc[c2], df2{p1.z, p1.w});
+        }
+      }
+      if (bvec) {
+        if constexpr (D == 2) {
+          bacc = df_acc(bacc, df2{p1.z, p1.w});
+        } else {
+          const float2 x = __ldg(pb + q);
+          bacc = df_acc(bacc, df2{x.x, x.y});
+        }
+      }
+    }
+    if (val && rl > 0) acc[o + __ldg(rdp + R)] = dacc;
+    if (bvec) bvec[R] = df_to_double(bacc);
+  }
+  __syncwarp();
+  if (val)
+    for (int x = lane; x < region; x += 32) val[base + x] = df_to_double(acc[x]);
+}
+
+// rows per CTA of the gather: warps whose row copies fit a modest shared-memory budget
+int gather_warps(int max_row) {
+  const int per_warp = 32 * (max_row > 0 ? max_row : 1) * (int)sizeof(df2);
+  int w = (96 * 1024) / per_warp;
+  return w < 1 ? 1 : (w > 8 ? 8 : w);
+}
+
+}  // namespace
+
+int tile_smem_need(const TilePlan& T, int d, bool sinprod) {
+  const int xs = ((T.max_v * d * (int)sizeof(f3)) + 15) / 16 * 16;
+  return xs + ((sinprod && d == 2) ? T.max_v * d * (int)sizeof(SC) : 0);
+}
+
+int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg, double* val,
+                   double* b, cudaStream_t s) {
+  int* err = device_error_word();
+  if (!err) return set_error(FEM_ERR_OOM, "cannot allocate the device error word");
+  const float4* tab = sincos_table_device();
+  if (!tab) return set_error(FEM_ERR_CUDA, "sin/cos table unavailable");
+  const TilePlan& T = P->tile;
+  const int D = P->d;
+  if (P->NT == 0 || T.ntiles == 0) {
+    if (val && P->nnz > 0) FEM_CUDA(cudaMemsetAsync(val, 0, sizeof(double) * P->nnz, s));
+    if (b && P->N > 0) FEM_CUDA(cudaMemsetAsync(b, 0, sizeof(double) * P->N, s));
+    return FEM_OK;
+  }
+  TileArgs a;
+  a.NT = P->NT;
+  a.elist = T.elist;
+  a.lelem = T.lelem;
+  a.voff = T.voff;
+  a.vlist = T.vlist;
+  a.ipos = T.ipos;
+  a.pk = T.pk;
+  a.pb = T.pb;
+  a.xs_bytes = ((T.max_v * D * (int)sizeof(f3)) + 15) / 16 * 16;
+  const int want_a = val != nullptr, want_b = b != nullptr;
+  const int smem = tile_smem_need(T, D, f_kind == FEM_F_SINPROD && want_b);
+#define FEM_TILE_LAUNCH(DD, TT)                                                                               \
+  do {                                                                                                        \
+    if (smem > 48 * 1024)                                                                                     \
+      FEM_CUDA(cudaFuncSetAttribute(k_tile_elements<DD, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); \
+    FEM_LAUNCH((k_tile_elements<DD, TT>), T.ntiles, TT, smem, s, a, node, k, f_kind, f_arg, want_a, want_b, tab, err); \
+  } while (0)
+  if (D == 2) {
+    if (T.TE == 128) FEM_TILE_LAUNCH(2, 128);
+    else FEM_TILE_LAUNCH(2, 256);
+  } else {
+    if (T.TE == 128) FEM_TILE_LAUNCH(3, 128);
+    else FEM_TILE_LAUNCH(3, 256);
+  }
+#undef FEM_TILE_LAUNCH
+  const int wpc = gather_warps(T.max_row);
+  const int bt = 32 * wpc;
+  const int gsm = wpc * 32 * (T.max_row > 0 ? T.max_row : 1) * (int)sizeof(df2);
+  const int64_t grid = (P->N + bt - 1) / bt;
+  if (D == 2) {
+    if (gsm > 48 * 1024)
+      FEM_CUDA(cudaFuncSetAttribute(k_row_gather<2, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm));
+    FEM_LAUNCH((k_row_gather<2, uint16_t>), (int)grid, bt, gsm, s, P->N, T.max_row, P->row_ptr, P->inc_ptr,
+               (const uint16_t*)T.pw, T.rdp, T.pk, T.pb, val, b);
+  } else {
+    if (gsm > 48 * 1024)
+      FEM_CUDA(cudaFuncSetAttribute(k_row_gather<3, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm));
+    FEM_LAUNCH((k_row_gather<3, uint32_t>), (int)grid, bt, gsm, s, P->N, T.max_row, P->row_ptr, P->inc_ptr,
+               (const uint32_t*)T.pw, T.rdp, T.pk, T.pb, val, b);
+  }
+  return FEM_OK;
+}
+
+}  // namespace fem

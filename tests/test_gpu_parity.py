@@ -111,6 +111,78 @@ def test_every_launch_shape_gives_the_same_bits(case):
                 assert torch.equal(v, ref[0]) and torch.equal(b, ref[1]), (thr, cta, pers)
 
 
+def _fan(m_ring, seed=0):
+    """A disc of m_ring triangles around one centre vertex: the centre's row has m_ring + 1 entries."""
+    rng = np.random.default_rng(seed)
+    ang = np.sort(rng.uniform(0, 2 * np.pi, m_ring))
+    node = np.vstack([[0.0, 0.0], np.stack([np.cos(ang), np.sin(ang)], 1) * rng.uniform(0.8, 1.2, (m_ring, 1))])
+    elem = np.array([[0, 1 + i, 1 + (i + 1) % m_ring] for i in range(m_ring)], np.int32)
+    return node, elem
+
+
+@pytest.mark.parametrize("case", ["sq37p", "kuhn5", "kuhn7s", "delaunay2", "delaunay3"])
+def test_all_value_paths_give_the_same_bits(case):
+    """Tiles (both sizes) and owner-computes blocks sum every entry in the same order: identical bits,
+    for every load kind and for stiffness-only / load-only calls; the FP64 two-pass path agrees with
+    the oracle."""
+    d, node, elem, k, _ = mesh_case(case)
+    N, NT = node.shape[0], elem.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    fa.fem_pattern_set_locality(p, dev(node))
+    kd = None if k is None else dev(k)
+    fq = np.random.default_rng(8).normal(size=NT * (d + 1))
+    loads = [(fa.FEM_F_SINPROD, None), (fa.FEM_F_CONST, dev(np.array([2.5]))), (fa.FEM_F_QPVALUES, dev(fq))]
+    paths = [(fa.FEM_PATH_TILES, 256), (fa.FEM_PATH_TILES, 128), (fa.FEM_PATH_BLOCKED, 0)]
+    for fk, farg in loads:
+        ref = None
+        for path, te in paths:
+            fa.fem_pattern_force_path(p, path, te or 256)
+            assert fa.fem_pattern_value_path(p)["path"] == ("tiles" if path == fa.FEM_PATH_TILES else "blocked")
+            v, b = fa.assemble(p, dev(node), kd, fk, farg, fa.FEM_DETERMINISTIC)
+            vs = torch.empty_like(v)
+            fa.fem_assemble(p, dev(node), kd, fk, farg, vs, None, fa.FEM_DETERMINISTIC)
+            bs = torch.empty_like(b)
+            fa.fem_assemble(p, dev(node), kd, fk, farg, None, bs, fa.FEM_DETERMINISTIC)
+            fa.get_error()
+            assert torch.equal(vs, v) and torch.equal(bs, b), (path, te, fk)
+            if ref is None:
+                ref = (v, b)
+                _, _, vo, so = oracle.assemble(d, node, elem, k)
+                assert_close_scaled(host(v), vo, so)
+                ok = {fa.FEM_F_SINPROD: oracle.F_SINPROD, fa.FEM_F_CONST: oracle.F_CONST,
+                      fa.FEM_F_QPVALUES: oracle.F_QP}[fk]
+                oarg = {fa.FEM_F_SINPROD: None, fa.FEM_F_CONST: np.array([2.5]), fa.FEM_F_QPVALUES: fq}[fk]
+                sarg = np.abs(oarg) if oarg is not None else None
+                bo = oracle.rhs(d, node, elem, ok, oarg)
+                bsc = oracle.rhs(d, node, elem, ok, sarg) if fk == fa.FEM_F_QPVALUES else np.abs(bo)
+                assert_close_scaled(host(b), bo, bsc + 1e-300, what="rhs")
+            else:
+                assert torch.equal(v, ref[0]) and torch.equal(b, ref[1]), (path, te, fk)
+    fa.fem_pattern_force_path(p, fa.FEM_PATH_TWO_PASS)
+    assert fa.fem_pattern_value_path(p)["path"] == "two_pass"
+    v2, _ = fa.assemble(p, dev(node), kd, fa.FEM_F_SINPROD, None, fa.FEM_DETERMINISTIC)
+    _, _, vo, so = oracle.assemble(d, node, elem, k)
+    assert_close_scaled(host(v2), vo, so)
+
+
+def test_long_rows_take_the_tile_path():
+    """A vertex with 40 neighbours (row of 41 entries) is beyond the owner-computes records (32 per
+    row) but within the tile path's (256)."""
+    node, elem = _fan(40, 4)
+    p = fa.Pattern(dev(elem), node.shape[0])
+    fa.fem_pattern_set_locality(p, dev(node))
+    assert fa.fem_pattern_value_path(p)["path"] == "tiles"
+    v, b = fa.assemble(p, dev(node), None, fa.FEM_F_SINPROD, None, fa.FEM_DETERMINISTIC)
+    fa.get_error()
+    _, _, vo, so = oracle.assemble(2, node, elem, None)
+    assert_close_scaled(host(v), vo, so)
+    bo = oracle.rhs(2, node, elem, oracle.F_SINPROD)
+    assert_close_scaled(host(b), bo, np.abs(bo) + 1e-300, what="rhs")
+    with pytest.raises(fa.FemError) as e:
+        fa.fem_pattern_force_path(p, fa.FEM_PATH_BLOCKED)
+    assert e.value.code == fa.FEM_ERR_STATE
+
+
 def test_qp_values_rhs():
     d, node, elem, k, _ = mesh_case("sq37p")
     rng = np.random.default_rng(5)
