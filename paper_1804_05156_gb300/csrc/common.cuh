@@ -104,8 +104,7 @@ struct TilePlan {
   int32_t* ipos = nullptr;     // [(d+1)][NT] packet (incidence) index of (elist[j], i)
   void* pw = nullptr;          // [NT*(d+1)] per incidence: other columns' in-row positions (uint16 2-D, uint32 3-D)
   uint8_t* rdp = nullptr;      // [N] in-row position of the diagonal
-  float4* pk = nullptr;        // [NT*(d+1)][2] packets of float pairs
-  float2* pb = nullptr;        // [NT*(d+1)] 3-D load terms
+  float4* pk = nullptr;        // [NT*(d+1)][2] packets: four float pairs per incidence
 };
 void free_tile_plan(TilePlan& T);
 int build_tile_plan(const struct Pattern* P, const int32_t* order, int TE, TilePlan* out, cudaStream_t s);

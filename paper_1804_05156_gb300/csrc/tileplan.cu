@@ -130,7 +130,6 @@ void free_tile_plan(TilePlan& T) {
   cudaFree(T.pw);
   cudaFree(T.rdp);
   cudaFree(T.pk);
-  cudaFree(T.pb);
   T = TilePlan();
 }
 
@@ -214,10 +213,8 @@ int build_tile_plan(const Pattern* P, const int32_t* order, int TE, TilePlan* ou
                (uint32_t*)T.pw, T.rdp, dev_int + 1, dev_int);
   }
   FEM_LAUNCH(k_tile_max_v, grid_for(T.ntiles, 256), 256, 0, s, T.voff, T.ntiles, dev_int + 2);
-  // 5. packets: (d+1) float pairs per incidence (2-D: the row's 3 entries and its load term; 3-D: the
-  //    row's 4 entries, load terms separately)
+  // 5. packets: four float pairs (32 bytes) per incidence
   TP_TRY(cudaMallocAsync((void**)&T.pk, sizeof(float4) * 2 * total, s));
-  if (P->d == 3) TP_TRY(cudaMallocAsync((void**)&T.pb, sizeof(float2) * total, s));
   int hs[3] = {0, 0, 0};
   TP_TRY(cudaMemcpyAsync(hs, dev_int, sizeof(hs), cudaMemcpyDeviceToHost, s));
   TP_TRY(cudaStreamSynchronize(s));

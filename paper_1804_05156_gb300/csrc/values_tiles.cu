@@ -5,13 +5,14 @@
 //   tile's vertices are staged in shared memory once (exact three-float splits; for the 2-D
 //   sine-product load also sin/cos(pi x/2) per coordinate), then each thread computes one element's
 //   local stiffness and load entries (element_df.cuh: Sec. 3.1.3, eq. (dlambda), Sec. 3.2) and writes,
-//   for each local row i, one packet of float pairs to the slot of incidence (t, i):
-//     2-D: (a_ii, a_ij, a_ik, b_i);  3-D: (a_ii, a_ij, a_ik, a_il), b_i separately,
-//   with j < k < l the other local indices.
-// Phase 2 (k_row_gather): one thread per row. Its packets are contiguous (the incidence lists are
-//   sorted by element), so it reads them in order, adds the diagonal and load terms in registers and
-//   the off-diagonal terms in a per-warp shared-memory copy of the warp's 32 rows (CSR order), then
-//   the warp converts and writes its rows' values with coalesced stores.
+//   for each local row i, one 32-byte packet of float pairs to the slot of incidence (t, i):
+//     2-D: (a_ii, a_ij, a_ik, b_i);  3-D: (a_ij, a_ik, a_il, b_i),
+//   with j < k < l the other local indices. The 3-D diagonal is re-formed from the packet in phase 2
+//   exactly as the element routine forms it (a_ii = ((0 - a_ij) - a_ik) - a_il), so it costs no bytes.
+// Phase 2 (k_row_gather): one thread per row, one warp per 32 consecutive rows. A row's packets are
+//   contiguous (the incidence lists are sorted by row, then element). Each thread adds its row's
+//   diagonal and load terms in registers and the off-diagonal terms in the warp's shared-memory copy
+//   of its 32 rows (CSR order); the warp then converts and writes the rows with coalesced stores.
 // Every CSR entry is the float-float sum of its element contributions in ascending element order,
 // rounded to double once, whatever the tile size: the same bits as the owner-computes kernel.
 #include <cuda_runtime.h>
@@ -33,12 +34,13 @@ struct TileArgs {
   const int32_t* vlist;
   const int32_t* ipos;
   float4* pk;
-  float2* pb;
   int xs_bytes;
 };
 
+// 3-D: registers capped so that 768 threads (six 128-thread tiles) fit an SM; a few spilled bytes cost
+// less than the lost occupancy.
 template <int D, int TE>
-__global__ void __launch_bounds__(TE) k_tile_elements(TileArgs a, const double* __restrict__ node,
+__global__ void __launch_bounds__(TE, (D == 3 ? 768 : TE) / TE) k_tile_elements(TileArgs a, const double* __restrict__ node,
                                                       const double* __restrict__ k, int f_kind,
                                                       const double* __restrict__ f_arg, int want_a, int want_b,
                                                       const float4* __restrict__ tab, int* __restrict__ err) {
@@ -53,12 +55,15 @@ __global__ void __launch_bounds__(TE) k_tile_elements(TileArgs a, const double* 
   const int64_t j = (int64_t)tile * TE + threadIdx.x;
   const bool act = j < a.NT;
   int t = 0;
-  int lv[D1];
+  int lv[D1], qi[D1];
   double kd = 1.0;
   if (act) {
     t = __ldg(a.elist + j);
 #pragma unroll
-    for (int i = 0; i < D1; ++i) lv[i] = __ldg(a.lelem + (int64_t)i * a.NT + j);
+    for (int i = 0; i < D1; ++i) {
+      lv[i] = __ldg(a.lelem + (int64_t)i * a.NT + j);
+      qi[i] = __ldg(a.ipos + (int64_t)i * a.NT + j);
+    }
     if (k && want_a) kd = __ldg(k + t);
   }
   for (int v = threadIdx.x; v < nv; v += TE) {
@@ -93,30 +98,49 @@ __global__ void __launch_bounds__(TE) k_tile_elements(TileArgs a, const double* 
   if (!ok) report(err, FEM_ERR_DEGENERATE);
 #pragma unroll
   for (int i = 0; i < D1; ++i) {
-    const int64_t q = __ldg(a.ipos + (int64_t)i * a.NT + j);
-    df2 o[D1];  // a_ii, then a_ij for j != i ascending
-    o[0] = L.a[pidx<D>(i, i)];
-    int c = 1;
+    df2 o[D1];  // 2-D: a_ii, a_ij, a_ik; 3-D: a_ij, a_ik, a_il (j < k < l, the other local indices)
+    int c = 0;
+    if constexpr (D == 2) o[c++] = L.a[pidx<D>(i, i)];
 #pragma unroll
     for (int jj = 0; jj < D1; ++jj)
       if (jj != i) o[c++] = L.a[pidx<D>(i, jj)];
-    float4* dst = a.pk + 2 * q;
+    float4* dst = a.pk + 2 * (size_t)qi[i];
     dst[0] = make_float4(o[0].h, o[0].l, o[1].h, o[1].l);
-    if constexpr (D == 2) {
-      dst[1] = make_float4(o[2].h, o[2].l, L.bt[i].h, L.bt[i].l);
-    } else {
-      dst[1] = make_float4(o[2].h, o[2].l, o[3].h, o[3].l);
-      a.pb[q] = make_float2(L.bt[i].h, L.bt[i].l);
-    }
+    dst[1] = make_float4(o[2].h, o[2].l, L.bt[i].h, L.bt[i].l);
   }
 }
 
+// One packet into a row's sums: the diagonal and load terms in registers, the off-diagonal terms in the
+// warp's shared-memory copy of its rows. w holds the in-row positions of the other columns, 8 bits each.
+template <int D>
+__device__ __forceinline__ void add_packet(const float4& p0, const float4& p1, uint32_t w, int o, df2* acc, df2& dacc,
+                                           df2& bacc, bool want_a, bool want_b) {
+  if (want_a) {
+    const int c0 = o + (int)(w & 0xffu), c1 = o + (int)((w >> 8) & 0xffu);
+    if constexpr (D == 2) {
+      dacc = df_acc(dacc, df2{p0.x, p0.y});
+      acc[c0] = df_acc(acc[c0], df2{p0.z, p0.w});
+      acc[c1] = df_acc(acc[c1], df2{p1.x, p1.y});
+    } else {
+      const df2 o1 = {p0.x, p0.y}, o2 = {p0.z, p0.w}, o3 = {p1.x, p1.y};
+      const int c2 = o + (int)((w >> 16) & 0xffu);
+      dacc = df_acc(dacc, df_sub(df_sub(df_sub(df2{0.0f, 0.0f}, o1), o2), o3));
+      acc[c0] = df_acc(acc[c0], o1);
+      acc[c1] = df_acc(acc[c1], o2);
+      acc[c2] = df_acc(acc[c2], o3);
+    }
+  }
+  if (want_b) bacc = df_acc(bacc, df2{p1.z, p1.w});
+}
+
+// One thread per row, one warp per 32 consecutive rows. A row's packets are contiguous; each thread
+// loads U of them before adding them in order, so several loads are in flight per thread.
 template <int D, typename PW>
 __global__ void __launch_bounds__(256) k_row_gather(int64_t N, int max_row, const int32_t* __restrict__ row_ptr,
                                                     const int32_t* __restrict__ inc_ptr, const PW* __restrict__ pw,
                                                     const uint8_t* __restrict__ rdp, const float4* __restrict__ pk,
-                                                    const float2* __restrict__ pb, double* __restrict__ val,
-                                                    double* __restrict__ bvec) {
+                                                    double* __restrict__ val, double* __restrict__ bvec) {
+  constexpr int U = (D == 2) ? 2 : 4;
   extern __shared__ __align__(16) unsigned char sm[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   df2* acc = reinterpret_cast<df2*>(sm) + (size_t)wid * 32 * max_row;
@@ -127,7 +151,8 @@ __global__ void __launch_bounds__(256) k_row_gather(int64_t N, int max_row, cons
   const int64_t Rend = (R0 + 32 < N) ? R0 + 32 : N;
   const int base = __ldg(row_ptr + R0);
   const int region = __ldg(row_ptr + Rend) - base;
-  if (val)
+  const bool want_a = val != nullptr, want_b = bvec != nullptr;
+  if (want_a)
     for (int x = lane; x < region; x += 32) acc[x] = df2{0.0f, 0.0f};
   __syncwarp();
   if (act) {
@@ -135,41 +160,35 @@ __global__ void __launch_bounds__(256) k_row_gather(int64_t N, int max_row, cons
     const int o = rp - base;
     df2 dacc = {0.0f, 0.0f}, bacc = {0.0f, 0.0f};
     const int q1 = __ldg(inc_ptr + R + 1);
-    for (int q = __ldg(inc_ptr + R); q < q1; ++q) {
-      const float4 p1 = __ldg(pk + 2 * (size_t)q + 1);
-      if (val) {
-        const float4 p0 = __ldg(pk + 2 * (size_t)q);
-        const uint32_t w = (uint32_t)__ldg(pw + q);
-        dacc = df_acc(dacc, df2{p0.x, p0.y});
-        const int c0 = o + (int)(w & 0xffu), c1 = o + (int)((w >> 8) & 0xffu);
-        acc[c0] = df_acc(acc[c0], df2{p0.z, p0.w});
-        acc[c1] = df_acc(acc[c1], df2{p1.x, p1.y});
-        if constexpr (D == 3) {
-          const int c2 = o + (int)((w >> 16) & 0xffu);
-          acc[c2] = df_acc(acc[c2], df2{p1.z, p1.w});
-        }
+    int q = __ldg(inc_ptr + R);
+    for (; q + U - 1 < q1; q += U) {
+      float4 x0[U], x1[U];
+      uint32_t w[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        x0[u] = __ldg(pk + 2 * (size_t)(q + u));
+        x1[u] = __ldg(pk + 2 * (size_t)(q + u) + 1);
+        w[u] = (uint32_t)__ldg(pw + q + u);
       }
-      if (bvec) {
-        if constexpr (D == 2) {
-          bacc = df_acc(bacc, df2{p1.z, p1.w});
-        } else {
-          const float2 x = __ldg(pb + q);
-          bacc = df_acc(bacc, df2{x.x, x.y});
-        }
-      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) add_packet<D>(x0[u], x1[u], w[u], o, acc, dacc, bacc, want_a, want_b);
     }
-    if (val && rl > 0) acc[o + __ldg(rdp + R)] = dacc;
-    if (bvec) bvec[R] = df_to_double(bacc);
+    for (; q < q1; ++q)
+      add_packet<D>(__ldg(pk + 2 * (size_t)q), __ldg(pk + 2 * (size_t)q + 1), (uint32_t)__ldg(pw + q), o, acc, dacc,
+                    bacc, want_a, want_b);
+    if (want_a && rl > 0) acc[o + __ldg(rdp + R)] = dacc;
+    if (want_b) bvec[R] = df_to_double(bacc);
   }
   __syncwarp();
-  if (val)
+  if (want_a)
     for (int x = lane; x < region; x += 32) val[base + x] = df_to_double(acc[x]);
 }
 
-// rows per CTA of the gather: warps whose row copies fit a modest shared-memory budget
+__host__ __device__ constexpr int gather_warp_bytes(int max_row) { return 32 * max_row * (int)sizeof(df2); }
+
+// warps per CTA of the gather: as many (up to 8) as fit 48 KB of row copies
 int gather_warps(int max_row) {
-  const int per_warp = 32 * (max_row > 0 ? max_row : 1) * (int)sizeof(df2);
-  int w = (96 * 1024) / per_warp;
+  const int w = (48 * 1024) / gather_warp_bytes(max_row > 0 ? max_row : 1);
   return w < 1 ? 1 : (w > 8 ? 8 : w);
 }
 
@@ -201,7 +220,6 @@ int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_
   a.vlist = T.vlist;
   a.ipos = T.ipos;
   a.pk = T.pk;
-  a.pb = T.pb;
   a.xs_bytes = ((T.max_v * D * (int)sizeof(f3)) + 15) / 16 * 16;
   const int want_a = val != nullptr, want_b = b != nullptr;
   const int smem = tile_smem_need(T, D, f_kind == FEM_F_SINPROD && want_b);
@@ -219,20 +237,19 @@ int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_
     else FEM_TILE_LAUNCH(3, 256);
   }
 #undef FEM_TILE_LAUNCH
-  const int wpc = gather_warps(T.max_row);
+  const int mr = T.max_row > 0 ? T.max_row : 1;
+  const int wpc = gather_warps(mr);
   const int bt = 32 * wpc;
-  const int gsm = wpc * 32 * (T.max_row > 0 ? T.max_row : 1) * (int)sizeof(df2);
+  const int gsm = wpc * gather_warp_bytes(mr);
   const int64_t grid = (P->N + bt - 1) / bt;
   if (D == 2) {
-    if (gsm > 48 * 1024)
-      FEM_CUDA(cudaFuncSetAttribute(k_row_gather<2, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm));
-    FEM_LAUNCH((k_row_gather<2, uint16_t>), (int)grid, bt, gsm, s, P->N, T.max_row, P->row_ptr, P->inc_ptr,
-               (const uint16_t*)T.pw, T.rdp, T.pk, T.pb, val, b);
+    FEM_CUDA(cudaFuncSetAttribute(k_row_gather<2, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm));
+    FEM_LAUNCH((k_row_gather<2, uint16_t>), (int)grid, bt, gsm, s, P->N, mr, P->row_ptr, P->inc_ptr,
+               (const uint16_t*)T.pw, T.rdp, T.pk, val, b);
   } else {
-    if (gsm > 48 * 1024)
-      FEM_CUDA(cudaFuncSetAttribute(k_row_gather<3, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm));
-    FEM_LAUNCH((k_row_gather<3, uint32_t>), (int)grid, bt, gsm, s, P->N, T.max_row, P->row_ptr, P->inc_ptr,
-               (const uint32_t*)T.pw, T.rdp, T.pk, T.pb, val, b);
+    FEM_CUDA(cudaFuncSetAttribute(k_row_gather<3, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm));
+    FEM_LAUNCH((k_row_gather<3, uint32_t>), (int)grid, bt, gsm, s, P->N, mr, P->row_ptr, P->inc_ptr,
+               (const uint32_t*)T.pw, T.rdp, T.pk, val, b);
   }
   return FEM_OK;
 }
