@@ -96,21 +96,25 @@ int fem_pattern_force_launch(fem_pattern_t p, int threads, int ctas_per_sm, int 
  *   FEM_PATH_TILES    elements computed once per tile of 128 or 256 elements in locality order, each
  *                     row's local entries written as packets to the row's incidence slots, then one
  *                     thread per row sums its packets (two launches; float-float arithmetic);
+ *   FEM_PATH_TILES_FUSED  the same two phases in one cooperative launch of resident CTAs, tiles and
+ *                     row groups taken from device counters, a grid-wide barrier between the phases;
  *   FEM_PATH_BLOCKED  owner-computes blocks of rows, elements on block boundaries computed by every
  *                     block they touch, sums formed in shared memory (one launch; float-float);
  *   FEM_PATH_TWO_PASS per-element FP64 values to scratch, then a per-slot FP64 reduction.
- * TILES and BLOCKED give identical bits. fem_pattern_set_locality times TILES (both tile sizes)
- * against the best BLOCKED launch and keeps the faster; without coordinates TILES (256) is used. */
+ * TILES, TILES_FUSED and BLOCKED give identical bits. fem_pattern_set_locality times TILES and
+ * TILES_FUSED (both tile sizes) against the best BLOCKED launch and keeps the fastest; without
+ * coordinates TILES (256) is used. A batch (fem_batch_*) considers the one-launch forms only. */
 #define FEM_PATH_TWO_PASS 0
 #define FEM_PATH_BLOCKED 1
 #define FEM_PATH_TILES 2
+#define FEM_PATH_TILES_FUSED 3
 /* The path fem_assemble(FEM_DETERMINISTIC) takes, the tile size (0 unless TILES) and the tuner's time
  * for it in ms (0 when not tuned). Outputs are host pointers, nullable. */
 int fem_pattern_value_path(fem_pattern_t p, int* path, int* tile_elems, float* tuned_ms);
 /* Select the path: TWO_PASS drops both plans; BLOCKED needs the blocked plan (FEM_ERR_STATE if the
- * mesh has none); TILES builds the tile plan for tile_elems (128 or 256) if it is not the current one
- * (synchronises `stream`; FEM_ERR_STATE if a row has more than 256 entries). fem_pattern_force_launch
- * selects BLOCKED. */
+ * mesh has none); TILES and TILES_FUSED build the tile plan for tile_elems (128 or 256) if it is not
+ * the current one (synchronises `stream`; FEM_ERR_STATE if a row has more than 256 entries, or for
+ * TILES_FUSED if its shared memory does not fit). fem_pattern_force_launch selects BLOCKED. */
 int fem_pattern_force_path(fem_pattern_t p, int path, int tile_elems, fem_stream_t stream);
 
 /* Sizes and library-owned device arrays of a pattern (valid until fem_pattern_destroy):
@@ -144,7 +148,9 @@ int fem_assemble_rhs(fem_pattern_t p, const double* node, int f_kind, const doub
  * the side opposite vertex i (2-D: vertices (i+1, i+2) mod 3; 3-D: faces [2 4 3], [1 3 4],
  * [1 4 2], [1 2 3] in the paper's 1-based numbering). With bdflag [NT][d+1] (int8), Dirichlet
  * sides are those with bdflag == 1. With bdflag == NULL every side that belongs to exactly one
- * element is Dirichlet ("whole boundary"). */
+ * element is Dirichlet ("whole boundary"); that mask depends on the topology only, so the first such
+ * call finds it (one pass over the sides) and keeps it in the pattern (N bytes), and later calls copy
+ * it. */
 int fem_boundary_nodes(fem_pattern_t p, const int8_t* bdflag, uint8_t* is_bd, fem_stream_t stream);
 
 /* ---- Dirichlet (Sec. 3.3) ------------------------------------------------------------------------

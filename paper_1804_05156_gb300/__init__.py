@@ -21,7 +21,7 @@ FEM_ERR_ARG, FEM_ERR_INDEX, FEM_ERR_DEGENERATE, FEM_ERR_CUDA, FEM_ERR_OOM, FEM_E
     -1, -2, -3, -4, -5, -6, -7)
 FEM_DETERMINISTIC, FEM_ATOMIC = 0, 1
 FEM_F_CONST, FEM_F_SINPROD, FEM_F_QPVALUES = 0, 1, 2
-FEM_PATH_TWO_PASS, FEM_PATH_BLOCKED, FEM_PATH_TILES = 0, 1, 2
+FEM_PATH_TWO_PASS, FEM_PATH_BLOCKED, FEM_PATH_TILES, FEM_PATH_TILES_FUSED = 0, 1, 2, 3
 
 _lib = None
 
@@ -192,10 +192,11 @@ def fem_pattern_force_launch(p: Pattern, threads: int, ctas_per_sm: int, persist
 
 
 def fem_pattern_value_path(p: Pattern) -> dict:
-    """The deterministic value path of the pattern: {"path": "tiles"|"blocked"|"two_pass", "tile_elems", "tuned_ms"}."""
+    """The deterministic value path: {"path": "tiles"|"tiles_fused"|"blocked"|"two_pass", "tile_elems", "tuned_ms"}."""
     pa, te, ms = C.c_int(), C.c_int(), C.c_float()
     _check(lib().fem_pattern_value_path(p.handle, C.byref(pa), C.byref(te), C.byref(ms)))
-    names = {FEM_PATH_TWO_PASS: "two_pass", FEM_PATH_BLOCKED: "blocked", FEM_PATH_TILES: "tiles"}
+    names = {FEM_PATH_TWO_PASS: "two_pass", FEM_PATH_BLOCKED: "blocked", FEM_PATH_TILES: "tiles",
+             FEM_PATH_TILES_FUSED: "tiles_fused"}
     return {"path": names[pa.value], "tile_elems": te.value, "tuned_ms": ms.value}
 
 

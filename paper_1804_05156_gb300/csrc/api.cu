@@ -107,6 +107,7 @@ void free_pattern(Pattern& P) {
   cudaFree(P.inc);
   cudaFree(P.scratch);
   cudaFree(P.work_counter);
+  cudaFree(P.bd_whole);
   P = Pattern();
 }
 
@@ -149,7 +150,7 @@ int fem_mesh_build_pattern(int d, int64_t N, int64_t NT, const int32_t* elem, fe
     return set_error(FEM_ERR_OOM, "cannot allocate the device error word");
   }
   int rc = fem::build_pattern(&P, elem, s);
-  if (rc == FEM_OK && cudaMalloc((void**)&P.work_counter, sizeof(int)) != cudaSuccess) {
+  if (rc == FEM_OK && cudaMalloc((void**)&P.work_counter, 4 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     P.work_counter = nullptr;
     rc = set_error(FEM_ERR_OOM, "work counter allocation failed");
@@ -212,12 +213,13 @@ int fem_pattern_force_launch(fem_pattern_t p, int threads, int ctas_per_sm, int 
 int fem_pattern_value_path(fem_pattern_t p, int* path, int* tile_elems, float* tuned_ms) {
   if (!p) return set_error(FEM_ERR_ARG, "null pattern");
   const Pattern& P = p->P;
-  const int pth = P.use_tiles ? FEM_PATH_TILES : (P.blk.ok ? FEM_PATH_BLOCKED : FEM_PATH_TWO_PASS);
+  const int pth = P.use_tiles ? (P.tile.fused ? FEM_PATH_TILES_FUSED : FEM_PATH_TILES)
+                              : (P.blk.ok ? FEM_PATH_BLOCKED : FEM_PATH_TWO_PASS);
   if (path) *path = pth;
   if (tile_elems) *tile_elems = P.use_tiles ? P.tile.TE : 0;
   if (tuned_ms) {
     *tuned_ms = 0.0f;
-    if (pth == FEM_PATH_TILES && P.tile.tuned_ms < 1e29f) *tuned_ms = P.tile.tuned_ms;
+    if ((pth == FEM_PATH_TILES || pth == FEM_PATH_TILES_FUSED) && P.tile.tuned_ms < 1e29f) *tuned_ms = P.tile.tuned_ms;
     if (pth == FEM_PATH_BLOCKED) *tuned_ms = P.blk.tuned_ms;
   }
   return FEM_OK;
@@ -237,7 +239,7 @@ int fem_pattern_force_path(fem_pattern_t p, int path, int tile_elems, fem_stream
     P.use_tiles = false;
     return FEM_OK;
   }
-  if (path != FEM_PATH_TILES) return set_error(FEM_ERR_ARG, "unknown value path %d", path);
+  if (path != FEM_PATH_TILES && path != FEM_PATH_TILES_FUSED) return set_error(FEM_ERR_ARG, "unknown value path %d", path);
   if (tile_elems != 128 && tile_elems != 256) return set_error(FEM_ERR_ARG, "tile size must be 128 or 256");
   if (!(P.tile.ok && P.tile.TE == tile_elems)) {
     fem::TilePlan T;
@@ -250,6 +252,10 @@ int fem_pattern_force_path(fem_pattern_t p, int path, int tile_elems, fem_stream
     fem::free_tile_plan(P.tile);
     P.tile = T;
   }
+  const bool fused = path == FEM_PATH_TILES_FUSED;
+  if (fused && fem::tile_fused_smem(P.tile, P.d) == 0)
+    return set_error(FEM_ERR_STATE, "the fused tile launch does not fit this mesh in shared memory");
+  P.tile.fused = fused;
   P.use_tiles = true;
   return FEM_OK;
 }

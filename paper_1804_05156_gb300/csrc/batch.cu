@@ -137,6 +137,9 @@ int fem_batch_plan(int d, int B, const int64_t* N, const int64_t* NT, const int3
     delete h;
     return rc;
   }
+  // the batch runs in one launch (the fused tile form or the persistent blocked form)
+  h->pat->P.one_launch = true;
+  fem::enforce_one_launch(&h->pat->P);
   // nnz offsets: row_ptr at the mesh boundaries
   h->nnz_off.assign(B + 1, 0);
   std::vector<int32_t> rp((size_t)Ntot + 1);

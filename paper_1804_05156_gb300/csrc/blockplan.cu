@@ -405,6 +405,7 @@ int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group
     } else {
       free_tile_plan(T);
     }
+    enforce_one_launch(P);
     return FEM_OK;
   }
   // With coordinates: time every feasible (block size, launch shape) on the device, keep the fastest.
@@ -432,7 +433,7 @@ int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group
     rc = build_block_plan(P, node_hint, group, Vs[vi], &B, s);
     if (rc) break;
     bool kept = false;
-    for (int si = 0; si < 2 * nshapes && B.ok; ++si) {
+    for (int si = P->one_launch ? nshapes : 0; si < 2 * nshapes && B.ok; ++si) {
       B.threads = shapes[si % nshapes][0];
       B.minb = shapes[si % nshapes][1];
       B.persistent = si >= nshapes;
@@ -460,8 +461,8 @@ int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group
     }
     if (!kept) free_block_plan(B);
   }
-  // The two-phase path on the chosen vertex order: time each tile size, keep the fastest if it beats
-  // the blocked plan.
+  // The two-phase path on the chosen vertex order: time each tile size in both launch forms (two
+  // launches, or one fused cooperative launch), keep the fastest if it beats the blocked plan.
   TilePlan bestT;
   for (int ti = 0; ti < 2 && rc == FEM_OK; ++ti) {
     const int TEs[] = {256, 128};
@@ -472,25 +473,36 @@ int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group
       free_tile_plan(T);
       continue;
     }
-    Pattern Q = *P;
-    Q.tile = T;
-    const int fk = sinprod ? FEM_F_SINPROD : FEM_F_CONST;
-    rc = assemble_tiles(&Q, node_hint, nullptr, fk, nullptr, val, bb, s);  // warm-up
-    if (rc == FEM_OK) {
-      cudaEventRecord(e0, s);
-      for (int r = 0; r < 3 && rc == FEM_OK; ++r) rc = assemble_tiles(&Q, node_hint, nullptr, fk, nullptr, val, bb, s);
-      cudaEventRecord(e1, s);
-      if (cudaEventSynchronize(e1) != cudaSuccess) rc = cuda_error(cudaGetLastError(), "tuning run");
+    float t_best = 1e30f;
+    bool f_best = false;
+    for (int fu = P->one_launch ? 1 : 0; fu < 2 && rc == FEM_OK; ++fu) {
+      T.fused = fu == 1;
+      if (T.fused && tile_fused_smem(T, d) == 0) continue;
+      Pattern Q = *P;
+      Q.tile = T;
+      const int fk = sinprod ? FEM_F_SINPROD : FEM_F_CONST;
+      rc = assemble_tiles(&Q, node_hint, nullptr, fk, nullptr, val, bb, s);  // warm-up
+      if (rc == FEM_OK) {
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3 && rc == FEM_OK; ++r) rc = assemble_tiles(&Q, node_hint, nullptr, fk, nullptr, val, bb, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = cuda_error(cudaGetLastError(), "tuning run");
+      }
+      if (rc == FEM_OK) {
+        float ms = 1e30f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 3.0f;
+        if (ms < t_best) {
+          t_best = ms;
+          f_best = T.fused;
+        }
+      }
     }
-    float ms = 1e30f;
-    if (rc == FEM_OK) {
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms /= 3.0f;
-    }
-    if (rc == FEM_OK && ms < bestT.tuned_ms) {
+    T.fused = f_best;
+    if (rc == FEM_OK && t_best < bestT.tuned_ms) {
       free_tile_plan(bestT);
       bestT = T;
-      bestT.tuned_ms = ms;
+      bestT.tuned_ms = t_best;
     } else {
       free_tile_plan(T);
     }
@@ -507,13 +519,26 @@ int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group
     return rc;
   }
   if (best.order) P->blk = best;
-  if (bestT.ok && (!best.order || bestT.tuned_ms < best_ms)) {
+  if (bestT.ok && bestT.tuned_ms < 1e29f && (!best.order || bestT.tuned_ms < best_ms)) {
     P->tile = bestT;
     P->use_tiles = true;
   } else {
     free_tile_plan(bestT);
   }
+  enforce_one_launch(P);
   return FEM_OK;
+}
+
+void enforce_one_launch(Pattern* P) {
+  if (!P->one_launch) return;
+  if (P->use_tiles && !P->tile.fused) {
+    if (tile_fused_smem(P->tile, P->d) != 0) {
+      P->tile.fused = true;
+      return;
+    }
+    P->use_tiles = false;
+  }
+  if (!P->use_tiles && P->blk.ok) P->blk.persistent = true;
 }
 
 }  // namespace fem

@@ -96,13 +96,27 @@ __global__ void k_free_scatter(const uint8_t* __restrict__ is_bd, const int32_t*
 
 }  // namespace
 
-int boundary_nodes(const Pattern* P, const int8_t* bdflag, uint8_t* is_bd, cudaStream_t s) {
-  if (P->N > 0) FEM_CUDA(cudaMemsetAsync(is_bd, 0, (size_t)P->N, s));
+int boundary_nodes(Pattern* P, const int8_t* bdflag, uint8_t* is_bd, cudaStream_t s) {
   const int64_t total = P->NT * P->d1;
-  if (bdflag)
+  if (bdflag) {
+    if (P->N > 0) FEM_CUDA(cudaMemsetAsync(is_bd, 0, (size_t)P->N, s));
     FEM_LAUNCH(k_mark_flagged, grid_for(total, 256), 256, 0, s, P->elem, bdflag, P->NT, P->d, is_bd);
-  else
-    FEM_LAUNCH(k_mark_unshared, grid_for(total, 256), 256, 0, s, P->elem, P->NT, P->d, P->inc_ptr, P->inc, is_bd);
+    return FEM_OK;
+  }
+  if (P->N == 0) return FEM_OK;
+  // The whole-boundary mask depends on the topology only: found on the first call, then copied.
+  if (!P->bd_whole) {
+    uint8_t* m = nullptr;
+    FEM_CUDA(cudaMalloc((void**)&m, (size_t)P->N));
+    cudaError_t e = cudaMemsetAsync(m, 0, (size_t)P->N, s);
+    if (e != cudaSuccess) {
+      cudaFree(m);
+      return cuda_error(e, "cudaMemsetAsync");
+    }
+    FEM_LAUNCH(k_mark_unshared, grid_for(total, 256), 256, 0, s, P->elem, P->NT, P->d, P->inc_ptr, P->inc, m);
+    P->bd_whole = m;
+  }
+  FEM_CUDA(cudaMemcpyAsync(is_bd, P->bd_whole, (size_t)P->N, cudaMemcpyDeviceToDevice, s));
   return FEM_OK;
 }
 

@@ -97,6 +97,7 @@ struct TilePlan {
   int max_v = 0, max_row = 0;  // most vertices of one tile; longest row
   bool ok = false;             // local ids fit 16 bits and rows have <= 256 entries
   float tuned_ms = 1e30f;      // the tuner's time for this plan (1e30 if not timed)
+  bool fused = false;          // both phases in one cooperative launch (k_tiles_fused)
   int32_t* elist = nullptr;    // [NT] caller element ids in tile order
   uint16_t* lelem = nullptr;   // [(d+1)][NT] local vertex ids, tile order
   int32_t* voff = nullptr;     // [ntiles+1] vertex-list offsets
@@ -125,16 +126,22 @@ struct Pattern {
   BlockPlan blk;               // owner-computes locality plan (blk.ok == false: two-pass path only)
   TilePlan tile;               // two-phase plan (tile.ok == false: not available)
   bool use_tiles = false;      // the deterministic value path runs the two-phase kernels
-  int* work_counter = nullptr; // device counter of the persistent launch
+  bool one_launch = false;     // plans must run in a single launch (batched assembly under a graph)
+  int* work_counter = nullptr; // [4] device counters: [0] blocked persistent launch, [1..3] fused tile launch
+  uint8_t* bd_whole = nullptr;  // [N] whole-boundary vertex mask, computed on first request
 };
 // (Re)build P->blk, halving the block size until the packed limits hold (blk.ok false if they never do).
 int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group, cudaStream_t s);
+// For a pattern that must run in one launch: switch the tile plan to its fused form, or fall back to the
+// persistent blocked launch.
+void enforce_one_launch(Pattern* P);
 int blocked_smem_budget(int ctas_per_sm);
 int blocked_smem_need(const BlockPlan& B, int d, bool sinprod);
 int assemble_blocked(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg,
                      double* val, double* b, cudaStream_t s);
 int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg, double* val,
                    double* b, cudaStream_t s);
+int tile_fused_smem(const TilePlan& T, int d);  // 0: the fused launch does not fit
 
 // scratch doubles per element: stiffness unique entries + rhs entries (+ gradient entries)
 inline int64_t scratch_per_elem(int d) { return d == 2 ? 9 : 14; }
@@ -151,7 +158,7 @@ int assemble_values(const Pattern* P, const double* node, const double* k, int f
 int assemble_values_two_pass(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg,
                               double* val, double* b, double* scratch, int* err, cudaStream_t s);
 int* device_error_word_if_ready();  // the current device's error word, or nullptr if never allocated
-int boundary_nodes(const Pattern* P, const int8_t* bdflag, uint8_t* is_bd, cudaStream_t s);
+int boundary_nodes(Pattern* P, const int8_t* bdflag, uint8_t* is_bd, cudaStream_t s);
 int apply_dirichlet(const Pattern* P, const uint8_t* is_bd, const double* gD, double* val, double* b,
                     int32_t* free_node, int64_t* n_free, cudaStream_t s);
 struct BatchPlan;

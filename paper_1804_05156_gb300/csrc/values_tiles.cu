@@ -13,9 +13,15 @@
 //   contiguous (the incidence lists are sorted by row, then element). Each thread adds its row's
 //   diagonal and load terms in registers and the off-diagonal terms in the warp's shared-memory copy
 //   of its 32 rows (CSR order); the warp then converts and writes the rows with coalesced stores.
+// Fused form (k_tiles_fused): both phases in one cooperative launch of resident CTAs. Tiles, then
+//   groups of rows, are taken from device counters; between the phases a grid-wide barrier (an
+//   arrival counter, polled with a bounded wait) orders every packet write before any read.
 // Every CSR entry is the float-float sum of its element contributions in ascending element order,
-// rounded to double once, whatever the tile size: the same bits as the owner-computes kernel.
+// rounded to double once, whatever the tile size or launch form: the same bits as the owner-computes
+// kernel.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "element_df.cuh"
@@ -28,6 +34,7 @@ namespace {
 
 struct TileArgs {
   int64_t NT;
+  int ntiles;
   const int32_t* elist;
   const uint16_t* lelem;
   const int32_t* voff;
@@ -37,18 +44,25 @@ struct TileArgs {
   int xs_bytes;
 };
 
-// 3-D: registers capped so that 768 threads (six 128-thread tiles) fit an SM; a few spilled bytes cost
-// less than the lost occupancy.
+struct RowArgs {
+  int64_t N;
+  int max_row;
+  const int32_t* row_ptr;
+  const int32_t* inc_ptr;
+  const void* pw;
+  const uint8_t* rdp;
+  const float4* pk;
+};
+
+// Phase 1 for one tile (all TE threads of the CTA; one __syncthreads inside).
 template <int D, int TE>
-__global__ void __launch_bounds__(TE, (D == 3 ? 768 : TE) / TE) k_tile_elements(TileArgs a, const double* __restrict__ node,
-                                                      const double* __restrict__ k, int f_kind,
-                                                      const double* __restrict__ f_arg, int want_a, int want_b,
-                                                      const float4* __restrict__ tab, int* __restrict__ err) {
+__device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, unsigned char* sm,
+                                                 const double* __restrict__ node, const double* __restrict__ k,
+                                                 int f_kind, const double* __restrict__ f_arg, int want_a, int want_b,
+                                                 const float4* __restrict__ tab, int* __restrict__ err) {
   constexpr int D1 = D + 1;
-  extern __shared__ __align__(16) unsigned char sm[];
   VtxDF<D>* xs = reinterpret_cast<VtxDF<D>*>(sm);
   SC* scs = reinterpret_cast<SC*>(sm + a.xs_bytes);
-  const int tile = blockIdx.x;
   const int v0 = __ldg(a.voff + tile), nv = __ldg(a.voff + tile + 1) - v0;
   const bool sinprod2 = (D == 2) && f_kind == FEM_F_SINPROD && want_b;
   // element data first: its loads are in flight during the vertex staging
@@ -133,55 +147,129 @@ __device__ __forceinline__ void add_packet(const float4& p0, const float4& p1, u
   if (want_b) bacc = df_acc(bacc, df2{p1.z, p1.w});
 }
 
-// One thread per row, one warp per 32 consecutive rows. A row's packets are contiguous; each thread
-// loads U of them before adding them in order, so several loads are in flight per thread.
-template <int D, typename PW>
-__global__ void __launch_bounds__(256) k_row_gather(int64_t N, int max_row, const int32_t* __restrict__ row_ptr,
-                                                    const int32_t* __restrict__ inc_ptr, const PW* __restrict__ pw,
-                                                    const uint8_t* __restrict__ rdp, const float4* __restrict__ pk,
-                                                    double* __restrict__ val, double* __restrict__ bvec) {
+// packet load: read-only path in the two-launch form; L2 (coherent) path when the packets were written
+// earlier in the same launch
+template <bool FRESH>
+__device__ __forceinline__ float4 load_packet_half(const float4* p) {
+  if constexpr (FRESH) return __ldcg(p);
+  else return __ldg(p);
+}
+
+// Phase 2 for the 32 rows R0 .. R0+31 of one warp. A row's packets are contiguous; each thread loads U
+// of them before adding them in order, so several loads are in flight per thread.
+template <int D, typename PW, bool FRESH>
+__device__ __forceinline__ void rows_of_warp(const RowArgs& g, int64_t R0, df2* acc, double* __restrict__ val,
+                                             double* __restrict__ bvec) {
   constexpr int U = (D == 2) ? 2 : 4;
-  extern __shared__ __align__(16) unsigned char sm[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  df2* acc = reinterpret_cast<df2*>(sm) + (size_t)wid * 32 * max_row;
-  const int64_t R0 = (int64_t)blockIdx.x * blockDim.x + wid * 32;
-  if (R0 >= N) return;  // whole warp
+  const PW* __restrict__ pw = static_cast<const PW*>(g.pw);
+  const int lane = threadIdx.x & 31;
   const int64_t R = R0 + lane;
-  const bool act = R < N;
-  const int64_t Rend = (R0 + 32 < N) ? R0 + 32 : N;
-  const int base = __ldg(row_ptr + R0);
-  const int region = __ldg(row_ptr + Rend) - base;
+  const bool act = R < g.N;
+  const int64_t Rend = (R0 + 32 < g.N) ? R0 + 32 : g.N;
+  const int base = __ldg(g.row_ptr + R0);
+  const int region = __ldg(g.row_ptr + Rend) - base;
   const bool want_a = val != nullptr, want_b = bvec != nullptr;
   if (want_a)
     for (int x = lane; x < region; x += 32) acc[x] = df2{0.0f, 0.0f};
   __syncwarp();
   if (act) {
-    const int rp = __ldg(row_ptr + R), rl = __ldg(row_ptr + R + 1) - rp;
+    const int rp = __ldg(g.row_ptr + R), rl = __ldg(g.row_ptr + R + 1) - rp;
     const int o = rp - base;
     df2 dacc = {0.0f, 0.0f}, bacc = {0.0f, 0.0f};
-    const int q1 = __ldg(inc_ptr + R + 1);
-    int q = __ldg(inc_ptr + R);
+    const int q1 = __ldg(g.inc_ptr + R + 1);
+    int q = __ldg(g.inc_ptr + R);
     for (; q + U - 1 < q1; q += U) {
       float4 x0[U], x1[U];
       uint32_t w[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        x0[u] = __ldg(pk + 2 * (size_t)(q + u));
-        x1[u] = __ldg(pk + 2 * (size_t)(q + u) + 1);
+        x0[u] = load_packet_half<FRESH>(g.pk + 2 * (size_t)(q + u));
+        x1[u] = load_packet_half<FRESH>(g.pk + 2 * (size_t)(q + u) + 1);
         w[u] = (uint32_t)__ldg(pw + q + u);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) add_packet<D>(x0[u], x1[u], w[u], o, acc, dacc, bacc, want_a, want_b);
     }
     for (; q < q1; ++q)
-      add_packet<D>(__ldg(pk + 2 * (size_t)q), __ldg(pk + 2 * (size_t)q + 1), (uint32_t)__ldg(pw + q), o, acc, dacc,
-                    bacc, want_a, want_b);
-    if (want_a && rl > 0) acc[o + __ldg(rdp + R)] = dacc;
+      add_packet<D>(load_packet_half<FRESH>(g.pk + 2 * (size_t)q), load_packet_half<FRESH>(g.pk + 2 * (size_t)q + 1),
+                    (uint32_t)__ldg(pw + q), o, acc, dacc, bacc, want_a, want_b);
+    if (want_a && rl > 0) acc[o + __ldg(g.rdp + R)] = dacc;
     if (want_b) bvec[R] = df_to_double(bacc);
   }
   __syncwarp();
   if (want_a)
     for (int x = lane; x < region; x += 32) val[base + x] = df_to_double(acc[x]);
+  __syncwarp();
+}
+
+// 3-D: registers capped so that 768 threads (six 128-thread tiles) fit an SM; a few spilled bytes cost
+// less than the lost occupancy.
+template <int D, int TE>
+__global__ void __launch_bounds__(TE, (D == 3 ? 768 : TE) / TE)
+    k_tile_elements(TileArgs a, const double* __restrict__ node, const double* __restrict__ k, int f_kind,
+                    const double* __restrict__ f_arg, int want_a, int want_b, const float4* __restrict__ tab,
+                    int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  elements_of_tile<D, TE>(a, blockIdx.x, sm, node, k, f_kind, f_arg, want_a, want_b, tab, err);
+}
+
+template <int D, typename PW>
+__global__ void __launch_bounds__(256) k_row_gather(RowArgs g, double* __restrict__ val, double* __restrict__ bvec) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int wid = threadIdx.x >> 5;
+  const int64_t R0 = (int64_t)blockIdx.x * blockDim.x + wid * 32;
+  if (R0 >= g.N) return;  // whole warp
+  rows_of_warp<D, PW, false>(g, R0, reinterpret_cast<df2*>(sm) + (size_t)wid * 32 * g.max_row, val, bvec);
+}
+
+constexpr int kBarrierPolls = 1 << 24;  // bounded grid-barrier wait (with a short sleep per poll)
+
+// ctr[0]: next tile, ctr[1]: CTAs past phase 1, ctr[2]: next group of TE rows; zeroed before the launch.
+template <int D, int TE, typename PW>
+__global__ void __launch_bounds__(TE, (D == 3 ? 768 : TE) / TE)
+    k_tiles_fused(TileArgs a, RowArgs g, const double* __restrict__ node, const double* __restrict__ k, int f_kind,
+                  const double* __restrict__ f_arg, double* __restrict__ val, double* __restrict__ bvec,
+                  const float4* __restrict__ tab, int* __restrict__ ctr, int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ int s_item;
+  const int want_a = val != nullptr, want_b = bvec != nullptr;
+  for (;;) {
+    __syncthreads();  // the previous tile is done with the staged vertices and s_item
+    if (threadIdx.x == 0) s_item = atomicAdd(&ctr[0], 1);
+    __syncthreads();
+    const int tile = s_item;
+    if (tile >= a.ntiles) break;
+    elements_of_tile<D, TE>(a, tile, sm, node, k, f_kind, f_arg, want_a, want_b, tab, err);
+  }
+  // grid-wide barrier: every packet of every tile is written before any row reads one
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&ctr[1], 1);
+    int polls = 0;
+    while (*(volatile int*)&ctr[1] < (int)gridDim.x && polls < kBarrierPolls) {
+      __nanosleep(64);
+      ++polls;
+    }
+    __threadfence();
+    s_item = (polls < kBarrierPolls) ? 0 : -1;
+  }
+  __syncthreads();
+  if (s_item < 0) {
+    if (threadIdx.x == 0) report(err, FEM_ERR_TIMEOUT);
+    return;
+  }
+  const int wid = threadIdx.x >> 5;
+  df2* acc = reinterpret_cast<df2*>(sm) + (size_t)wid * 32 * g.max_row;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(&ctr[2], 1);
+    __syncthreads();
+    const int64_t G0 = (int64_t)s_item * TE;
+    if (G0 >= g.N) break;
+    const int64_t R0 = G0 + wid * 32;
+    if (R0 < g.N) rows_of_warp<D, PW, true>(g, R0, acc, val, bvec);
+  }
 }
 
 __host__ __device__ constexpr int gather_warp_bytes(int max_row) { return 32 * max_row * (int)sizeof(df2); }
@@ -199,6 +287,14 @@ int tile_smem_need(const TilePlan& T, int d, bool sinprod) {
   return xs + ((sinprod && d == 2) ? T.max_v * d * (int)sizeof(SC) : 0);
 }
 
+// Shared memory of the fused kernel (staging of phase 1 or row copies of phase 2, whichever is larger);
+// 0 if it exceeds what one CTA may use.
+int tile_fused_smem(const TilePlan& T, int d) {
+  const int mr = T.max_row > 0 ? T.max_row : 1;
+  const int need = std::max(tile_smem_need(T, d, true), (T.TE / 32) * gather_warp_bytes(mr));
+  return need <= 200 * 1024 ? need : 0;
+}
+
 int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg, double* val,
                    double* b, cudaStream_t s) {
   int* err = device_error_word();
@@ -214,6 +310,7 @@ int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_
   }
   TileArgs a;
   a.NT = P->NT;
+  a.ntiles = T.ntiles;
   a.elist = T.elist;
   a.lelem = T.lelem;
   a.voff = T.voff;
@@ -221,7 +318,61 @@ int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_
   a.ipos = T.ipos;
   a.pk = T.pk;
   a.xs_bytes = ((T.max_v * D * (int)sizeof(f3)) + 15) / 16 * 16;
+  RowArgs g;
+  g.N = P->N;
+  g.max_row = T.max_row > 0 ? T.max_row : 1;
+  g.row_ptr = P->row_ptr;
+  g.inc_ptr = P->inc_ptr;
+  g.pw = T.pw;
+  g.rdp = T.rdp;
+  g.pk = T.pk;
   const int want_a = val != nullptr, want_b = b != nullptr;
+  if (T.fused) {
+    // one cooperative launch: as many CTAs as are resident at once, counters zeroed in-stream
+    const int smem = tile_fused_smem(T, D);
+    if (smem == 0) return set_error(FEM_ERR_STATE, "the fused tile launch does not fit this mesh");
+    int* ctr = P->work_counter + 1;
+    FEM_CUDA(cudaMemsetAsync(ctr, 0, 3 * sizeof(int), s));
+    const void* fn = nullptr;
+    const char* name = nullptr;
+#define FEM_FUSED_PICK(DD, TT, PWT)                                   \
+  do {                                                                \
+    fn = (const void*)k_tiles_fused<DD, TT, PWT>;                     \
+    name = "(k_tiles_fused<" #DD ", " #TT ">)";                       \
+  } while (0)
+    if (D == 2) {
+      if (T.TE == 128) FEM_FUSED_PICK(2, 128, uint16_t);
+      else FEM_FUSED_PICK(2, 256, uint16_t);
+    } else {
+      if (T.TE == 128) FEM_FUSED_PICK(3, 128, uint32_t);
+      else FEM_FUSED_PICK(3, 256, uint32_t);
+    }
+#undef FEM_FUSED_PICK
+    FEM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0, nsm = 0, dev = 0;
+    FEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, T.TE, smem));
+    FEM_CUDA(cudaGetDevice(&dev));
+    FEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (per_sm < 1) return set_error(FEM_ERR_STATE, "the fused tile kernel cannot be resident");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(per_sm * nsm));
+    cfg.blockDim = dim3((unsigned)T.TE);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void* args[] = {(void*)&a, (void*)&g, (void*)&node, (void*)&k, (void*)&f_kind, (void*)&f_arg,
+                    (void*)&val, (void*)&b, (void*)&tab, (void*)&ctr, (void*)&err};
+    const bool tm = g_timing.load(std::memory_order_relaxed);
+    if (tm) timing_mark(name, s, true);
+    FEM_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (tm) timing_mark(name, s, false);
+    return FEM_OK;
+  }
   const int smem = tile_smem_need(T, D, f_kind == FEM_F_SINPROD && want_b);
 #define FEM_TILE_LAUNCH(DD, TT)                                                                               \
   do {                                                                                                        \
@@ -237,19 +388,16 @@ int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_
     else FEM_TILE_LAUNCH(3, 256);
   }
 #undef FEM_TILE_LAUNCH
-  const int mr = T.max_row > 0 ? T.max_row : 1;
-  const int wpc = gather_warps(mr);
+  const int wpc = gather_warps(g.max_row);
   const int bt = 32 * wpc;
-  const int gsm = wpc * gather_warp_bytes(mr);
+  const int gsm = wpc * gather_warp_bytes(g.max_row);
   const int64_t grid = (P->N + bt - 1) / bt;
   if (D == 2) {
     FEM_CUDA(cudaFuncSetAttribute(k_row_gather<2, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm));
-    FEM_LAUNCH((k_row_gather<2, uint16_t>), (int)grid, bt, gsm, s, P->N, mr, P->row_ptr, P->inc_ptr,
-               (const uint16_t*)T.pw, T.rdp, T.pk, val, b);
+    FEM_LAUNCH((k_row_gather<2, uint16_t>), (int)grid, bt, gsm, s, g, val, b);
   } else {
     FEM_CUDA(cudaFuncSetAttribute(k_row_gather<3, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm));
-    FEM_LAUNCH((k_row_gather<3, uint32_t>), (int)grid, bt, gsm, s, P->N, mr, P->row_ptr, P->inc_ptr,
-               (const uint32_t*)T.pw, T.rdp, T.pk, val, b);
+    FEM_LAUNCH((k_row_gather<3, uint32_t>), (int)grid, bt, gsm, s, g, val, b);
   }
   return FEM_OK;
 }

@@ -132,12 +132,14 @@ def test_all_value_paths_give_the_same_bits(case):
     kd = None if k is None else dev(k)
     fq = np.random.default_rng(8).normal(size=NT * (d + 1))
     loads = [(fa.FEM_F_SINPROD, None), (fa.FEM_F_CONST, dev(np.array([2.5]))), (fa.FEM_F_QPVALUES, dev(fq))]
-    paths = [(fa.FEM_PATH_TILES, 256), (fa.FEM_PATH_TILES, 128), (fa.FEM_PATH_BLOCKED, 0)]
+    paths = [(fa.FEM_PATH_TILES, 256), (fa.FEM_PATH_TILES, 128), (fa.FEM_PATH_TILES_FUSED, 128),
+             (fa.FEM_PATH_TILES_FUSED, 256), (fa.FEM_PATH_BLOCKED, 0)]
+    names = {fa.FEM_PATH_TILES: "tiles", fa.FEM_PATH_TILES_FUSED: "tiles_fused", fa.FEM_PATH_BLOCKED: "blocked"}
     for fk, farg in loads:
         ref = None
         for path, te in paths:
             fa.fem_pattern_force_path(p, path, te or 256)
-            assert fa.fem_pattern_value_path(p)["path"] == ("tiles" if path == fa.FEM_PATH_TILES else "blocked")
+            assert fa.fem_pattern_value_path(p)["path"] == names[path]
             v, b = fa.assemble(p, dev(node), kd, fk, farg, fa.FEM_DETERMINISTIC)
             vs = torch.empty_like(v)
             fa.fem_assemble(p, dev(node), kd, fk, farg, vs, None, fa.FEM_DETERMINISTIC)
@@ -358,6 +360,12 @@ def test_batched_matches_per_mesh_oracle():
         assert_close_scaled(v[bt.nnz_off[i]:bt.nnz_off[i + 1]], vo, so)
         bo = oracle.rhs(2, m["node"], m["elem"], oracle.F_SINPROD)
         assert_close_scaled(bb[bt.node_off[i]:bt.node_off[i + 1]], bo, np.abs(bo) + 1e-30)
+    # the batch runs as one launch: the fused tile kernel or the persistent owner-computes kernel
+    path = fa.fem_pattern_value_path(bt.pattern)["path"]
+    assert path == "tiles_fused" or (path == "blocked" and fa.fem_pattern_launch_shape(bt.pattern)["persistent"])
+    n0 = fa.launch_count()
+    bt.assemble(dev(node_cat), dev(k_cat), fa.FEM_F_SINPROD, None, val, b, fa.FEM_DETERMINISTIC)
+    assert fa.launch_count() - n0 == 1
     # graph replay gives the same bits
     val2, b2 = torch.empty_like(val), torch.empty_like(b)
     n0 = fa.launch_count()
@@ -366,6 +374,16 @@ def test_batched_matches_per_mesh_oracle():
     torch.cuda.synchronize()
     assert fa.launch_count() > n0
     assert torch.equal(val, val2) and torch.equal(b, b2)
+    # and so does the other one-launch form
+    other = fa.FEM_PATH_BLOCKED if path == "tiles_fused" else fa.FEM_PATH_TILES_FUSED
+    fa.fem_pattern_force_path(bt.pattern, other, 128)
+    if other == fa.FEM_PATH_BLOCKED:
+        shp = fa.fem_pattern_launch_shape(bt.pattern)
+        fa.fem_pattern_force_launch(bt.pattern, shp["threads"], shp["ctas_per_sm"], True)
+    val3, b3 = torch.empty_like(val), torch.empty_like(b)
+    bt.assemble(dev(node_cat), dev(k_cat), fa.FEM_F_SINPROD, None, val3, b3, fa.FEM_DETERMINISTIC)
+    fa.get_error()
+    assert torch.equal(val, val3) and torch.equal(b, b3)
 
 
 def test_edge_cases():
