@@ -7,10 +7,13 @@
 //   dL_A/dx_m = k |tau| (S g_m - sum_i Q_im g_i),  Q = (W + W^T) P
 //   dL_b/dx_m = |tau| g_m sum_q w_q f_q rl_q + |tau| sum_q w_q lambda_m(q) grad f(x_q) rl_q,
 //               rl_q = sum_i r_i lambda_i(q)
-// One thread per element writes gk[t] and its (d+1) x d vertex contributions (float pairs) to the
-// pattern's scratch; a second kernel sums each vertex's contributions over its incidence list in
-// ascending element order (deterministic) and writes gnode. No FP64 arithmetic except the final
-// rounding of each output (one FP64 add).
+// One thread per element writes gk[t] and its (d+1) x d vertex contributions (float pairs); a second
+// kernel sums each vertex's contributions over its incidence list in ascending element order
+// (deterministic) and writes gnode. When the pattern has a tile plan the elements run in tile order with
+// their vertices split once per tile in shared memory, and the contributions of element-row (t, m) go to
+// the plan's packet slot of incidence (t, m), so each vertex reads its contributions contiguously;
+// otherwise they run in the caller's order and go to the pattern's scratch. No FP64 arithmetic except
+// the loss-weight pair sums and the final rounding of each output.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -22,25 +25,17 @@ const float4* sincos_table_device();  // values_blocked.cu
 
 namespace {
 
+// Adjoint of one element: out[m][c] = dL/dx_{m,c} contributions and gkv = dL/dk_t, from the exact
+// coordinate splits V, the coefficient kt, the symmetrised loss weights Ws = W + W^T (with_w) and the
+// load-vector weights rv of the element's vertices (with_r).
+// Stiffness part in the form that needs the fewest products: h_j = sum_i Ws_ij g_i, then
+// S = (1/2) sum_j h_j . g_j and sum_i Q_im g_i = sum_j (g_j . g_m) h_j.
 template <int D>
-__global__ void __launch_bounds__(256) k_backward_df(const int32_t* __restrict__ elem, int NT,
-                                                     const double* __restrict__ node, const double* __restrict__ k,
-                                                     int f_kind, const double* __restrict__ f_arg,
-                                                     const int32_t* __restrict__ slot, const double* __restrict__ w,
-                                                     const double* __restrict__ r, double* __restrict__ gk,
-                                                     float2* __restrict__ scratch, const float4* __restrict__ tab,
-                                                     int* __restrict__ err) {
+__device__ __forceinline__ bool element_adjoint(const VtxDF<D>* const (&V)[D + 1], int t, df2 kt, bool with_w,
+                                                const df2 (&Ws)[D + 1][D + 1], bool with_r, const df2 (&rv)[D + 1],
+                                                int f_kind, const double* __restrict__ f_arg,
+                                                const float4* __restrict__ tab, df2 (&out)[D + 1][D], df2& gkv) {
   constexpr int D1 = D + 1;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= NT) return;
-  int e[D1];
-#pragma unroll
-  for (int i = 0; i < D1; ++i) e[i] = __ldg(elem + (size_t)t * D1 + i);
-  VtxDF<D> V[D1];
-#pragma unroll
-  for (int i = 0; i < D1; ++i)
-#pragma unroll
-    for (int m = 0; m < D; ++m) V[i].x[m] = split3(__ldg(node + (size_t)e[i] * D + m));
   // scaled inward normals n_i and the positive measure |tau| (d! |tau| = signed 2-D area x 2, 3-D vol x 6)
   df2 n[D1][D];
   df2 dmeas;  // d! |tau|
@@ -48,9 +43,9 @@ __global__ void __launch_bounds__(256) k_backward_df(const int32_t* __restrict__
     df2 ev[3][2];
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
-      ev[0][m] = f3_diff(V[2].x[m], V[1].x[m]);
-      ev[1][m] = f3_diff(V[0].x[m], V[2].x[m]);
-      ev[2][m] = f3_diff(V[1].x[m], V[0].x[m]);
+      ev[0][m] = f3_diff(V[2]->x[m], V[1]->x[m]);
+      ev[1][m] = f3_diff(V[0]->x[m], V[2]->x[m]);
+      ev[2][m] = f3_diff(V[1]->x[m], V[0]->x[m]);
     }
     dmeas = df_sub(df_mul(ev[1][0], ev[2][1]), df_mul(ev[1][1], ev[2][0]));
 #pragma unroll
@@ -63,20 +58,20 @@ __global__ void __launch_bounds__(256) k_backward_df(const int32_t* __restrict__
 #pragma unroll
     for (int q = 0; q < 3; ++q)
 #pragma unroll
-      for (int m = 0; m < 3; ++m) ed[q][m] = f3_diff(V[q + 1].x[m], V[0].x[m]);
+      for (int m = 0; m < 3; ++m) ed[q][m] = f3_diff(V[q + 1]->x[m], V[0]->x[m]);
     df_cross(ed[1], ed[2], n[1]);
     df_cross(ed[2], ed[0], n[2]);
     df_cross(ed[0], ed[1], n[3]);
     df2 u[3], v[3];
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-      u[m] = f3_diff(V[3].x[m], V[1].x[m]);
-      v[m] = f3_diff(V[2].x[m], V[1].x[m]);
+      u[m] = f3_diff(V[3]->x[m], V[1]->x[m]);
+      v[m] = f3_diff(V[2]->x[m], V[1]->x[m]);
     }
     df_cross(u, v, n[0]);
     dmeas = df_dot<3>(n[3], ed[2]);
   }
-  if (!(dmeas.h > 0.0f && dmeas.h < INFINITY)) report(err, FEM_ERR_DEGENERATE);
+  const bool ok = dmeas.h > 0.0f && dmeas.h < INFINITY;
   const df2 inv = df_recip(dmeas);
   const df2 meas = (D == 2) ? df_scale(dmeas, 0.5f) : df_mul(dmeas, df2{0.1666666716337204f, -4.9670538793e-09f});
   df2 g[D1][D];
@@ -84,32 +79,27 @@ __global__ void __launch_bounds__(256) k_backward_df(const int32_t* __restrict__
   for (int i = 0; i < D1; ++i)
 #pragma unroll
     for (int c = 0; c < D; ++c) g[i][c] = df_mul(n[i][c], inv);
-  df2 out[D1][D];
 #pragma unroll
   for (int i = 0; i < D1; ++i)
 #pragma unroll
     for (int c = 0; c < D; ++c) out[i][c] = df2{0.0f, 0.0f};
-  if (w) {
-    df2 P[D1][D1];
+  gkv = df2{0.0f, 0.0f};
+  if (with_w) {
+    df2 h[D1][D];
 #pragma unroll
-    for (int i = 0; i < D1; ++i)
+    for (int j = 0; j < D1; ++j)
 #pragma unroll
-      for (int j = i; j < D1; ++j) {
-        P[i][j] = df_dot<D>(g[i], g[j]);
-        P[j][i] = P[i][j];
+      for (int c = 0; c < D; ++c) {
+        df2 a = df_mul(Ws[0][j], g[0][c]);
+#pragma unroll
+        for (int i = 1; i < D1; ++i) a = df_add(a, df_mul(Ws[i][j], g[i][c]));
+        h[j][c] = a;
       }
-    df2 W[D1][D1];
+    df2 S2 = df_dot<D>(h[0], g[0]);
 #pragma unroll
-    for (int i = 0; i < D1; ++i)
-#pragma unroll
-      for (int j = 0; j < D1; ++j) W[i][j] = df_from_double_fast(__ldg(w + __ldg(slot + (size_t)(i * D1 + j) * NT + t)));
-    df2 S = df2{0.0f, 0.0f};
-#pragma unroll
-    for (int i = 0; i < D1; ++i)
-#pragma unroll
-      for (int j = 0; j < D1; ++j) S = df_add(S, df_mul(W[i][j], P[i][j]));
-    if (gk) gk[t] = df_to_double(df_mul(meas, S));
-    const df2 kt = k ? df_from_double_fast(__ldg(k + t)) : df2{1.0f, 0.0f};
+    for (int j = 1; j < D1; ++j) S2 = df_add(S2, df_dot<D>(h[j], g[j]));
+    const df2 S = df_scale(S2, 0.5f);
+    gkv = df_mul(meas, S);
     const df2 km = df_mul(kt, meas);
 #pragma unroll
     for (int m = 0; m < D1; ++m) {
@@ -117,23 +107,16 @@ __global__ void __launch_bounds__(256) k_backward_df(const int32_t* __restrict__
 #pragma unroll
       for (int c = 0; c < D; ++c) acc[c] = df_mul(S, g[m][c]);
 #pragma unroll
-      for (int i = 0; i < D1; ++i) {
-        df2 q = df2{0.0f, 0.0f};
+      for (int j = 0; j < D1; ++j) {
+        const df2 pjm = df_dot<D>(g[j], g[m]);
 #pragma unroll
-        for (int j = 0; j < D1; ++j) q = df_add(q, df_mul(df_add(W[i][j], W[j][i]), P[j][m]));
-#pragma unroll
-        for (int c = 0; c < D; ++c) acc[c] = df_sub(acc[c], df_mul(q, g[i][c]));
+        for (int c = 0; c < D; ++c) acc[c] = df_sub(acc[c], df_mul(pjm, h[j][c]));
       }
 #pragma unroll
       for (int c = 0; c < D; ++c) out[m][c] = df_mul(km, acc[c]);
     }
-  } else if (gk) {
-    gk[t] = 0.0;
   }
-  if (r) {
-    df2 rv[D1];
-#pragma unroll
-    for (int i = 0; i < D1; ++i) rv[i] = df_from_double_fast(__ldg(r + e[i]));
+  if (with_r) {
     // quadrature points: f, grad f and barycentric weights lambda_i(q)
     df2 fq[D1], gf[D1][D];
     float lam_self, lam_other, wq;
@@ -157,7 +140,7 @@ __global__ void __launch_bounds__(256) k_backward_df(const int32_t* __restrict__
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-          for (int m = 0; m < 2; ++m) sc[i][m] = sincospi_half(V[i].x[m], tab);
+          for (int m = 0; m < 2; ++m) sc[i][m] = sincospi_half(V[i]->x[m], tab);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const int u = (q + 1) % 3, v = (q + 2) % 3;
@@ -171,10 +154,11 @@ __global__ void __launch_bounds__(256) k_backward_df(const int32_t* __restrict__
         const df2 al = {0.58541017770767212f, 1.8917296174e-08f}, be = {0.13819660246372223f, -1.3387116971e-09f};
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-          const float nn = rintf(V[0].x[m].a);
+          const float nn = rintf(V[0]->x[m].a);
           df2 y[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) y[i] = df_add(two_sum(V[i].x[m].a, -nn), fast_two_sum(V[i].x[m].b, V[i].x[m].c));
+          for (int i = 0; i < 4; ++i)
+            y[i] = df_add(two_sum(V[i]->x[m].a, -nn), fast_two_sum(V[i]->x[m].b, V[i]->x[m].c));
           const df2 sy = df_add(df_add(y[0], y[1]), df_add(y[2], y[3]));
           const float sgn = (__float2int_rn(nn) & 1) ? -1.0f : 1.0f;
 #pragma unroll
@@ -234,10 +218,145 @@ __global__ void __launch_bounds__(256) k_backward_df(const int32_t* __restrict__
         out[m][c] = df_add(out[m][c], df_mul(meas, df_add(df_mul(g[m][c], Rb), s2)));
       }
   }
+  return ok;
+}
+
+// Ws = W + W^T of element t from the loss weights on its slots (pairs summed in FP64, then split)
+template <int D>
+__device__ __forceinline__ void sym_weights(const int32_t* __restrict__ slot, int64_t NT, int t,
+                                            const double* __restrict__ w, df2 (&Ws)[D + 1][D + 1]) {
+  constexpr int D1 = D + 1;
+#pragma unroll
+  for (int i = 0; i < D1; ++i)
+#pragma unroll
+    for (int j = i; j < D1; ++j) {
+      const double wij = __ldg(w + __ldg(slot + (size_t)(i * D1 + j) * NT + t));
+      const double wji = (i == j) ? wij : __ldg(w + __ldg(slot + (size_t)(j * D1 + i) * NT + t));
+      Ws[i][j] = df_from_double_fast(__dadd_rn(wij, wji));
+      Ws[j][i] = Ws[i][j];
+    }
+}
+
+// Element order of the caller, vertices read per element; contributions to scratch[(m*D+c)*NT + t].
+template <int D>
+__global__ void __launch_bounds__(128, 4) k_backward_df(const int32_t* __restrict__ elem, int NT,
+                                                        const double* __restrict__ node, const double* __restrict__ k,
+                                                        int f_kind, const double* __restrict__ f_arg,
+                                                        const int32_t* __restrict__ slot, const double* __restrict__ w,
+                                                        const double* __restrict__ r, double* __restrict__ gk,
+                                                        float2* __restrict__ scratch, const float4* __restrict__ tab,
+                                                        int* __restrict__ err) {
+  constexpr int D1 = D + 1;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= NT) return;
+  int e[D1];
+#pragma unroll
+  for (int i = 0; i < D1; ++i) e[i] = __ldg(elem + (size_t)t * D1 + i);
+  VtxDF<D> X[D1];
+#pragma unroll
+  for (int i = 0; i < D1; ++i)
+#pragma unroll
+    for (int m = 0; m < D; ++m) X[i].x[m] = split3(__ldg(node + (size_t)e[i] * D + m));
+  df2 Ws[D1][D1], rv[D1];
+  if (w) sym_weights<D>(slot, NT, t, w, Ws);
+  if (r) {
+#pragma unroll
+    for (int i = 0; i < D1; ++i) rv[i] = df_from_double_fast(__ldg(r + e[i]));
+  }
+  const df2 kt = k ? df_from_double_fast(__ldg(k + t)) : df2{1.0f, 0.0f};
+  const VtxDF<D>* V[D1];
+#pragma unroll
+  for (int i = 0; i < D1; ++i) V[i] = &X[i];
+  df2 out[D1][D], gkv;
+  if (!element_adjoint<D>(reinterpret_cast<const VtxDF<D>* const(&)[D1]>(V), t, kt, w != nullptr, Ws, r != nullptr,
+                          rv, f_kind, f_arg, tab, out, gkv))
+    report(err, FEM_ERR_DEGENERATE);
+  if (gk) gk[t] = df_to_double(gkv);
 #pragma unroll
   for (int m = 0; m < D1; ++m)
 #pragma unroll
     for (int c = 0; c < D; ++c) scratch[(size_t)(m * D + c) * NT + t] = make_float2(out[m][c].h, out[m][c].l);
+}
+
+// Tile order (the forward's tile plan): the tile's vertices are split once into shared memory; the
+// contributions of element-row (t, m) go to packet ipos(t, m), so each vertex's packets are contiguous.
+template <int D, int TE>
+__global__ void __launch_bounds__(TE, 512 / TE) k_backward_tiles(
+    int64_t NT, const int32_t* __restrict__ elist, const uint16_t* __restrict__ lelem, const int32_t* __restrict__ voff,
+    const int32_t* __restrict__ vlist, const int32_t* __restrict__ ipos, const double* __restrict__ node,
+    const double* __restrict__ k, int f_kind, const double* __restrict__ f_arg, const int32_t* __restrict__ slot,
+    const double* __restrict__ w, const double* __restrict__ r, double* __restrict__ gk, float4* __restrict__ pk,
+    const float4* __restrict__ tab, int* __restrict__ err) {
+  constexpr int D1 = D + 1;
+  extern __shared__ __align__(16) unsigned char sm[];
+  VtxDF<D>* xs = reinterpret_cast<VtxDF<D>*>(sm);
+  const int tile = blockIdx.x;
+  const int v0 = __ldg(voff + tile), nv = __ldg(voff + tile + 1) - v0;
+  const int64_t j = (int64_t)tile * TE + threadIdx.x;
+  const bool act = j < NT;
+  int t = 0, lv[D1], qi[D1];
+  if (act) {
+    t = __ldg(elist + j);
+#pragma unroll
+    for (int i = 0; i < D1; ++i) {
+      lv[i] = __ldg(lelem + (int64_t)i * NT + j);
+      qi[i] = __ldg(ipos + (int64_t)i * NT + j);
+    }
+  }
+  for (int v = threadIdx.x; v < nv; v += TE) {
+    const int R = __ldg(vlist + v0 + v);
+    VtxDF<D> x;
+#pragma unroll
+    for (int m = 0; m < D; ++m) x.x[m] = split3(__ldg(node + (size_t)R * D + m));
+    xs[v] = x;
+  }
+  __syncthreads();
+  if (!act) return;
+  df2 Ws[D1][D1], rv[D1];
+  if (w) sym_weights<D>(slot, NT, t, w, Ws);
+  if (r) {
+#pragma unroll
+    for (int i = 0; i < D1; ++i) rv[i] = df_from_double_fast(__ldg(r + __ldg(vlist + v0 + lv[i])));
+  }
+  const df2 kt = k ? df_from_double_fast(__ldg(k + t)) : df2{1.0f, 0.0f};
+  const VtxDF<D>* V[D1];
+#pragma unroll
+  for (int i = 0; i < D1; ++i) V[i] = &xs[lv[i]];
+  df2 out[D1][D], gkv;
+  if (!element_adjoint<D>(reinterpret_cast<const VtxDF<D>* const(&)[D1]>(V), t, kt, w != nullptr, Ws, r != nullptr,
+                          rv, f_kind, f_arg, tab, out, gkv))
+    report(err, FEM_ERR_DEGENERATE);
+  if (gk) gk[t] = df_to_double(gkv);
+#pragma unroll
+  for (int m = 0; m < D1; ++m) {
+    float4* dst = pk + 2 * (size_t)qi[m];
+    dst[0] = make_float4(out[m][0].h, out[m][0].l, out[m][1].h, out[m][1].l);
+    if constexpr (D == 3) dst[1] = make_float4(out[m][2].h, out[m][2].l, 0.0f, 0.0f);
+  }
+}
+
+// per vertex: its packets are contiguous, in ascending element order
+template <int D>
+__global__ void __launch_bounds__(256) k_backward_gather_tiles(const int32_t* __restrict__ inc_ptr, int64_t N,
+                                                               const float4* __restrict__ pk,
+                                                               double* __restrict__ gnode) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= N) return;
+  df2 acc[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) acc[c] = df2{0.0f, 0.0f};
+  const int q1 = __ldg(inc_ptr + v + 1);
+  for (int q = __ldg(inc_ptr + v); q < q1; ++q) {
+    const float4 a = __ldg(pk + 2 * (size_t)q);
+    acc[0] = df_acc(acc[0], df2{a.x, a.y});
+    acc[1] = df_acc(acc[1], df2{a.z, a.w});
+    if constexpr (D == 3) {
+      const float4 b = __ldg(pk + 2 * (size_t)q + 1);
+      acc[2] = df_acc(acc[2], df2{b.x, b.y});
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < D; ++c) gnode[v * D + c] = df_to_double(acc[c]);
 }
 
 template <int D>
@@ -277,13 +396,32 @@ int assemble_backward(const Pattern* P, const double* node, const double* k, int
     if (gnode && N > 0) FEM_CUDA(cudaMemsetAsync(gnode, 0, sizeof(double) * N * P->d, s));
     return FEM_OK;
   }
+  const TilePlan& T = P->tile;
+  if (T.ok && T.pk && (T.TE == 128 || T.TE == 256)) {
+    const int smem = ((T.max_v * P->d * (int)sizeof(f3)) + 15) / 16 * 16;
+    const int g2 = (N + 255) / 256;
+#define FEM_BWD_TILES(DD, TT)                                                                                      \
+  FEM_LAUNCH((k_backward_tiles<DD, TT>), T.ntiles, TT, smem, s, P->NT, T.elist, T.lelem, T.voff, T.vlist, T.ipos, \
+             node, k, f_kind, f_arg, P->slot, w, r, gk, T.pk, tab, err)
+    if (P->d == 2) {
+      if (T.TE == 128) FEM_BWD_TILES(2, 128);
+      else FEM_BWD_TILES(2, 256);
+      if (gnode) FEM_LAUNCH(k_backward_gather_tiles<2>, g2, 256, 0, s, P->inc_ptr, P->N, T.pk, gnode);
+    } else {
+      if (T.TE == 128) FEM_BWD_TILES(3, 128);
+      else FEM_BWD_TILES(3, 256);
+      if (gnode) FEM_LAUNCH(k_backward_gather_tiles<3>, g2, 256, 0, s, P->inc_ptr, P->N, T.pk, gnode);
+    }
+#undef FEM_BWD_TILES
+    return FEM_OK;
+  }
   float2* scr = reinterpret_cast<float2*>(P->scratch);
-  const int g1 = (NT + 255) / 256, g2 = (N + 255) / 256;
+  const int g1 = (NT + 127) / 128, g2 = (N + 255) / 256;
   if (P->d == 2) {
-    FEM_LAUNCH(k_backward_df<2>, g1, 256, 0, s, P->elem, NT, node, k, f_kind, f_arg, P->slot, w, r, gk, scr, tab, err);
+    FEM_LAUNCH(k_backward_df<2>, g1, 128, 0, s, P->elem, NT, node, k, f_kind, f_arg, P->slot, w, r, gk, scr, tab, err);
     if (gnode) FEM_LAUNCH(k_backward_gather_df<2>, g2, 256, 0, s, P->inc_ptr, P->inc, N, NT, scr, gnode);
   } else {
-    FEM_LAUNCH(k_backward_df<3>, g1, 256, 0, s, P->elem, NT, node, k, f_kind, f_arg, P->slot, w, r, gk, scr, tab, err);
+    FEM_LAUNCH(k_backward_df<3>, g1, 128, 0, s, P->elem, NT, node, k, f_kind, f_arg, P->slot, w, r, gk, scr, tab, err);
     if (gnode) FEM_LAUNCH(k_backward_gather_df<3>, g2, 256, 0, s, P->inc_ptr, P->inc, N, NT, scr, gnode);
   }
   return FEM_OK;

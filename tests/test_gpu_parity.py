@@ -277,16 +277,20 @@ def test_backward_matches_oracle_adjoint(case, f_kind):
     w = meshgen.normal(1808, meshgen.TAG_W, p.nnz)
     r = meshgen.normal(1808, meshgen.TAG_R, N)
     farg = meshgen.normal(7, 9, NT * (d + 1)) if f_kind == fa.FEM_F_QPVALUES else None
-    gn = torch.empty((N, d), dtype=torch.float64, device="cuda")
-    gk = torch.empty(NT, dtype=torch.float64, device="cuda")
-    fa.fem_assemble_backward(p, dev(node), dev(k), f_kind, None if farg is None else dev(farg), dev(w), dev(r), gn, gk)
-    fa.get_error()
     gno, gko = oracle.backward(d, node, elem, k, f_kind, farg, slot, w, r)
     # magnitude scale: the same adjoint with |w|, |r| bounds no cancellation; use max-based scale per array
     sn = 1e-10 * (np.abs(gno) + np.abs(gno).max())
     sk = 1e-10 * (np.abs(gko) + np.abs(gko).max())
-    assert np.all(np.abs(host(gn) - gno) <= sn)
-    assert np.all(np.abs(host(gk) - gko) <= sk)
+    # tile order (the pattern has a tile plan), then the caller's order (no plan)
+    for _ in range(2):
+        gn = torch.empty((N, d), dtype=torch.float64, device="cuda")
+        gk = torch.empty(NT, dtype=torch.float64, device="cuda")
+        fa.fem_assemble_backward(p, dev(node), dev(k), f_kind, None if farg is None else dev(farg), dev(w), dev(r),
+                                 gn, gk)
+        fa.get_error()
+        assert np.all(np.abs(host(gn) - gno) <= sn)
+        assert np.all(np.abs(host(gk) - gko) <= sk)
+        fa.fem_pattern_force_path(p, fa.FEM_PATH_TWO_PASS)
 
 
 def test_backward_central_fd_on_gpu():
