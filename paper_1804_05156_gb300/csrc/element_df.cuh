@@ -108,9 +108,10 @@ __device__ __forceinline__ void df_cross(const df2 (&u)[3], const df2 (&v)[3], d
   o[2] = df_sub(df_mul(u[0], v[1]), df_mul(u[1], v[0]));
 }
 
+// want_diag = false leaves L.a[0..3] (the diagonals) unset, for callers that re-form them.
 __device__ __forceinline__ bool element_df3(const VtxDF<3>* const (&V)[4], df2 kt, bool want_a, bool want_b,
                                             int f_kind, df2 fconst, const double* __restrict__ f_arg, int t,
-                                            const float4* __restrict__ tab, LocalDF<3>& L) {
+                                            const float4* __restrict__ tab, LocalDF<3>& L, bool want_diag = true) {
   df2 e[3][3];  // e[m-1] = x_m - x_0
 #pragma unroll
   for (int q = 0; q < 3; ++q)
@@ -141,8 +142,10 @@ __device__ __forceinline__ bool element_df3(const VtxDF<3>* const (&V)[4], df2 k
       for (int j = i + 1; j < 4; ++j) {
         const df2 aij = df_mul(s, df_dot<3>(n[i], n[j]));
         L.a[pidx<3>(i, j)] = aij;
-        L.a[i] = df_sub(L.a[i], aij);
-        L.a[j] = df_sub(L.a[j], aij);
+        if (want_diag) {
+          L.a[i] = df_sub(L.a[i], aij);
+          L.a[j] = df_sub(L.a[j], aij);
+        }
       }
   }
   if (want_b) {

@@ -107,7 +107,7 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
     ok = element_df2(V, S, kt, want_a, want_b, f_kind, fconst, f_arg, t, L);
   } else {
     const VtxDF<3>* const V[4] = {&xs[lv[0]], &xs[lv[1]], &xs[lv[2]], &xs[lv[3]]};
-    ok = element_df3(V, kt, want_a, want_b, f_kind, fconst, f_arg, t, tab, L);
+    ok = element_df3(V, kt, want_a, want_b, f_kind, fconst, f_arg, t, tab, L, false);  // diagonals: in the gather
   }
   if (!ok) report(err, FEM_ERR_DEGENERATE);
 #pragma unroll
@@ -223,8 +223,10 @@ __global__ void __launch_bounds__(256) k_row_gather(RowArgs g, double* __restric
 }
 
 constexpr int kBarrierPolls = 1 << 24;  // bounded grid-barrier wait (with a short sleep per poll)
+constexpr int kItemsPerClaim = 8;       // tiles (or row groups) taken per counter increment
 
-// ctr[0]: next tile, ctr[1]: CTAs past phase 1, ctr[2]: next group of TE rows; zeroed before the launch.
+// ctr[0]: next tile, ctr[1]: CTAs past phase 1, ctr[2]: next group of TE rows (taken kItemsPerClaim at a
+// time); zeroed before the launch.
 template <int D, int TE, typename PW>
 __global__ void __launch_bounds__(TE, (D == 3 ? 768 : TE) / TE)
     k_tiles_fused(TileArgs a, RowArgs g, const double* __restrict__ node, const double* __restrict__ k, int f_kind,
@@ -234,12 +236,16 @@ __global__ void __launch_bounds__(TE, (D == 3 ? 768 : TE) / TE)
   __shared__ int s_item;
   const int want_a = val != nullptr, want_b = bvec != nullptr;
   for (;;) {
-    __syncthreads();  // the previous tile is done with the staged vertices and s_item
-    if (threadIdx.x == 0) s_item = atomicAdd(&ctr[0], 1);
+    __syncthreads();  // the previous tiles are done with the staged vertices and s_item
+    if (threadIdx.x == 0) s_item = atomicAdd(&ctr[0], kItemsPerClaim);
     __syncthreads();
-    const int tile = s_item;
-    if (tile >= a.ntiles) break;
-    elements_of_tile<D, TE>(a, tile, sm, node, k, f_kind, f_arg, want_a, want_b, tab, err);
+    const int first = s_item;
+    if (first >= a.ntiles) break;
+    const int last = min(first + kItemsPerClaim, a.ntiles);
+    for (int tile = first; tile < last; ++tile) {
+      if (tile > first) __syncthreads();  // staging of the next tile overwrites shared memory
+      elements_of_tile<D, TE>(a, tile, sm, node, k, f_kind, f_arg, want_a, want_b, tab, err);
+    }
   }
   // grid-wide barrier: every packet of every tile is written before any row reads one
   __syncthreads();
@@ -263,12 +269,14 @@ __global__ void __launch_bounds__(TE, (D == 3 ? 768 : TE) / TE)
   df2* acc = reinterpret_cast<df2*>(sm) + (size_t)wid * 32 * g.max_row;
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) s_item = atomicAdd(&ctr[2], 1);
+    if (threadIdx.x == 0) s_item = atomicAdd(&ctr[2], kItemsPerClaim);
     __syncthreads();
     const int64_t G0 = (int64_t)s_item * TE;
     if (G0 >= g.N) break;
-    const int64_t R0 = G0 + wid * 32;
-    if (R0 < g.N) rows_of_warp<D, PW, true>(g, R0, acc, val, bvec);
+    for (int c = 0; c < kItemsPerClaim; ++c) {
+      const int64_t R0 = G0 + (int64_t)c * TE + wid * 32;
+      if (R0 < g.N) rows_of_warp<D, PW, true>(g, R0, acc, val, bvec);
+    }
   }
 }
 
