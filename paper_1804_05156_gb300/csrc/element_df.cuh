@@ -53,9 +53,10 @@ __device__ __forceinline__ SC sincospi_half(const f3& x, const float4* __restric
 // sin(pi (u + v)/2) = sin(pi u/2) cos(pi v/2) + cos(pi u/2) sin(pi v/2)
 __device__ __forceinline__ df2 sin_mid(const SC& u, const SC& v) { return df_add(df_mul(u.s, v.c), df_mul(u.c, v.s)); }
 
+// want_diag = false leaves L.a[0..2] (the diagonals) unset, for callers that re-form them.
 __device__ __forceinline__ bool element_df2(const VtxDF<2>* const (&V)[3], const SC* const (&S)[3], df2 kt, bool want_a,
                                             bool want_b, int f_kind, df2 fconst, const double* __restrict__ f_arg,
-                                            int t, LocalDF<2>& L) {
+                                            int t, LocalDF<2>& L, bool want_diag = true) {
   // side vectors ve_i (side opposite vertex i), each formed from its own endpoints
   df2 e[3][2];
 #pragma unroll
@@ -75,9 +76,11 @@ __device__ __forceinline__ bool element_df2(const VtxDF<2>* const (&V)[3], const
     L.a[3] = a01;
     L.a[4] = a02;
     L.a[5] = a12;
-    L.a[0] = df_neg(df_add(a01, a02));
-    L.a[1] = df_neg(df_add(a01, a12));
-    L.a[2] = df_neg(df_add(a02, a12));
+    if (want_diag) {
+      L.a[0] = df_neg(df_add(a01, a02));
+      L.a[1] = df_neg(df_add(a01, a12));
+      L.a[2] = df_neg(df_add(a02, a12));
+    }
   }
   if (want_b) {
     const df2 meas = df_scale(a2abs, 0.5f);

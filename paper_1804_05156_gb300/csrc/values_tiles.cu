@@ -5,10 +5,11 @@
 //   tile's vertices are staged in shared memory once (exact three-float splits; for the 2-D
 //   sine-product load also sin/cos(pi x/2) per coordinate), then each thread computes one element's
 //   local stiffness and load entries (element_df.cuh: Sec. 3.1.3, eq. (dlambda), Sec. 3.2) and writes,
-//   for each local row i, one 32-byte packet of float pairs to the slot of incidence (t, i):
-//     2-D: (a_ii, a_ij, a_ik, b_i);  3-D: (a_ij, a_ik, a_il, b_i),
-//   with j < k < l the other local indices. The 3-D diagonal is re-formed from the packet in phase 2
-//   exactly as the element routine forms it (a_ii = ((0 - a_ij) - a_ik) - a_il), so it costs no bytes.
+//   for each local row i, one packet of float pairs to the slot of incidence (t, i):
+//     2-D: (a_ij, a_ik, b_i), 24 bytes;  3-D: (a_ij, a_ik, a_il, b_i), 32 bytes,
+//   with j < k < l the other local indices. The diagonal is re-formed from the packet in phase 2 exactly
+//   as the element routine forms it (2-D a_ii = -(a_ij + a_ik), 3-D ((0 - a_ij) - a_ik) - a_il), so it
+//   costs no bytes.
 // Phase 2 (k_row_gather): one thread per row, one warp per 32 consecutive rows. A row's packets are
 //   contiguous (the incidence lists are sorted by row, then element). Each thread adds its row's
 //   diagonal and load terms in registers and the off-diagonal terms in the warp's shared-memory copy
@@ -104,7 +105,7 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
   if constexpr (D == 2) {
     const VtxDF<2>* const V[3] = {&xs[lv[0]], &xs[lv[1]], &xs[lv[2]]};
     const SC* const S[3] = {&scs[lv[0] * 2], &scs[lv[1] * 2], &scs[lv[2] * 2]};
-    ok = element_df2(V, S, kt, want_a, want_b, f_kind, fconst, f_arg, t, L);
+    ok = element_df2(V, S, kt, want_a, want_b, f_kind, fconst, f_arg, t, L, false);  // diagonals: in the gather
   } else {
     const VtxDF<3>* const V[4] = {&xs[lv[0]], &xs[lv[1]], &xs[lv[2]], &xs[lv[3]]};
     ok = element_df3(V, kt, want_a, want_b, f_kind, fconst, f_arg, t, tab, L, false);  // diagonals: in the gather
@@ -112,15 +113,26 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
   if (!ok) report(err, FEM_ERR_DEGENERATE);
 #pragma unroll
   for (int i = 0; i < D1; ++i) {
-    df2 o[D1];  // 2-D: a_ii, a_ij, a_ik; 3-D: a_ij, a_ik, a_il (j < k < l, the other local indices)
+    df2 o[D];  // a_ij for the other local indices j, ascending
     int c = 0;
-    if constexpr (D == 2) o[c++] = L.a[pidx<D>(i, i)];
 #pragma unroll
     for (int jj = 0; jj < D1; ++jj)
       if (jj != i) o[c++] = L.a[pidx<D>(i, jj)];
-    float4* dst = a.pk + 2 * (size_t)qi[i];
-    dst[0] = make_float4(o[0].h, o[0].l, o[1].h, o[1].l);
-    dst[1] = make_float4(o[2].h, o[2].l, L.bt[i].h, L.bt[i].l);
+    if constexpr (D == 2) {
+      // 24-byte packet (a_ij, a_ik, b_i): one 16-byte and one 8-byte store, aligned by the slot's parity
+      float2* dst = reinterpret_cast<float2*>(a.pk) + 3 * (size_t)qi[i];
+      if ((qi[i] & 1) == 0) {
+        *reinterpret_cast<float4*>(dst) = make_float4(o[0].h, o[0].l, o[1].h, o[1].l);
+        dst[2] = make_float2(L.bt[i].h, L.bt[i].l);
+      } else {
+        dst[0] = make_float2(o[0].h, o[0].l);
+        *reinterpret_cast<float4*>(dst + 1) = make_float4(o[1].h, o[1].l, L.bt[i].h, L.bt[i].l);
+      }
+    } else {
+      float4* dst = a.pk + 2 * (size_t)qi[i];
+      dst[0] = make_float4(o[0].h, o[0].l, o[1].h, o[1].l);
+      dst[1] = make_float4(o[2].h, o[2].l, L.bt[i].h, L.bt[i].l);
+    }
   }
 }
 
@@ -132,9 +144,10 @@ __device__ __forceinline__ void add_packet(const float4& p0, const float4& p1, u
   if (want_a) {
     const int c0 = o + (int)(w & 0xffu), c1 = o + (int)((w >> 8) & 0xffu);
     if constexpr (D == 2) {
-      dacc = df_acc(dacc, df2{p0.x, p0.y});
-      acc[c0] = df_acc(acc[c0], df2{p0.z, p0.w});
-      acc[c1] = df_acc(acc[c1], df2{p1.x, p1.y});
+      const df2 o1 = {p0.x, p0.y}, o2 = {p0.z, p0.w};
+      dacc = df_acc(dacc, df_neg(df_add(o1, o2)));  // a_ii = -(a_ij + a_ik), as the element routine forms it
+      acc[c0] = df_acc(acc[c0], o1);
+      acc[c1] = df_acc(acc[c1], o2);
     } else {
       const df2 o1 = {p0.x, p0.y}, o2 = {p0.z, p0.w}, o3 = {p1.x, p1.y};
       const int c2 = o + (int)((w >> 16) & 0xffu);
@@ -144,7 +157,10 @@ __device__ __forceinline__ void add_packet(const float4& p0, const float4& p1, u
       acc[c2] = df_acc(acc[c2], o3);
     }
   }
-  if (want_b) bacc = df_acc(bacc, df2{p1.z, p1.w});
+  if (want_b) {
+    if constexpr (D == 2) bacc = df_acc(bacc, df2{p1.x, p1.y});
+    else bacc = df_acc(bacc, df2{p1.z, p1.w});
+  }
 }
 
 // packet load: read-only path in the two-launch form; L2 (coherent) path when the packets were written
@@ -153,6 +169,35 @@ template <bool FRESH>
 __device__ __forceinline__ float4 load_packet_half(const float4* p) {
   if constexpr (FRESH) return __ldcg(p);
   else return __ldg(p);
+}
+template <bool FRESH>
+__device__ __forceinline__ float2 load_pair(const float2* p) {
+  if constexpr (FRESH) return __ldcg(p);
+  else return __ldg(p);
+}
+// packet q as (p0, p1): 2-D three float pairs (24 bytes: a_ij, a_ik, b_i), 3-D four (32 bytes)
+template <int D, bool FRESH>
+__device__ __forceinline__ void load_packet(const float4* pk, int64_t q, float4& p0, float4& p1) {
+  if constexpr (D == 2) {
+    const float2* b = reinterpret_cast<const float2*>(pk) + 3 * q;
+    if (FRESH && (q & 1) == 0) {  // through L2: fewer, wider loads where the slot is 16-byte aligned
+      p0 = load_packet_half<FRESH>(reinterpret_cast<const float4*>(b));
+      const float2 z = load_pair<FRESH>(b + 2);
+      p1 = make_float4(z.x, z.y, 0.0f, 0.0f);
+    } else if (FRESH) {
+      const float2 x = load_pair<FRESH>(b);
+      const float4 yz = load_packet_half<FRESH>(reinterpret_cast<const float4*>(b + 1));
+      p0 = make_float4(x.x, x.y, yz.x, yz.y);
+      p1 = make_float4(yz.z, yz.w, 0.0f, 0.0f);
+    } else {
+      const float2 x = load_pair<FRESH>(b), y = load_pair<FRESH>(b + 1), z = load_pair<FRESH>(b + 2);
+      p0 = make_float4(x.x, x.y, y.x, y.y);
+      p1 = make_float4(z.x, z.y, 0.0f, 0.0f);
+    }
+  } else {
+    p0 = load_packet_half<FRESH>(pk + 2 * q);
+    p1 = load_packet_half<FRESH>(pk + 2 * q + 1);
+  }
 }
 
 // Phase 2 for the 32 rows R0 .. R0+31 of one warp. A row's packets are contiguous; each thread loads U
@@ -183,16 +228,17 @@ __device__ __forceinline__ void rows_of_warp(const RowArgs& g, int64_t R0, df2* 
       uint32_t w[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        x0[u] = load_packet_half<FRESH>(g.pk + 2 * (size_t)(q + u));
-        x1[u] = load_packet_half<FRESH>(g.pk + 2 * (size_t)(q + u) + 1);
+        load_packet<D, FRESH>(g.pk, q + u, x0[u], x1[u]);
         w[u] = (uint32_t)__ldg(pw + q + u);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) add_packet<D>(x0[u], x1[u], w[u], o, acc, dacc, bacc, want_a, want_b);
     }
-    for (; q < q1; ++q)
-      add_packet<D>(load_packet_half<FRESH>(g.pk + 2 * (size_t)q), load_packet_half<FRESH>(g.pk + 2 * (size_t)q + 1),
-                    (uint32_t)__ldg(pw + q), o, acc, dacc, bacc, want_a, want_b);
+    for (; q < q1; ++q) {
+      float4 x0, x1;
+      load_packet<D, FRESH>(g.pk, q, x0, x1);
+      add_packet<D>(x0, x1, (uint32_t)__ldg(pw + q), o, acc, dacc, bacc, want_a, want_b);
+    }
     if (want_a && rl > 0) acc[o + __ldg(g.rdp + R)] = dacc;
     if (want_b) bvec[R] = df_to_double(bacc);
   }
