@@ -398,7 +398,7 @@ int assemble_backward(const Pattern* P, const double* node, const double* k, int
   }
   const TilePlan& T = P->tile;
   if (T.ok && T.pk && (T.TE == 128 || T.TE == 256)) {
-    const int smem = ((T.max_v * P->d * (int)sizeof(f3)) + 15) / 16 * 16;
+    const int smem = ((T.max_v * vtx_bytes(P->d)) + 15) / 16 * 16;
     const int g2 = (N + 255) / 256;
 #define FEM_BWD_TILES(DD, TT)                                                                                      \
   FEM_LAUNCH((k_backward_tiles<DD, TT>), T.ntiles, TT, smem, s, P->NT, T.elist, T.lelem, T.voff, T.vlist, T.ipos, \

@@ -18,7 +18,8 @@
 
 namespace fem {
 
-struct df2 {
+// 8-byte aligned so that one 64-bit shared-memory access moves a pair
+struct __align__(8) df2 {
   float h, l;
 };
 

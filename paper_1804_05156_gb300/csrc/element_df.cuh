@@ -21,12 +21,14 @@ namespace fem {
 // Staged vertex: exact splits of the coordinates, and for the sine-product load the values
 // sin(pi x/2), cos(pi x/2) of each coordinate (df).
 template <int D>
-struct VtxDF {
+struct __align__(16) VtxDF {  // 16-byte aligned: staged vertices are read with 128-bit accesses
   f3 x[D];
 };
-struct SC {
+struct __align__(16) SC {
   df2 s, c;
 };
+// bytes of one staged vertex in shared memory
+inline int vtx_bytes(int d) { return d == 2 ? (int)sizeof(VtxDF<2>) : (int)sizeof(VtxDF<3>); }
 
 template <int D>
 struct LocalDF {

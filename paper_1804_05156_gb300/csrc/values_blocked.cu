@@ -281,7 +281,7 @@ int blocked_smem_budget(int ctas_per_sm) {
 
 int blocked_smem_need(const BlockPlan& B, int d, bool sinprod) {
   const int W = (d + 1) * (d + 2) / 2 + d + 1;
-  return B.max_v * d * 12 + (sinprod && d == 2 ? B.max_v * d * 16 : 0) + B.max_acc * 12 + B.V * (8 + 24) +
+  return B.max_v * vtx_bytes(d) + (sinprod && d == 2 ? B.max_v * d * (int)sizeof(SC) : 0) + B.max_acc * 12 + B.V * (8 + 24) +
          B.max_rec * 4 + B.max_e * 20 + 32 * W * 8 + 256;
 }
 
@@ -317,7 +317,7 @@ int assemble_blocked(const Pattern* P, const double* node, const double* k, int 
   a.row_ptr = P->row_ptr;
   // Shared memory per CTA: what the plan's launch shape (threads x CTAs per SM) leaves per CTA.
   const int budget = blocked_smem_budget(B.minb);
-  a.xs_bytes = ((B.max_v * D * (int)sizeof(f3)) + 15) / 16 * 16;
+  a.xs_bytes = ((B.max_v * vtx_bytes(D)) + 15) / 16 * 16;
   a.sc_bytes = (D == 2 && f_kind == FEM_F_SINPROD) ? ((B.max_v * D * (int)sizeof(SC)) + 15) / 16 * 16 : 0;
   a.acc_bytes = ((B.max_acc * 8) + 15) / 16 * 16;
   a.rec_bytes = ((B.max_rec * 4) + 15) / 16 * 16;

@@ -337,7 +337,7 @@ int gather_warps(int max_row) {
 }  // namespace
 
 int tile_smem_need(const TilePlan& T, int d, bool sinprod) {
-  const int xs = ((T.max_v * d * (int)sizeof(f3)) + 15) / 16 * 16;
+  const int xs = ((T.max_v * vtx_bytes(d)) + 15) / 16 * 16;
   return xs + ((sinprod && d == 2) ? T.max_v * d * (int)sizeof(SC) : 0);
 }
 
@@ -371,7 +371,7 @@ int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_
   a.vlist = T.vlist;
   a.ipos = T.ipos;
   a.pk = T.pk;
-  a.xs_bytes = ((T.max_v * D * (int)sizeof(f3)) + 15) / 16 * 16;
+  a.xs_bytes = ((T.max_v * vtx_bytes(D)) + 15) / 16 * 16;
   RowArgs g;
   g.N = P->N;
   g.max_row = T.max_row > 0 ? T.max_row : 1;
