@@ -80,10 +80,28 @@ __device__ __forceinline__ df2 df_recip(df2 a) {
 // Sum over m of a_m * b_m for df vectors, relative error ~2^-46 against sum_m |a_m b_m|.
 template <int D>
 __device__ __forceinline__ df2 df_dot(const df2 (&a)[D], const df2 (&b)[D]) {
-  df2 s = df_mul(a[0], b[0]);
+  // leading products exact (product + FMA residual), their sum by two-sum; residuals, cross terms and
+  // the sum's own errors gathered in one float; one renormalisation at the end
+  float s = __fmul_rn(a[0].h, b[0].h);
+  float t = __fmaf_rn(a[0].h, b[0].h, -s);
+  t = __fmaf_rn(a[0].h, b[0].l, t);
+  t = __fmaf_rn(a[0].l, b[0].h, t);
 #pragma unroll
-  for (int m = 1; m < D; ++m) s = df_add(s, df_mul(a[m], b[m]));
-  return s;
+  for (int m = 1; m < D; ++m) {
+    const float p = __fmul_rn(a[m].h, b[m].h);
+    const float e = __fmaf_rn(a[m].h, b[m].h, -p);
+    const df2 u = two_sum(s, p);
+    s = u.h;
+    t = __fadd_rn(t, __fadd_rn(u.l, e));
+    t = __fmaf_rn(a[m].h, b[m].l, t);
+    t = __fmaf_rn(a[m].l, b[m].h, t);
+  }
+  return fast_two_sum(s, t);
+}
+// a0 b0 - a1 b1, the same way
+__device__ __forceinline__ df2 df_dot2m(df2 a0, df2 b0, df2 a1, df2 b1) {
+  const df2 A[2] = {a0, df_neg(a1)}, B[2] = {b0, b1};
+  return df_dot<2>(A, B);
 }
 
 // ---- doubles in -----------------------------------------------------------------------------------

@@ -67,7 +67,7 @@ __device__ __forceinline__ bool element_df2(const VtxDF<2>* const (&V)[3], const
     e[1][m] = f3_diff(V[0]->x[m], V[2]->x[m]);
     e[2][m] = f3_diff(V[1]->x[m], V[0]->x[m]);
   }
-  const df2 a2 = df_sub(df_mul(e[1][0], e[2][1]), df_mul(e[1][1], e[2][0]));  // twice the signed area
+  const df2 a2 = df_dot2m(e[1][0], e[2][1], e[1][1], e[2][0]);  // twice the signed area
   const df2 a2abs = a2.h < 0.0f ? df_neg(a2) : a2;
   const bool ok = a2abs.h > 0.0f && a2abs.h < INFINITY;
   if (want_a) {
@@ -108,9 +108,9 @@ __device__ __forceinline__ bool element_df2(const VtxDF<2>* const (&V)[3], const
 }
 
 __device__ __forceinline__ void df_cross(const df2 (&u)[3], const df2 (&v)[3], df2 (&o)[3]) {
-  o[0] = df_sub(df_mul(u[1], v[2]), df_mul(u[2], v[1]));
-  o[1] = df_sub(df_mul(u[2], v[0]), df_mul(u[0], v[2]));
-  o[2] = df_sub(df_mul(u[0], v[1]), df_mul(u[1], v[0]));
+  o[0] = df_dot2m(u[1], v[2], u[2], v[1]);
+  o[1] = df_dot2m(u[2], v[0], u[0], v[2]);
+  o[2] = df_dot2m(u[0], v[1], u[1], v[0]);
 }
 
 // want_diag = false leaves L.a[0..3] (the diagonals) unset, for callers that re-form them.
