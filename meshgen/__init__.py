@@ -169,6 +169,27 @@ def kuhn_mesh(n: int, jitter: float = 0.0, seed: int = 0) -> dict:
             "is_bd": onb.astype(np.uint8), "bdflag": bd}
 
 
+def side_flags(mesh: dict, faces: dict) -> np.ndarray:
+    """bdFlag [NT, d+1] (int8) for the unit square / cube meshes above: every boundary side gets the
+    flag its face name maps to ("x0", "x1", "y0", "y1", and "z0", "z1" in 3-D; missing names give 1),
+    interior sides 0. Boundary nodes are not jittered, so a side lies on face "x0" when all its
+    vertices have x == 0 exactly."""
+    d, node, elem, bd = mesh["d"], mesh["node"], mesh["elem"], mesh["bdflag"]
+    out = np.zeros(bd.shape, dtype=np.int8)
+    names = ["x", "y", "z"][:d]
+    for j in range(d + 1):
+        others = [k for k in range(d + 1) if k != j]
+        xs = node[elem[:, others]]  # [NT, d, d]
+        onb = bd[:, j] != 0
+        flag = np.where(onb, 1, 0).astype(np.int8)
+        for ax, nm in enumerate(names):
+            for val, tag in ((0.0, "0"), (1.0, "1")):
+                on = onb & np.all(xs[:, :, ax] == val, axis=1)
+                flag[on] = faces.get(nm + tag, 1)
+        out[:, j] = flag
+    return out
+
+
 def batch_sides(seed: int = 1806, count: int = 256, lo: int = 16, hi: int = 512) -> np.ndarray:
     """Mesh sides n uniform on {lo, ..., hi}."""
     u = uniform(seed, TAG_SIDES, count)

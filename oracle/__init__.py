@@ -58,6 +58,14 @@ def _load():
         lib.ora_backward.argtypes = [I32, I64, I64, P, P, P, I32, P, P, P, P, P, P]
         lib.ora_local_affine.restype = I32
         lib.ora_local_affine.argtypes = [P, P]
+        lib.ora_boundary_terms.restype = I32
+        lib.ora_boundary_terms.argtypes = [I32, I64, I64, P, P, P, P, C.c_double, C.c_double, P, P, P, P]
+        lib.ora_side_points.restype = I32
+        lib.ora_side_points.argtypes = [I32, I64, P, P, P]
+        lib.ora_mean_shift.restype = I32
+        lib.ora_mean_shift.argtypes = [I64, P]
+        lib.ora_zero_average.restype = I32
+        lib.ora_zero_average.argtypes = [I32, I64, I64, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -199,3 +207,37 @@ def local_affine(p):
     At = np.zeros((3, 3), np.float64)
     _check(_load().ora_local_affine(_p(p), _p(At)))
     return At
+
+
+def boundary_terms(d, node, elem, bdflag, row_ptr, col, val, b, g_side=None, g_const=0.0, alpha=0.0):
+    """(val', b') after the Neumann (bdflag 2) and Robin (bdflag 3) side terms (inputs not modified)."""
+    node, elem, bdflag = _c(node, np.float64), _c(elem, np.int32), _c(bdflag, np.int8)
+    row_ptr, col, g_side = _c(row_ptr, np.int64), _c(col, np.int64), _c(g_side, np.float64)
+    val, b = np.array(val, np.float64, copy=True), np.array(b, np.float64, copy=True)
+    _check(_load().ora_boundary_terms(d, node.shape[0], elem.shape[0], _p(node), _p(elem), _p(bdflag), _p(g_side),
+                                      float(g_const), float(alpha), _p(row_ptr), _p(col), _p(val), _p(b)))
+    return val, b
+
+
+def side_points(d, node, elem):
+    """Quadrature point of every side (midpoint 2-D, centroid 3-D): [NT, d+1, d]."""
+    node, elem = _c(node, np.float64), _c(elem, np.int32)
+    out = np.zeros((elem.shape[0], d + 1, d), np.float64)
+    _check(_load().ora_side_points(d, elem.shape[0], _p(node), _p(elem), _p(out)))
+    return out
+
+
+def mean_shift(b):
+    """b - mean(b)."""
+    out = np.array(b, np.float64, copy=True)
+    _check(_load().ora_mean_shift(out.size, _p(out)))
+    return out
+
+
+def zero_average(d, node, elem, u):
+    """(u - c, c) with c the area-weighted mean of the P1 function u."""
+    node, elem = _c(node, np.float64), _c(elem, np.int32)
+    out = np.array(u, np.float64, copy=True)
+    c = np.zeros(1, np.float64)
+    _check(_load().ora_zero_average(d, node.shape[0], elem.shape[0], _p(node), _p(elem), _p(out), _p(c)))
+    return out, float(c[0])

@@ -31,6 +31,11 @@
  *                     d|tau|/dx_m = |tau| g_m and dg_i/dx_m = -g_m g_i^T (g_i = grad lambda_i).
  *   ora_local_affine  Sec. 3.1.1 local stiffness by the affine map to the reference triangle
  *                     (a second, independent formula used only to pin the first).
+ *   ora_boundary_terms  Neumann (bdFlag 2) and Robin (bdFlag 3) sides: the one-point side rule of the
+ *                     paper's Neumann code (Sec. 3.3) for the load, and the side mass matrix for Robin.
+ *   ora_side_points   the quadrature point (midpoint / centroid) of every side.
+ *   ora_mean_shift    the pure-Neumann compatibility fix b - mean(b) (Sec. 3.3).
+ *   ora_zero_average  u - c with c the area-weighted mean of u (Sec. 3.3), the zero-average constraint.
  */
 #include <math.h>
 #include <stdint.h>
@@ -576,5 +581,134 @@ int ora_local_affine(const double* p /* 3x2 row-major */, double* At /* 3x3 */) 
   }
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) At[3 * i + j] = area * (y[i][0] * y[j][0] + y[i][1] * y[j][1]);
+  return ORA_OK;
+}
+
+/* ------------------------------------------------------------------------------------------------
+ * Neumann and Robin sides ("Boundary conditions" and Sec. 3.3), and the pure-Neumann fixes.
+ *
+ * bdFlag(t, j) = 2 marks the side opposite vertex j of element t as Neumann, 3 as Robin
+ * (du/dn + alpha u = g_R). The side's vertices are the element's other d vertices, taken in
+ * ascending local index. Its measure |s|: 2-D the edge length sqrt(dx^2 + dy^2); 3-D the triangle
+ * area |(p1 - p0) x (p2 - p0)| / 2.
+ *   Neumann and Robin load: b[v] += (|s| * g) / d for each vertex v of the side, g the side's value
+ *   (g_side[t][j], or g_const when g_side is NULL) at its midpoint (2-D, the paper's rule) or centroid
+ *   (3-D reading: the same one-point rule on a triangle).
+ *   Robin matrix: alpha * integral over the side of lambda_a lambda_b = alpha |s| (1 + delta_ab) / (d (d+1))
+ *   added to the CSR entry (a, b) for every pair of the side's vertices (a 1-D or 2-D mass matrix).
+ * Contributions are added element by element (t ascending), side by side (j ascending), vertex by
+ * vertex (ascending local index), each as ((alpha * |s|) * w) / (d (d+1)) and (|s| * g) / d in that
+ * order, without contraction.
+ * ------------------------------------------------------------------------------------------------ */
+static double side_measure(int d, const double* node, const int32_t* e, int j) {
+  int32_t v[3];
+  int c = 0;
+  for (int k = 0; k <= d; ++k)
+    if (k != j) v[c++] = e[k];
+  if (d == 2) {
+    const double dx = node[2 * v[1]] - node[2 * v[0]], dy = node[2 * v[1] + 1] - node[2 * v[0] + 1];
+    return sqrt(dx * dx + dy * dy);
+  }
+  double u[3], w[3], x[3];
+  for (int m = 0; m < 3; ++m) {
+    u[m] = node[3 * v[1] + m] - node[3 * v[0] + m];
+    w[m] = node[3 * v[2] + m] - node[3 * v[0] + m];
+  }
+  x[0] = u[1] * w[2] - u[2] * w[1];
+  x[1] = u[2] * w[0] - u[0] * w[2];
+  x[2] = u[0] * w[1] - u[1] * w[0];
+  return sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]) * 0.5;
+}
+
+static int64_t find_col(const int64_t* row_ptr, const int64_t* col, int64_t r, int64_t c) {
+  int64_t lo = row_ptr[r], hi = row_ptr[r + 1];
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) / 2;
+    if (col[mid] < c) lo = mid + 1;
+    else hi = mid;
+  }
+  return (lo < row_ptr[r + 1] && col[lo] == c) ? lo : -1;
+}
+
+int ora_boundary_terms(int d, int64_t N, int64_t NT, const double* node, const int32_t* elem, const int8_t* bdflag,
+                       const double* g_side, double g_const, double alpha, const int64_t* row_ptr,
+                       const int64_t* col, double* val, double* b) {
+  if (d != 2 && d != 3) return ORA_ERR_ARG;
+  const int d1 = d + 1;
+  for (int64_t t = 0; t < NT; ++t) {
+    const int32_t* e = elem + t * d1;
+    for (int j = 0; j < d1; ++j) {
+      const int flag = bdflag[t * d1 + j];
+      if (flag != 2 && flag != 3) continue;
+      const double m = side_measure(d, node, e, j);
+      const double g = g_side ? g_side[t * d1 + j] : g_const;
+      for (int a = 0; a < d1; ++a) {
+        if (a == j) continue;
+        if (e[a] < 0 || e[a] >= N) return ORA_ERR_INDEX;
+        if (b) b[e[a]] = b[e[a]] + (m * g) / (double)d;
+        if (flag == 3 && val) {
+          for (int c = 0; c < d1; ++c) {
+            if (c == j) continue;
+            const int64_t pos = find_col(row_ptr, col, e[a], e[c]);
+            if (pos < 0) return ORA_ERR_INDEX;
+            const double wgt = (a == c) ? 2.0 : 1.0;
+            val[pos] = val[pos] + ((alpha * m) * wgt) / (double)(d * d1);
+          }
+        }
+      }
+    }
+  }
+  return ORA_OK;
+}
+
+/* quadrature point of every side: the midpoint (2-D) or centroid (3-D) of its vertices, [NT][d+1][d] */
+int ora_side_points(int d, int64_t NT, const double* node, const int32_t* elem, double* pts) {
+  if (d != 2 && d != 3) return ORA_ERR_ARG;
+  const int d1 = d + 1;
+  for (int64_t t = 0; t < NT; ++t)
+    for (int j = 0; j < d1; ++j)
+      for (int m = 0; m < d; ++m) {
+        double s = 0.0;
+        for (int k = 0; k < d1; ++k)
+          if (k != j) s = s + node[(int64_t)elem[t * d1 + k] * d + m];
+        pts[(t * d1 + j) * d + m] = s / (double)d;
+      }
+  return ORA_OK;
+}
+
+/* pure Neumann: b <- b - mean(b), the mean summed in index order */
+int ora_mean_shift(int64_t N, double* b) {
+  if (N <= 0) return ORA_OK;
+  double s = 0.0;
+  for (int64_t i = 0; i < N; ++i) s = s + b[i];
+  const double mean = s / (double)N;
+  for (int64_t i = 0; i < N; ++i) b[i] = b[i] - mean;
+  return ORA_OK;
+}
+
+/* zero average: c = sum_t mean(u(elem_t)) |tau_t| / sum_t |tau_t| (2-D |area|, 3-D signed volume), u <- u - c */
+int ora_zero_average(int d, int64_t N, int64_t NT, const double* node, const int32_t* elem, double* u,
+                     double* c_out) {
+  if (d != 2 && d != 3) return ORA_ERR_ARG;
+  const int d1 = d + 1;
+  double* meas = (double*)malloc(sizeof(double) * (NT > 0 ? NT : 1));
+  if (!meas) return ORA_ERR_OOM;
+  int rc = ora_measure(d, N, NT, node, elem, meas);
+  if (rc) {
+    free(meas);
+    return rc;
+  }
+  double num = 0.0, den = 0.0;
+  for (int64_t t = 0; t < NT; ++t) {
+    double s = 0.0;
+    for (int i = 0; i < d1; ++i) s = s + u[elem[t * d1 + i]];
+    const double area = d == 2 ? fabs(meas[t]) : meas[t];
+    num = num + (s / (double)d1) * area;
+    den = den + area;
+  }
+  free(meas);
+  const double c = den > 0.0 ? num / den : 0.0;
+  for (int64_t v = 0; v < N; ++v) u[v] = u[v] - c;
+  if (c_out) *c_out = c;
   return ORA_OK;
 }

@@ -448,3 +448,137 @@ def test_backward_invariants(d):
     homog = float((node * gn).sum())
     assert abs(homog - (d - 2) * L) <= 1e-12 * scale
     assert abs(float(k @ gk) - L) <= 1e-12 * (abs(L) + float(np.abs(k * gk).sum()))
+
+
+# --- Neumann / Robin sides and the pure-Neumann fixes (Sec. 3.3 and "Boundary conditions") --------
+
+def _geometry(d, n, jitter, seed):
+    return meshgen.square_mesh(n, jitter, seed) if d == 2 else meshgen.kuhn_mesh(n, jitter, seed)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_neumann_constant_g_integrates_the_side_measure(d):
+    """Constant g: the side rule is exact, so the Neumann load sums to g |Gamma_N| and each vertex gets
+    g times a d-th of its incident Neumann sides' measure."""
+    m = _geometry(d, 5, 0.2, 31)
+    node, elem = m["node"], m["elem"]
+    N = node.shape[0]
+    flags = meshgen.side_flags(m, {"x0": 2, "x1": 2})  # two opposite faces of measure 1 each
+    rp, col = oracle.pattern(d, N, elem)
+    z = np.zeros(rp[-1])
+    _, b = oracle.boundary_terms(d, node, elem, flags, rp, col, z, np.zeros(N), g_const=2.5)
+    assert abs(b.sum() - 2.5 * 2.0) <= 1e-14
+    # only vertices on the two faces receive load; on x = 0 (2-D) each vertex gets g times half the
+    # lengths of its two boundary edges
+    x0 = np.isclose(node[:, 0], 0.0)
+    assert np.all(b[~(x0 | np.isclose(node[:, 0], 1.0))] == 0.0)
+    if d == 2:
+        ys = np.sort(node[x0, 1])
+        h = np.diff(ys)
+        exp = np.zeros(ys.size)
+        exp[:-1] += h / 2
+        exp[1:] += h / 2
+        order = np.argsort(node[x0, 1])
+        assert np.allclose(b[x0][order], 2.5 * exp, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_robin_side_mass_matrix(d):
+    """The Robin matrix is alpha times the side mass matrix: u^T M u = alpha int u^2 over Gamma_R, exact for
+    linear u (u = 1 gives alpha |Gamma_R|; u = x on the face y = 1 (2-D) or z = 1 (3-D) gives alpha/3)."""
+    m = _geometry(d, 4, 0.2, 32)
+    node, elem = m["node"], m["elem"]
+    N = node.shape[0]
+    face = "y1" if d == 2 else "z1"
+    flags = meshgen.side_flags(m, {face: 3})
+    rp, col = oracle.pattern(d, N, elem)
+    val, _ = oracle.boundary_terms(d, node, elem, flags, rp, col, np.zeros(rp[-1]), np.zeros(N), alpha=1.7)
+    M = dense_from_csr(rp, col, val, N)
+    assert np.array_equal(M, M.T)
+    one = np.ones(N)
+    assert abs(one @ M @ one - 1.7) <= 1e-14
+    x = node[:, 0]
+    assert abs(x @ M @ x - 1.7 / 3.0) <= 1e-14
+    # Robin sides add no load when g = 0, and the load matches the Neumann rule when g != 0
+    _, b = oracle.boundary_terms(d, node, elem, flags, rp, col, np.zeros(rp[-1]), np.zeros(N), g_const=1.0, alpha=1.7)
+    assert abs(b.sum() - 1.0) <= 1e-14
+
+
+def test_side_points_are_midpoints_and_centroids():
+    m = meshgen.square_mesh(3, 0.2, 33)
+    p = oracle.side_points(2, m["node"], m["elem"])
+    e = m["elem"]
+    for t in range(e.shape[0]):
+        for j in range(3):
+            a, b = [e[t, k] for k in range(3) if k != j]
+            assert np.array_equal(p[t, j], (m["node"][a] + m["node"][b]) / 2)
+    m3 = meshgen.kuhn_mesh(2, 0.1, 33)
+    p3 = oracle.side_points(3, m3["node"], m3["elem"])
+    e3 = m3["elem"]
+    assert np.allclose(p3[:, 0], m3["node"][e3[:, 1:]].mean(axis=1), rtol=1e-15, atol=1e-16)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_pure_neumann_reproduces_linear_solution(d):
+    """-Laplace u = 0 with du/dn = g on the whole boundary, u = c + x - 2y (+ 0.5 z): g is constant on each
+    face, so the side rule is exact, mean(b) = 0 up to rounding, and the solve with freeNode = 2:N followed by
+    the zero-average shift returns the zero-average linear function."""
+    m = _geometry(d, 6, 0.2, 34)
+    node, elem = m["node"], m["elem"]
+    N = node.shape[0]
+    grad = np.array([1.0, -2.0, 0.5])[:d]
+    faces = {"x0": 10, "x1": 11, "y0": 20, "y1": 21, "z0": 30, "z1": 31}
+    flags = meshgen.side_flags(m, faces)
+    g_side = np.zeros(flags.shape)
+    for nm, code in faces.items():
+        ax, sgn = "xyz".index(nm[0]), (1.0 if nm[1] == "1" else -1.0)
+        if ax < d:
+            g_side[flags == code] = sgn * grad[ax]
+    neu = np.where(flags > 1, 2, flags).astype(np.int8)
+    rp, col, val, _ = oracle.assemble(d, node, elem)
+    _, b = oracle.boundary_terms(d, node, elem, neu, rp, col, val, np.zeros(N), g_side=g_side)
+    assert abs(b.mean()) <= 1e-15
+    b = oracle.mean_shift(b)
+    assert abs(b.sum()) <= 1e-14
+    A = dense_from_csr(rp, col, val, N)
+    u = np.zeros(N)
+    u[1:] = np.linalg.solve(A[1:, 1:], b[1:])
+    u0, _ = oracle.zero_average(d, node, elem, u)
+    exact, _ = oracle.zero_average(d, node, elem, node @ grad)
+    assert np.allclose(u0, exact, rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_robin_and_dirichlet_reproduce_linear_solution(d):
+    """u = 1 + x: Dirichlet u = 1 on x = 0, Robin du/dn + alpha u = 1 + 2 alpha on x = 1 (u = 2 there),
+    zero Neumann elsewhere. The Robin matrix is exact for the linear u and the load for the constant g, so
+    the solution is u at every node."""
+    m = _geometry(d, 5, 0.2, 35)
+    node, elem = m["node"], m["elem"]
+    N = node.shape[0]
+    alpha = 0.7
+    faces = {"x0": 1, "x1": 3, "y0": 2, "y1": 2, "z0": 2, "z1": 2}
+    flags = meshgen.side_flags(m, faces)
+    g_side = np.where(flags == 3, 1.0 + 2.0 * alpha, 0.0)
+    rp, col, val, _ = oracle.assemble(d, node, elem)
+    val, b = oracle.boundary_terms(d, node, elem, flags, rp, col, val, np.zeros(N), g_side=g_side, alpha=alpha)
+    isbd = oracle.boundary(d, N, elem, flags)
+    gD = 1.0 + node[:, 0]
+    val2, b2, free = oracle.dirichlet(rp, col, val, b, isbd, gD)
+    A2 = dense_from_csr(rp, col, val2, N)
+    assert np.allclose(np.linalg.solve(A2, b2), gD, rtol=0, atol=1e-12)
+
+
+def test_mean_shift_and_zero_average():
+    m = meshgen.square_mesh(7, 0.2, 36)
+    rng = np.random.default_rng(36)
+    b = rng.normal(size=m["node"].shape[0]) + 3.0
+    s = oracle.mean_shift(b)
+    assert abs(s.mean()) <= 1e-14 * np.abs(b).max() and np.allclose(s - b, -b.mean(), rtol=0, atol=1e-14)
+    u = rng.normal(size=b.size)
+    u0, c = oracle.zero_average(2, m["node"], m["elem"], u)
+    meas = np.abs(oracle.measure(2, m["node"], m["elem"]))
+    assert abs((u0[m["elem"]].mean(axis=1) * meas).sum()) <= 1e-14 * np.abs(u).max()
+    # a constant function's average is the constant
+    _, c1 = oracle.zero_average(2, m["node"], m["elem"], np.full(b.size, 4.25))
+    assert abs(c1 - 4.25) <= 1e-15
