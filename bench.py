@@ -455,6 +455,16 @@ def run_ours(args):
     ms_di = _time_steps(dirich, max(3, min(args.steps, 10)), flush, s)
     out["atomic_variant"] = {"ms": ms_at, "Melem_s": NT / (ms_at * 1e-3) / 1e6}
     out["dirichlet_ms"] = ms_di
+    if "bdflag" in mesh and args.shard != "rows":
+        # Neumann on x = 0 and x = 1, Robin on y = 1, Dirichlet on y = 0 (the mixed problem of Sec. 3.3)
+        faces = {"x0": 2, "x1": 2, "y1": 3, "y0": 1, "z0": 2, "z1": 3}
+        flags = torch.as_tensor(meshgen.side_flags(mesh, faces)).cuda()
+        fa.fem_assemble(p, node_d, k_d, f_kind, None, val, b, variant)
+        steps_b = max(3, min(args.steps, 10))
+        ms_nr = _time_steps(lambda: fa.fem_boundary_terms(p, node_d, flags, None, 1.0, 1.0, val, b), steps_b, flush, s)
+        ms_ms = _time_steps(lambda: fa.fem_mean_shift(b), steps_b, flush, s)
+        ms_za = _time_steps(lambda: fa.fem_zero_average(p, node_d, b), steps_b, flush, s)
+        out["neumann_robin"] = {"boundary_terms_ms": ms_nr, "mean_shift_ms": ms_ms, "zero_average_ms": ms_za}
     if not args.no_extras and ws == 1:
         out["extras"] = extras(fa, args, flush, value)
     if rank == 0 and not args.no_cpu_baseline:

@@ -163,6 +163,27 @@ int fem_boundary_nodes(fem_pattern_t p, const int8_t* bdflag, uint8_t* is_bd, fe
 int fem_apply_dirichlet(fem_pattern_t p, const uint8_t* is_bd, const double* gD, double* val, double* b,
                         int32_t* free_node, int64_t* n_free, fem_stream_t stream);
 
+/* ---- Neumann and Robin sides, pure-Neumann fixes ("Boundary conditions", Sec. 3.3) --------------
+ * Side j of element t is the side opposite local vertex j; bdflag [NT][d+1] (int8, device) = 2 marks it
+ * Neumann, 3 Robin (du/dn + alpha u = g). Its vertices are the element's other d vertices; |s| is the
+ * edge length (2-D) or triangle area (3-D). g is the side's value at its quadrature point, the midpoint
+ * (2-D, the paper's rule) or centroid (3-D): g_side [NT][d+1] (device, nullable: g_const for every side).
+ * Adds to b (nullable) |s| g / d for each vertex of each flagged side, and to val (nullable) for each
+ * Robin side alpha |s| (1 + delta_ab) / (d (d+1)) at the CSR entry of every pair (a, b) of its vertices
+ * (the side mass matrix). Each row is updated by one thread in ascending element order, then ascending
+ * side, with uncontracted FP64 operations: deterministic. Flags 0 and 1 are ignored. */
+int fem_boundary_terms(fem_pattern_t p, const double* node, const int8_t* bdflag, const double* g_side, double g_const,
+                       double alpha, double* val, double* b, fem_stream_t stream);
+/* The quadrature point of every side (the mean of its vertices): pts [NT][d+1][d] (device). */
+int fem_side_points(fem_pattern_t p, const double* node, double* pts, fem_stream_t stream);
+/* Pure Neumann compatibility: x <- x - mean(x) for a device array of n doubles; the sum is a fixed-shape
+ * FP64 reduction (deterministic). Allocates a few KB of stream-ordered scratch. */
+int fem_mean_shift(double* x, int64_t n, fem_stream_t stream);
+/* Zero average: u <- u - c with c = sum_t mean(u over tau_t) |tau_t| / sum_t |tau_t| (2-D |area|, 3-D
+ * signed volume), the constraint that fixes the constant of a pure-Neumann solution; c_out (device,
+ * nullable) receives c. Fixed-shape FP64 reduction (deterministic). */
+int fem_zero_average(fem_pattern_t p, const double* node, double* u, double* c_out, fem_stream_t stream);
+
 /* ---- backward (gradients of the assembled system) ----------------------------------------------
  * For L = sum_s w[s] val[s] + sum_i r[i] b[i] (w [nnz], r [N]; either may be NULL = 0), writes
  * gnode [N][d] = dL/dnode and gk [NT] = dL/dk (either may be NULL to skip). The basis gradients are

@@ -61,6 +61,10 @@ def lib():
             "fem_boundary_nodes": (I32, [P, P, P, P]),
             "fem_apply_dirichlet": (I32, [P, P, P, P, P, P, P, P]),
             "fem_assemble_backward": (I32, [P, P, P, I32, P, P, P, P, P, P]),
+            "fem_boundary_terms": (I32, [P, P, P, P, C.c_double, C.c_double, P, P, P]),
+            "fem_side_points": (I32, [P, P, P, P]),
+            "fem_mean_shift": (I32, [P, C.c_int64, P]),
+            "fem_zero_average": (I32, [P, P, P, P, P]),
             "fem_batch_plan": (I32, [I32, I32, P, P, P, P, P]),
             "fem_batch_info": (I32, [P, P, P, P, P, P]),
             "fem_batch_set_locality": (I32, [P, P, P]),
@@ -202,6 +206,24 @@ def fem_pattern_value_path(p: Pattern) -> dict:
 
 def fem_pattern_force_path(p: Pattern, path: int, tile_elems: int = 256, stream=None):
     _check(lib().fem_pattern_force_path(p.handle, path, tile_elems, _stream(stream)))
+
+
+def fem_boundary_terms(p: Pattern, node, bdflag, g_side=None, g_const=0.0, alpha=0.0, val=None, b=None, stream=None):
+    """Neumann (bdflag 2) and Robin (bdflag 3) side terms added to val and b in place."""
+    _check(lib().fem_boundary_terms(p.handle, _ptr(node), _ptr(bdflag), _ptr(g_side), float(g_const), float(alpha),
+                                    _ptr(val), _ptr(b), _stream(stream)))
+
+
+def fem_side_points(p: Pattern, node, pts, stream=None):
+    _check(lib().fem_side_points(p.handle, _ptr(node), _ptr(pts), _stream(stream)))
+
+
+def fem_mean_shift(x, stream=None):
+    _check(lib().fem_mean_shift(_ptr(x), x.numel(), _stream(stream)))
+
+
+def fem_zero_average(p: Pattern, node, u, c_out=None, stream=None):
+    _check(lib().fem_zero_average(p.handle, _ptr(node), _ptr(u), _ptr(c_out), _stream(stream)))
 
 
 def fem_mesh_build_pattern(elem: torch.Tensor, N: int, stream=None) -> Pattern:

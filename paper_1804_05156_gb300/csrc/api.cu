@@ -324,6 +324,37 @@ int fem_apply_dirichlet(fem_pattern_t p, const uint8_t* is_bd, const double* gD,
   return fem::apply_dirichlet(&p->P, is_bd, gD, val, b, free_node, n_free, (cudaStream_t)stream);
 }
 
+int fem_boundary_terms(fem_pattern_t p, const double* node, const int8_t* bdflag, const double* g_side, double g_const,
+                       double alpha, double* val, double* b, fem_stream_t stream) {
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  if (!node || !bdflag) return set_error(FEM_ERR_ARG, "node and bdflag are required");
+  if (!aligned(node, 8) || !aligned(g_side, 8) || !aligned(val, 8) || !aligned(b, 8))
+    return set_error(FEM_ERR_ARG, "misaligned array");
+  if (!val && !b) return FEM_OK;
+  return fem::boundary_terms(&p->P, node, bdflag, g_side, g_const, alpha, val, b, (cudaStream_t)stream);
+}
+
+int fem_side_points(fem_pattern_t p, const double* node, double* pts, fem_stream_t stream) {
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  if (!node || !pts) return set_error(FEM_ERR_ARG, "node and pts are required");
+  if (!aligned(node, 8) || !aligned(pts, 8)) return set_error(FEM_ERR_ARG, "misaligned array");
+  return fem::side_points(&p->P, node, pts, (cudaStream_t)stream);
+}
+
+int fem_mean_shift(double* x, int64_t n, fem_stream_t stream) {
+  if (n < 0) return set_error(FEM_ERR_ARG, "n must be >= 0");
+  if (n > 0 && !x) return set_error(FEM_ERR_ARG, "null array");
+  if (!aligned(x, 8)) return set_error(FEM_ERR_ARG, "misaligned array");
+  return fem::mean_shift(x, n, (cudaStream_t)stream);
+}
+
+int fem_zero_average(fem_pattern_t p, const double* node, double* u, double* c_out, fem_stream_t stream) {
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  if (!node || !u) return set_error(FEM_ERR_ARG, "node and u are required");
+  if (!aligned(node, 8) || !aligned(u, 8) || !aligned(c_out, 8)) return set_error(FEM_ERR_ARG, "misaligned array");
+  return fem::zero_average(&p->P, node, u, c_out, (cudaStream_t)stream);
+}
+
 int fem_assemble_backward(fem_pattern_t p, const double* node, const double* k, int f_kind, const double* f_arg,
                           const double* w, const double* r, double* gnode, double* gk, fem_stream_t stream) {
   int rc = check_values_args(p, node, k, f_kind, f_arg, FEM_DETERMINISTIC);

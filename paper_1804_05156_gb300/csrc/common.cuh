@@ -161,6 +161,11 @@ int* device_error_word_if_ready();  // the current device's error word, or nullp
 int boundary_nodes(Pattern* P, const int8_t* bdflag, uint8_t* is_bd, cudaStream_t s);
 int apply_dirichlet(const Pattern* P, const uint8_t* is_bd, const double* gD, double* val, double* b,
                     int32_t* free_node, int64_t* n_free, cudaStream_t s);
+int boundary_terms(const Pattern* P, const double* node, const int8_t* bdflag, const double* g_side, double g_const,
+                   double alpha, double* val, double* b, cudaStream_t s);
+int side_points(const Pattern* P, const double* node, double* pts, cudaStream_t s);
+int mean_shift(double* x, int64_t n, cudaStream_t s);
+int zero_average(const Pattern* P, const double* node, double* u, double* c_out, cudaStream_t s);
 struct BatchPlan;
 int assemble_backward(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg,
                       const double* w, const double* r, double* gnode, double* gk, cudaStream_t s);

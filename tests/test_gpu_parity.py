@@ -472,3 +472,65 @@ def test_full_size_sampled_rows(cfg, variant):
     isbd = torch.empty(N, dtype=torch.uint8, device="cuda")
     fa.fem_boundary_nodes(p, None, isbd)
     assert np.array_equal(host(isbd), m["is_bd"])
+
+
+# ---- Neumann / Robin sides and the pure-Neumann fixes ------------------------------------------------
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_neumann_robin_terms_bit_exact(d):
+    """Side terms on top of an assembled system: the same val and b in, the same bits out as the oracle
+    (per-row order and operations are fixed on both sides)."""
+    m = meshgen.square_mesh(9, 0.2, 51, True) if d == 2 else meshgen.kuhn_mesh(3, 0.1, 51)
+    node, elem = m["node"], m["elem"]
+    N, NT = node.shape[0], elem.shape[0]
+    flags = meshgen.side_flags(m, {"x0": 2, "x1": 2, "y1": 3, "y0": 1, "z1": 3, "z0": 2})
+    k = meshgen.lognormal(51, 3, NT)
+    p = fa.Pattern(dev(elem), N)
+    val, b = fa.assemble(p, dev(node), dev(k), fa.FEM_F_SINPROD, None, fa.FEM_DETERMINISTIC)
+    v0, b0 = host(val), host(b)
+    rp, col = host(p.row_ptr).astype(np.int64), host(p.col_idx).astype(np.int64)
+    g = meshgen.normal(52, 9, NT * (d + 1)).reshape(NT, d + 1)
+    for g_side, g_const in ((g, 0.0), (None, 1.75)):
+        v, bb = val.clone(), b.clone()
+        fa.fem_boundary_terms(p, dev(node), dev(flags), None if g_side is None else dev(g_side), g_const, 0.7, v, bb)
+        fa.get_error()
+        vo, bo = oracle.boundary_terms(d, node, elem, flags, rp, col, v0, b0, g_side=g_side, g_const=g_const, alpha=0.7)
+        assert np.array_equal(host(v), vo) and np.array_equal(host(bb), bo)
+        assert not np.array_equal(vo, v0) and not np.array_equal(bo, b0)
+    # load only, matrix only
+    bb = b.clone()
+    fa.fem_boundary_terms(p, dev(node), dev(flags), None, 1.0, 0.7, None, bb)
+    _, bo = oracle.boundary_terms(d, node, elem, flags, rp, col, v0, b0, g_const=1.0, alpha=0.7)
+    assert np.array_equal(host(bb), bo)
+    pts = torch.empty((NT, d + 1, d), dtype=torch.float64, device="cuda")
+    fa.fem_side_points(p, dev(node), pts)
+    assert np.array_equal(host(pts), oracle.side_points(d, node, elem))
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_mean_shift_and_zero_average_match_oracle(d):
+    m = meshgen.square_mesh(40, 0.2, 53, True) if d == 2 else meshgen.kuhn_mesh(8, 0.1, 53)
+    node, elem = m["node"], m["elem"]
+    N = node.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    rng = np.random.default_rng(53)
+    x = rng.normal(size=N) + 2.0
+    xd = dev(x)
+    fa.fem_mean_shift(xd)
+    xo = oracle.mean_shift(x)
+    assert np.all(np.abs(host(xd) - xo) <= 1e-13 * np.abs(x).max())
+    assert abs(float(xd.sum())) <= 1e-11
+    u = rng.normal(size=N)
+    ud = dev(u)
+    c = torch.empty(1, dtype=torch.float64, device="cuda")
+    fa.fem_zero_average(p, dev(node), ud, c)
+    uo, co = oracle.zero_average(d, node, elem, u)
+    assert abs(float(c.item()) - co) <= 1e-13 * np.abs(u).max()
+    assert np.all(np.abs(host(ud) - uo) <= 1e-13 * np.abs(u).max())
+    # deterministic: the same bits again
+    ud2 = dev(u)
+    fa.fem_zero_average(p, dev(node), ud2)
+    assert torch.equal(ud, ud2)
+    # empty input is a no-op
+    fa.fem_mean_shift(torch.empty(0, dtype=torch.float64, device="cuda"))
+    fa.get_error()
