@@ -66,6 +66,8 @@ def _load():
         lib.ora_mean_shift.argtypes = [I64, P]
         lib.ora_zero_average.restype = I32
         lib.ora_zero_average.argtypes = [I32, I64, I64, P, P, P, P]
+        lib.ora_operator_triples.restype = I64
+        lib.ora_operator_triples.argtypes = [I32, I64, I64, P, P, I32, P, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -241,3 +243,18 @@ def zero_average(d, node, elem, u):
     c = np.zeros(1, np.float64)
     _check(_load().ora_zero_average(d, node.shape[0], elem.shape[0], _p(node), _p(elem), _p(out), _p(c)))
     return out, float(c[0])
+
+
+OP_MASS, OP_ANISO = 1, 2
+
+
+def operator(d, node, elem, op, coef=None):
+    """CSR (row_ptr, col, val, scale) of the mass matrix (op 1, coefficient per element) or of the
+    anisotropic operator (op 2, symmetric tensor per element, upper triangle)."""
+    node, elem, coef = _c(node, np.float64), _c(elem, np.int32), _c(coef, np.float64)
+    N, NT = node.shape[0], elem.shape[0]
+    cnt = max(NT * (d + 1) ** 2, 1)
+    I, J = np.zeros(cnt, np.int64), np.zeros(cnt, np.int64)
+    S, Ss = np.zeros(cnt, np.float64), np.zeros(cnt, np.float64)
+    q = _check(_load().ora_operator_triples(d, N, NT, _p(node), _p(elem), op, _p(coef), _p(I), _p(J), _p(S), _p(Ss)))
+    return sparse(N, N, I[:q], J[:q], S[:q], Ss[:q])

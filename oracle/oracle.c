@@ -36,6 +36,8 @@
  *   ora_side_points   the quadrature point (midpoint / centroid) of every side.
  *   ora_mean_shift    the pure-Neumann compatibility fix b - mean(b) (Sec. 3.3).
  *   ora_zero_average  u - c with c the area-weighted mean of u (Sec. 3.3), the zero-average constraint.
+ *   ora_operator_triples  triples of the mass matrix and of the anisotropic operator div(K grad u) on
+ *                     the same element loop (grad lambda from eq. (dlambda)).
  */
 #include <math.h>
 #include <stdint.h>
@@ -711,4 +713,77 @@ int ora_zero_average(int d, int64_t N, int64_t NT, const double* node, const int
   for (int64_t v = 0; v < N; ++v) u[v] = u[v] - c;
   if (c_out) *c_out = c;
   return ORA_OK;
+}
+
+/* ------------------------------------------------------------------------------------------------
+ * Other second-order operators on the same element loop (the same triples order as ora_triples):
+ *   op 1, mass:        m_ij^tau = c_t |tau| (1 + delta_ij) / ((d+1)(d+2)),  the exact integral of
+ *                      c lambda_i lambda_j over tau (c_t = coef[t], 1 when coef is NULL);
+ *   op 2, anisotropic: a_ij^tau = n_i^T K_t n_j / (d!^2 |tau|) = |tau| grad lambda_i^T K_t grad lambda_j
+ *                      (eq. (dlambda)), K_t symmetric, given by its upper triangle in coef[t]:
+ *                      2-D (xx, xy, yy), 3-D (xx, xy, xz, yy, yz, zz).
+ * Sscale: the magnitude bound of each entry's rounding: |m_ij| for the mass matrix; for the anisotropic
+ * matrix sum_ab |n|_ia |K_ab| |n|_jb / (d!^2 |tau|) with the normal magnitudes of normal_magnitudes (for
+ * the diagonal summed over the other vertices q != i, which bounds minus the off-diagonal row sum too).
+ * ------------------------------------------------------------------------------------------------ */
+static void sym_tensor(int d, const double* c, double K[3][3]) {
+  if (d == 2) {
+    K[0][0] = c[0]; K[0][1] = c[1]; K[1][0] = c[1]; K[1][1] = c[2];
+  } else {
+    K[0][0] = c[0]; K[0][1] = c[1]; K[0][2] = c[2];
+    K[1][0] = c[1]; K[1][1] = c[3]; K[1][2] = c[4];
+    K[2][0] = c[2]; K[2][1] = c[4]; K[2][2] = c[5];
+  }
+}
+
+static double quad_form(int d, const double* u, double K[3][3], const double* v) {
+  double s = 0.0;
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) s = s + u[a] * (K[a][b] * v[b]);
+  return s;
+}
+
+int64_t ora_operator_triples(int d, int64_t N, int64_t NT, const double* node, const int32_t* elem, int op,
+                             const double* coef, int64_t* I, int64_t* J, double* S, double* Sscale) {
+  if ((d != 2 && d != 3) || (op != 1 && op != 2) || (op == 2 && !coef)) return ORA_ERR_ARG;
+  const int d1 = d + 1, nk = d * (d + 1) / 2;
+  const double dd = (d == 2) ? 4.0 : 36.0;
+  int64_t q = 0;
+  for (int64_t t = 0; t < NT; ++t) {
+    const int32_t* e = elem + d1 * t;
+    for (int i = 0; i < d1; ++i)
+      if (e[i] < 0 || e[i] >= N) return ORA_ERR_INDEX;
+    double n[4][3], nm[4][3], K[3][3], Ka[3][3];
+    const double meas = element_normals(d, node, e, n);
+    if (!(meas > 0.0)) return ORA_ERR_DEGENERATE;
+    if (op == 2) {
+      sym_tensor(d, coef + nk * t, K);
+      for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) Ka[a][b] = fabs(K[a][b]);
+      normal_magnitudes(d, node, e, nm);
+    }
+    const double c = (op == 1 && coef) ? coef[t] : 1.0;
+    for (int i = 0; i < d1; ++i)
+      for (int j = 0; j < d1; ++j) {
+        double v, sc;
+        if (op == 1) {
+          v = c * (meas * ((i == j ? 2.0 : 1.0) / (double)(d1 * (d + 2))));
+          sc = fabs(v);
+        } else {
+          v = quad_form(d, n[i], K, n[j]) / (dd * meas);
+          sc = 0.0;
+          for (int qq = 0; qq < d1; ++qq) {
+            if (i == j ? qq == i : qq != j) continue;
+            sc = sc + quad_form(d, nm[i], Ka, nm[qq]);
+          }
+          sc = sc / (dd * meas);
+        }
+        I[q] = e[i];
+        J[q] = e[j];
+        S[q] = v;
+        if (Sscale) Sscale[q] = sc;
+        q += 1;
+      }
+  }
+  return q;
 }

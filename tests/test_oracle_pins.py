@@ -582,3 +582,81 @@ def test_mean_shift_and_zero_average():
     # a constant function's average is the constant
     _, c1 = oracle.zero_average(2, m["node"], m["elem"], np.full(b.size, 4.25))
     assert abs(c1 - 4.25) <= 1e-15
+
+
+# --- other second-order operators on the same element loop: mass, anisotropic div(K grad u) ------------
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_mass_matrix_integrates_products_exactly(d):
+    """M_ij = int lambda_i lambda_j: 1^T M 1 = |Omega|, x^T M x = int x^2 = 1/3 on the unit square/cube
+    (P1 products are exact), symmetric positive definite; the local matrix equals the degree-2 rule's
+    (the 2-D edge midpoints, the 3-D four points) applied to lambda_i lambda_j."""
+    m = _geometry(d, 4, 0.2, 61)
+    node, elem = m["node"], m["elem"]
+    N = node.shape[0]
+    c = meshgen.lognormal(61, 3, elem.shape[0])
+    rp, col, val, _ = oracle.operator(d, node, elem, oracle.OP_MASS)
+    M = dense_from_csr(rp, col, val, N)
+    assert np.array_equal(M, M.T)
+    one = np.ones(N)
+    assert abs(one @ M @ one - 1.0) <= 1e-14
+    x = node[:, 0]
+    assert abs(x @ M @ x - 1.0 / 3.0) <= 1e-14
+    assert np.linalg.eigvalsh(M).min() > 0
+    # coefficient: c-weighted, element by element
+    rpc, colc, valc, _ = oracle.operator(d, node, elem, oracle.OP_MASS, c)
+    meas = np.abs(oracle.measure(d, node, elem))
+    assert abs(valc.sum() - (c * meas).sum()) <= 1e-14 * (c * meas).sum()
+    # the local matrix by the degree-2 rule on one element
+    e = elem[3]
+    p = node[e]
+    if d == 2:
+        lam = np.array([[0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]])
+        w = np.full(3, 1.0 / 3.0)
+    else:
+        a, b = (5 + 3 * math.sqrt(5)) / 20, (5 - math.sqrt(5)) / 20
+        lam = np.full((4, 4), b) + np.eye(4) * (a - b)
+        w = np.full(4, 0.25)
+    loc = meas[3] * np.einsum("q,qi,qj->ij", w, lam, lam)
+    one_el, _ = np.zeros(elem.shape[0]), None
+    one_el[3] = 1.0
+    rp1, col1, val1, _ = oracle.operator(d, node, elem, oracle.OP_MASS, one_el)
+    M1 = dense_from_csr(rp1, col1, val1, N)
+    assert np.allclose(M1[np.ix_(e, e)], loc, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_anisotropic_operator(d):
+    """div(K grad u): K = I gives the stiffness matrix; zero row sums; for linear u = g.x the energy
+    u^T A u = g^T K g |Omega| exactly (constant K); rotating the mesh by Q and K by Q K Q^T changes nothing."""
+    m = _geometry(d, 4, 0.2, 62)
+    node, elem = m["node"], m["elem"]
+    N, NT = node.shape[0], elem.shape[0]
+    nk = d * (d + 1) // 2
+    eye = np.array([1.0, 0.0, 1.0]) if d == 2 else np.array([1.0, 0.0, 0.0, 1.0, 0.0, 1.0])
+    rpI, colI, vI, _ = oracle.operator(d, node, elem, oracle.OP_ANISO, np.tile(eye, (NT, 1)))
+    rpS, colS, vS, _ = oracle.assemble(d, node, elem)
+    assert np.array_equal(colI, colS) and np.array_equal(vI, vS)
+    if d == 2:
+        Kf = np.array([2.0, 0.3, 0.7])
+        Km = np.array([[2.0, 0.3], [0.3, 0.7]])
+    else:
+        Kf = np.array([2.0, 0.3, -0.2, 0.7, 0.1, 1.3])
+        Km = np.array([[2.0, 0.3, -0.2], [0.3, 0.7, 0.1], [-0.2, 0.1, 1.3]])
+    rp, col, v, sc = oracle.operator(d, node, elem, oracle.OP_ANISO, np.tile(Kf, (NT, 1)))
+    A = dense_from_csr(rp, col, v, N)
+    S = dense_from_csr(rp, col, sc, N)
+    assert np.all(np.abs(A - A.T) <= 1e-15 * (S + S.T))  # symmetric up to the rounding of n_i^T K n_j
+    assert np.all(np.abs(A.sum(axis=1)) <= 1e-13 * np.abs(A).sum(axis=1))
+    g = np.array([0.4, -1.1, 0.6])[:d]
+    u = node @ g
+    assert abs(u @ A @ u - g @ Km @ g) <= 1e-13
+    th = 0.37
+    if d == 2:
+        Q = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    else:
+        Q = np.array([[math.cos(th), -math.sin(th), 0.0], [math.sin(th), math.cos(th), 0.0], [0.0, 0.0, 1.0]])
+    KQ = Q @ Km @ Q.T
+    iu = np.triu_indices(d)
+    rpq, colq, vq, _ = oracle.operator(d, node @ Q.T, elem, oracle.OP_ANISO, np.tile(KQ[iu], (NT, 1)))
+    assert np.all(np.abs(vq - v) <= 1e-12 * sc)
