@@ -465,6 +465,17 @@ def run_ours(args):
         ms_ms = _time_steps(lambda: fa.fem_mean_shift(b), steps_b, flush, s)
         ms_za = _time_steps(lambda: fa.fem_zero_average(p, node_d, b), steps_b, flush, s)
         out["neumann_robin"] = {"boundary_terms_ms": ms_nr, "mean_shift_ms": ms_ms, "zero_average_ms": ms_za}
+        # the other operators on the same pattern: mass matrix (coefficient k) and -div(K grad u)
+        Kt = np.array([1.5, 0.2, 0.8]) if d == 2 else np.array([1.5, 0.2, -0.1, 0.8, 0.1, 1.2])
+        K_d = torch.as_tensor(np.tile(Kt, (NT, 1))).cuda()
+        fa.fem_assemble_operator(p, node_d, fa.FEM_OP_MASS, k_d, val)
+        fa.fem_assemble_operator(p, node_d, fa.FEM_OP_ANISO, K_d, val)
+        ms_mass = _time_steps(lambda: fa.fem_assemble_operator(p, node_d, fa.FEM_OP_MASS, k_d, val), steps_b, flush, s)
+        ms_an = _time_steps(lambda: fa.fem_assemble_operator(p, node_d, fa.FEM_OP_ANISO, K_d, val), steps_b, flush, s)
+        fa.get_error()
+        out["operators"] = {"mass_ms": ms_mass, "mass_Melem_s": NT / (ms_mass * 1e-3) / 1e6,
+                            "aniso_ms": ms_an, "aniso_Melem_s": NT / (ms_an * 1e-3) / 1e6}
+        del K_d
     if not args.no_extras and ws == 1:
         out["extras"] = extras(fa, args, flush, value)
     if rank == 0 and not args.no_cpu_baseline:

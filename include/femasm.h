@@ -163,6 +163,22 @@ int fem_boundary_nodes(fem_pattern_t p, const int8_t* bdflag, uint8_t* is_bd, fe
 int fem_apply_dirichlet(fem_pattern_t p, const uint8_t* is_bd, const double* gD, double* val, double* b,
                         int32_t* free_node, int64_t* n_free, fem_stream_t stream);
 
+/* ---- other second-order operators on the same element loop (values only) ------------------------
+ * FEM_OP_MASS:  m_ij^tau = c_t |tau| (1 + delta_ij) / ((d+1)(d+2)), the exact integral of c lambda_i
+ *               lambda_j; coef = c [NT] (device, nullable: c = 1).
+ * FEM_OP_ANISO: a_ij^tau = |tau| grad lambda_i^T K_t grad lambda_j = n_i^T K_t n_j / (d!^2 |tau|) (eq.
+ *               (dlambda)), the operator -div(K grad u) with a symmetric tensor per element; coef [NT][m]
+ *               (device) holds its upper triangle, 2-D m = 3 (xx, xy, yy), 3-D m = 6 (xx, xy, xz, yy, yz, zz).
+ * FEM_OP_STIFFNESS: the stiffness matrix with coefficient coef [NT] (= fem_assemble_stiffness).
+ * The same pattern, float-float arithmetic and fixed summation order as fem_assemble; mass and
+ * anisotropic operators always take the tile path (its plan is built on the first such call if the
+ * pattern has none: synchronises). Same element checks (FEM_ERR_DEGENERATE through the error word). */
+#define FEM_OP_STIFFNESS 0
+#define FEM_OP_MASS 1
+#define FEM_OP_ANISO 2
+int fem_assemble_operator(fem_pattern_t p, const double* node, int op, const double* coef, double* val,
+                          fem_stream_t stream);
+
 /* ---- Neumann and Robin sides, pure-Neumann fixes ("Boundary conditions", Sec. 3.3) --------------
  * Side j of element t is the side opposite local vertex j; bdflag [NT][d+1] (int8, device) = 2 marks it
  * Neumann, 3 Robin (du/dn + alpha u = g). Its vertices are the element's other d vertices; |s| is the

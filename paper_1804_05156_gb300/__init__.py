@@ -22,6 +22,7 @@ FEM_ERR_ARG, FEM_ERR_INDEX, FEM_ERR_DEGENERATE, FEM_ERR_CUDA, FEM_ERR_OOM, FEM_E
 FEM_DETERMINISTIC, FEM_ATOMIC = 0, 1
 FEM_F_CONST, FEM_F_SINPROD, FEM_F_QPVALUES = 0, 1, 2
 FEM_PATH_TWO_PASS, FEM_PATH_BLOCKED, FEM_PATH_TILES, FEM_PATH_TILES_FUSED = 0, 1, 2, 3
+FEM_OP_STIFFNESS, FEM_OP_MASS, FEM_OP_ANISO = 0, 1, 2
 
 _lib = None
 
@@ -62,6 +63,7 @@ def lib():
             "fem_apply_dirichlet": (I32, [P, P, P, P, P, P, P, P]),
             "fem_assemble_backward": (I32, [P, P, P, I32, P, P, P, P, P, P]),
             "fem_boundary_terms": (I32, [P, P, P, P, C.c_double, C.c_double, P, P, P]),
+            "fem_assemble_operator": (I32, [P, P, I32, P, P, P]),
             "fem_side_points": (I32, [P, P, P, P]),
             "fem_mean_shift": (I32, [P, C.c_int64, P]),
             "fem_zero_average": (I32, [P, P, P, P, P]),
@@ -206,6 +208,15 @@ def fem_pattern_value_path(p: Pattern) -> dict:
 
 def fem_pattern_force_path(p: Pattern, path: int, tile_elems: int = 256, stream=None):
     _check(lib().fem_pattern_force_path(p.handle, path, tile_elems, _stream(stream)))
+
+
+def fem_assemble_operator(p: Pattern, node, op: int, coef=None, val=None, stream=None):
+    """Values [nnz] of the mass matrix (FEM_OP_MASS, coef c [NT] or None), of -div(K grad) (FEM_OP_ANISO,
+    coef [NT, d(d+1)/2] upper triangles) or of the stiffness matrix (FEM_OP_STIFFNESS, coef k [NT])."""
+    if val is None:
+        val = torch.empty(p.nnz, dtype=torch.float64, device=node.device)
+    _check(lib().fem_assemble_operator(p.handle, _ptr(node), op, _ptr(coef), _ptr(val), _stream(stream)))
+    return val
 
 
 def fem_boundary_terms(p: Pattern, node, bdflag, g_side=None, g_const=0.0, alpha=0.0, val=None, b=None, stream=None):

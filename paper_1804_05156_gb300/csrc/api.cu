@@ -324,6 +324,33 @@ int fem_apply_dirichlet(fem_pattern_t p, const uint8_t* is_bd, const double* gD,
   return fem::apply_dirichlet(&p->P, is_bd, gD, val, b, free_node, n_free, (cudaStream_t)stream);
 }
 
+int fem_assemble_operator(fem_pattern_t p, const double* node, int op, const double* coef, double* val,
+                          fem_stream_t stream) {
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  if (!node || !val) return set_error(FEM_ERR_ARG, "node and val are required");
+  if (!aligned(node, 8) || !aligned(coef, 8) || !aligned(val, 8)) return set_error(FEM_ERR_ARG, "misaligned array");
+  if (op == FEM_OP_STIFFNESS)
+    return fem_assemble(p, node, coef, FEM_F_CONST, nullptr, val, nullptr, FEM_DETERMINISTIC, stream);
+  if (op != FEM_OP_MASS && op != FEM_OP_ANISO) return set_error(FEM_ERR_ARG, "unknown operator %d", op);
+  if (op == FEM_OP_ANISO && !coef) return set_error(FEM_ERR_ARG, "the anisotropic operator needs its tensors");
+  Pattern& P = p->P;
+  if (P.NT == 0 || P.nnz == 0) {
+    if (P.nnz > 0) FEM_CUDA(cudaMemsetAsync(val, 0, sizeof(double) * P.nnz, (cudaStream_t)stream));
+    return FEM_OK;
+  }
+  if (!P.tile.ok) {
+    fem::TilePlan T;
+    int rc = fem::build_tile_plan(&P, P.blk.order, 128, &T, (cudaStream_t)stream);
+    if (rc) return rc;
+    if (!T.ok) {
+      fem::free_tile_plan(T);
+      return set_error(FEM_ERR_STATE, "this mesh has no tile plan (a row longer than 256 entries)");
+    }
+    P.tile = T;
+  }
+  return fem::assemble_tiles(&P, node, nullptr, FEM_F_CONST, nullptr, val, nullptr, (cudaStream_t)stream, op, coef);
+}
+
 int fem_boundary_terms(fem_pattern_t p, const double* node, const int8_t* bdflag, const double* g_side, double g_const,
                        double alpha, double* val, double* b, fem_stream_t stream) {
   if (!p) return set_error(FEM_ERR_ARG, "null pattern");

@@ -139,8 +139,9 @@ int blocked_smem_budget(int ctas_per_sm);
 int blocked_smem_need(const BlockPlan& B, int d, bool sinprod);
 int assemble_blocked(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg,
                      double* val, double* b, cudaStream_t s);
+// op: 0 stiffness (+ load vector), 1 mass, 2 anisotropic (values only; opk: their coefficients)
 int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg, double* val,
-                   double* b, cudaStream_t s);
+                   double* b, cudaStream_t s, int op = 0, const double* opk = nullptr);
 int tile_fused_smem(const TilePlan& T, int d);  // 0: the fused launch does not fit
 
 // scratch doubles per element: stiffness unique entries + rhs entries (+ gradient entries)

@@ -196,4 +196,105 @@ __device__ __forceinline__ bool element_df3(const VtxDF<3>* const (&V)[4], df2 k
   return ok;
 }
 
+// ---- other second-order operators on the same element (values only) --------------------------------
+// Mass: m_ij = c |tau| (1 + delta_ij) / ((d+1)(d+2)), the exact integral of c lambda_i lambda_j.
+// Anisotropic div(K grad u): a_ij = n_i^T K n_j / (d!^2 |tau|) = |tau| grad lambda_i^T K grad lambda_j
+// (eq. (dlambda)), K symmetric given by its upper triangle; the diagonal is left to the caller (the
+// row sums vanish, as for the stiffness matrix).
+constexpr int kOpStiffness = 0, kOpMass = 1, kOpAniso = 2;
+
+template <int D>
+__device__ __forceinline__ void sym_tensor_df(const double* __restrict__ c, df2 (&K)[D][D]) {
+  if constexpr (D == 2) {
+    K[0][0] = df_from_double(__ldg(c));
+    K[0][1] = K[1][0] = df_from_double(__ldg(c + 1));
+    K[1][1] = df_from_double(__ldg(c + 2));
+  } else {
+    K[0][0] = df_from_double(__ldg(c));
+    K[0][1] = K[1][0] = df_from_double(__ldg(c + 1));
+    K[0][2] = K[2][0] = df_from_double(__ldg(c + 2));
+    K[1][1] = df_from_double(__ldg(c + 3));
+    K[1][2] = K[2][1] = df_from_double(__ldg(c + 4));
+    K[2][2] = df_from_double(__ldg(c + 5));
+  }
+}
+
+// n^T K m
+template <int D>
+__device__ __forceinline__ df2 df_quad(const df2 (&n)[D], const df2 (&K)[D][D], const df2 (&m)[D]) {
+  df2 Km[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) Km[a] = df_dot<D>(K[a], m);
+  return df_dot<D>(n, Km);
+}
+
+// scaled normals n_i and d! |tau| (2-D: |2 area|, the paper's abs(); 3-D: 6 x signed volume)
+template <int D>
+__device__ __forceinline__ df2 element_normals_df(const VtxDF<D>* const (&V)[D + 1], df2 (&n)[D + 1][D]) {
+  if constexpr (D == 2) {
+    df2 e[3][2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      e[0][m] = f3_diff(V[2]->x[m], V[1]->x[m]);
+      e[1][m] = f3_diff(V[0]->x[m], V[2]->x[m]);
+      e[2][m] = f3_diff(V[1]->x[m], V[0]->x[m]);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      n[i][0] = df_neg(e[i][1]);
+      n[i][1] = e[i][0];
+    }
+    const df2 a2 = df_dot2m(e[1][0], e[2][1], e[1][1], e[2][0]);
+    return a2.h < 0.0f ? df_neg(a2) : a2;
+  } else {
+    df2 e[3][3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) e[q][m] = f3_diff(V[q + 1]->x[m], V[0]->x[m]);
+    df_cross(e[1], e[2], n[1]);
+    df_cross(e[2], e[0], n[2]);
+    df_cross(e[0], e[1], n[3]);
+    df2 u[3], v[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      u[m] = f3_diff(V[3]->x[m], V[1]->x[m]);
+      v[m] = f3_diff(V[2]->x[m], V[1]->x[m]);
+    }
+    df_cross(u, v, n[0]);
+    return df_dot<3>(n[3], e[2]);
+  }
+}
+
+// Local matrix of operator op (kOpMass or kOpAniso) into L.a (pidx order; mass: every entry; aniso: the
+// off-diagonal entries). coef: mass c_t (nullable: 1), aniso the tensor's upper triangle of element t.
+template <int D>
+__device__ __forceinline__ bool element_df_operator(const VtxDF<D>* const (&V)[D + 1], int op,
+                                                    const double* __restrict__ coef, LocalDF<D>& L) {
+  constexpr int D1 = D + 1;
+  df2 n[D1][D];
+  const df2 dm = element_normals_df<D>(V, n);  // d! |tau|
+  const bool ok = dm.h > 0.0f && dm.h < INFINITY;
+  if (op == kOpMass) {
+    // c |tau| / ((d+1)(d+2)) = c d! |tau| / (2 * 12) in 2-D, / (6 * 20) in 3-D
+    const df2 inv = (D == 2) ? df2{0.041666667908430099f, -1.2417634e-09f} : df2{0.0083333337679505348f, -4.3461720e-10f};
+    const df2 c = coef ? df_from_double(__ldg(coef)) : df2{1.0f, 0.0f};
+    const df2 off = df_mul(c, df_mul(dm, inv));
+    const df2 dia = df_scale(off, 2.0f);
+#pragma unroll
+    for (int i = 0; i < D1; ++i) L.a[i] = dia;
+#pragma unroll
+    for (int c2 = D1; c2 < D1 * (D1 + 1) / 2; ++c2) L.a[c2] = off;
+  } else {
+    df2 K[D][D];
+    sym_tensor_df<D>(coef, K);
+    const df2 s = df_recip(D == 2 ? df_scale(dm, 2.0f) : df_mul_f(dm, 6.0f));  // 1 / (d!^2 |tau|)
+#pragma unroll
+    for (int i = 0; i < D1; ++i)
+#pragma unroll
+      for (int j = i + 1; j < D1; ++j) L.a[pidx<D>(i, j)] = df_mul(s, df_quad<D>(n[i], K, n[j]));
+  }
+  return ok;
+}
+
 }  // namespace fem

@@ -43,6 +43,8 @@ struct TileArgs {
   const int32_t* ipos;
   float4* pk;
   int xs_bytes;
+  int op;               // kOpStiffness (with the load vector), kOpMass or kOpAniso (values only)
+  const double* opk;    // operator coefficients: mass c [NT] (nullable), aniso tensor [NT][d(d+1)/2]
 };
 
 struct RowArgs {
@@ -53,6 +55,7 @@ struct RowArgs {
   const void* pw;
   const uint8_t* rdp;
   const float4* pk;
+  bool diag_in_packet;  // the packet's last pair is the diagonal entry (mass matrix), not a load term
 };
 
 // Phase 1 for one tile (all TE threads of the CTA; one __syncthreads inside).
@@ -102,7 +105,17 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
 #pragma unroll
   for (int i = 0; i < D1; ++i) L.bt[i] = df2{0.0f, 0.0f};
   bool ok;
-  if constexpr (D == 2) {
+  if (a.op != kOpStiffness) {
+    const VtxDF<D>* V[D1];
+#pragma unroll
+    for (int i = 0; i < D1; ++i) V[i] = &xs[lv[i]];
+    const double* c = (a.op == kOpMass) ? (a.opk ? a.opk + t : nullptr) : a.opk + (size_t)t * (D * D1 / 2);
+    ok = element_df_operator<D>(reinterpret_cast<const VtxDF<D>* const(&)[D1]>(V), a.op, c, L);
+    if (a.op == kOpMass) {
+#pragma unroll
+      for (int i = 0; i < D1; ++i) L.bt[i] = L.a[i];  // the diagonal travels in the load slot
+    }
+  } else if constexpr (D == 2) {
     const VtxDF<2>* const V[3] = {&xs[lv[0]], &xs[lv[1]], &xs[lv[2]]};
     const SC* const S[3] = {&scs[lv[0] * 2], &scs[lv[1] * 2], &scs[lv[2] * 2]};
     ok = element_df2(V, S, kt, want_a, want_b, f_kind, fconst, f_arg, t, L, false);  // diagonals: in the gather
@@ -140,18 +153,19 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
 // warp's shared-memory copy of its rows. w holds the in-row positions of the other columns, 8 bits each.
 template <int D>
 __device__ __forceinline__ void add_packet(const float4& p0, const float4& p1, uint32_t w, int o, df2* acc, df2& dacc,
-                                           df2& bacc, bool want_a, bool want_b) {
+                                           df2& bacc, bool want_a, bool want_b, bool diag_in_packet = false) {
   if (want_a) {
     const int c0 = o + (int)(w & 0xffu), c1 = o + (int)((w >> 8) & 0xffu);
     if constexpr (D == 2) {
       const df2 o1 = {p0.x, p0.y}, o2 = {p0.z, p0.w};
-      dacc = df_acc(dacc, df_neg(df_add(o1, o2)));  // a_ii = -(a_ij + a_ik), as the element routine forms it
+      // a_ii = -(a_ij + a_ik), as the element routine forms it (or carried in the packet)
+      dacc = df_acc(dacc, diag_in_packet ? df2{p1.x, p1.y} : df_neg(df_add(o1, o2)));
       acc[c0] = df_acc(acc[c0], o1);
       acc[c1] = df_acc(acc[c1], o2);
     } else {
       const df2 o1 = {p0.x, p0.y}, o2 = {p0.z, p0.w}, o3 = {p1.x, p1.y};
       const int c2 = o + (int)((w >> 16) & 0xffu);
-      dacc = df_acc(dacc, df_sub(df_sub(df_sub(df2{0.0f, 0.0f}, o1), o2), o3));
+      dacc = df_acc(dacc, diag_in_packet ? df2{p1.z, p1.w} : df_sub(df_sub(df_sub(df2{0.0f, 0.0f}, o1), o2), o3));
       acc[c0] = df_acc(acc[c0], o1);
       acc[c1] = df_acc(acc[c1], o2);
       acc[c2] = df_acc(acc[c2], o3);
@@ -232,12 +246,12 @@ __device__ __forceinline__ void rows_of_warp(const RowArgs& g, int64_t R0, df2* 
         w[u] = (uint32_t)__ldg(pw + q + u);
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) add_packet<D>(x0[u], x1[u], w[u], o, acc, dacc, bacc, want_a, want_b);
+      for (int u = 0; u < U; ++u) add_packet<D>(x0[u], x1[u], w[u], o, acc, dacc, bacc, want_a, want_b, g.diag_in_packet);
     }
     for (; q < q1; ++q) {
       float4 x0, x1;
       load_packet<D, FRESH>(g.pk, q, x0, x1);
-      add_packet<D>(x0, x1, (uint32_t)__ldg(pw + q), o, acc, dacc, bacc, want_a, want_b);
+      add_packet<D>(x0, x1, (uint32_t)__ldg(pw + q), o, acc, dacc, bacc, want_a, want_b, g.diag_in_packet);
     }
     if (want_a && rl > 0) acc[o + __ldg(g.rdp + R)] = dacc;
     if (want_b) bvec[R] = df_to_double(bacc);
@@ -350,7 +364,7 @@ int tile_fused_smem(const TilePlan& T, int d) {
 }
 
 int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg, double* val,
-                   double* b, cudaStream_t s) {
+                   double* b, cudaStream_t s, int op, const double* opk) {
   int* err = device_error_word();
   if (!err) return set_error(FEM_ERR_OOM, "cannot allocate the device error word");
   const float4* tab = sincos_table_device();
@@ -372,6 +386,12 @@ int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_
   a.ipos = T.ipos;
   a.pk = T.pk;
   a.xs_bytes = ((T.max_v * vtx_bytes(D)) + 15) / 16 * 16;
+  a.op = op;
+  a.opk = opk;
+  if (op != kOpStiffness) {
+    b = nullptr;  // operators give values only
+    f_kind = FEM_F_CONST;
+  }
   RowArgs g;
   g.N = P->N;
   g.max_row = T.max_row > 0 ? T.max_row : 1;
@@ -380,6 +400,7 @@ int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_
   g.pw = T.pw;
   g.rdp = T.rdp;
   g.pk = T.pk;
+  g.diag_in_packet = op == kOpMass;
   const int want_a = val != nullptr, want_b = b != nullptr;
   if (T.fused) {
     // one cooperative launch: as many CTAs as are resident at once, counters zeroed in-stream

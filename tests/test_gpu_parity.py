@@ -534,3 +534,41 @@ def test_mean_shift_and_zero_average_match_oracle(d):
     # empty input is a no-op
     fa.fem_mean_shift(torch.empty(0, dtype=torch.float64, device="cuda"))
     fa.get_error()
+
+
+# ---- other operators: mass matrix and -div(K grad u) --------------------------------------------------
+
+@pytest.mark.parametrize("case", ["sq37p", "kuhn5", "delaunay2", "delaunay3"])
+def test_mass_and_anisotropic_operators_match_oracle(case):
+    d, node, elem, k, _ = mesh_case(case)
+    N, NT = node.shape[0], elem.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    rng = np.random.default_rng(71)
+    c = meshgen.lognormal(71, 3, NT)
+    nk = d * (d + 1) // 2
+    # SPD tensors: diagonal in [0.5, 2], off-diagonal up to 0.3
+    K = np.zeros((NT, nk))
+    diag_pos = [0, 2] if d == 2 else [0, 3, 5]
+    off_pos = [1] if d == 2 else [1, 2, 4]
+    K[:, diag_pos] = rng.uniform(0.5, 2.0, size=(NT, d))
+    K[:, off_pos] = rng.uniform(-0.3, 0.3, size=(NT, len(off_pos)))
+    for op, coef in ((fa.FEM_OP_MASS, None), (fa.FEM_OP_MASS, c), (fa.FEM_OP_ANISO, K)):
+        v = fa.fem_assemble_operator(p, dev(node), op, None if coef is None else dev(coef))
+        fa.get_error()
+        rp, col, vo, so = oracle.operator(d, node, elem, op, coef)
+        assert np.array_equal(host(p.col_idx), col)
+        assert_close_scaled(host(v), vo, so, what="operator %d" % op)
+        # deterministic and the same bits in the fused form
+        v2 = fa.fem_assemble_operator(p, dev(node), op, None if coef is None else dev(coef))
+        assert torch.equal(v, v2)
+        fa.fem_pattern_force_path(p, fa.FEM_PATH_TILES_FUSED, 128)
+        v3 = fa.fem_assemble_operator(p, dev(node), op, None if coef is None else dev(coef))
+        fa.fem_pattern_force_path(p, fa.FEM_PATH_TILES, 128)
+        assert torch.equal(v, v3)
+    # the stiffness operator is fem_assemble_stiffness
+    vs = fa.fem_assemble_operator(p, dev(node), fa.FEM_OP_STIFFNESS, dev(k))
+    vref = torch.empty_like(vs)
+    fa.fem_assemble_stiffness(p, dev(node), dev(k), vref, fa.FEM_DETERMINISTIC)
+    assert torch.equal(vs, vref)
+    with pytest.raises(fa.FemError):
+        fa.fem_assemble_operator(p, dev(node), fa.FEM_OP_ANISO, None)
