@@ -66,6 +66,8 @@ def _load():
         lib.ora_mean_shift.argtypes = [I64, P]
         lib.ora_zero_average.restype = I32
         lib.ora_zero_average.argtypes = [I32, I64, I64, P, P, P, P]
+        lib.ora_rhs_rule.restype = I32
+        lib.ora_rhs_rule.argtypes = [I32, I64, I64, P, P, I32, P, P, I32, P, P]
         lib.ora_operator_triples.restype = I64
         lib.ora_operator_triples.argtypes = [I32, I64, I64, P, P, I32, P, P, P, P, P]
         _lib = lib
@@ -258,3 +260,54 @@ def operator(d, node, elem, op, coef=None):
     S, Ss = np.zeros(cnt, np.float64), np.zeros(cnt, np.float64)
     q = _check(_load().ora_operator_triples(d, N, NT, _p(node), _p(elem), op, _p(coef), _p(I), _p(J), _p(S), _p(Ss)))
     return sparse(N, N, I[:q], J[:q], S[:q], Ss[:q])
+
+
+def _gauss_jacobi01(n, a):
+    """Gauss rule on [0, 1] for the weight (1 - v)^a, by the eigenvalues of the Jacobi matrix of the
+    orthogonal polynomials (Golub-Welsch); weights sum to 1 / (a + 1)."""
+    # monic recurrence of the Jacobi polynomials P_k^{(a, 0)} on [-1, 1]
+    k = np.arange(n, dtype=np.float64)
+    al = np.where(2 * k + a == 0, 0.0, -(a * a) / np.maximum((2 * k + a) * (2 * k + a + 2), 1e-300))
+    if n > 0 and a == 0:
+        al[:] = 0.0
+    kk = np.arange(1, n, dtype=np.float64)
+    be = 4 * kk * (kk + a) * kk * (kk + a) / ((2 * kk + a) ** 2 * (2 * kk + a + 1) * (2 * kk + a - 1))
+    J = np.diag(al) + np.diag(np.sqrt(be), 1) + np.diag(np.sqrt(be), -1)
+    t, vec = np.linalg.eigh(J)
+    mu0 = 2.0 ** (a + 1) / (a + 1)
+    w = mu0 * vec[0, :] ** 2
+    return 0.5 * (1.0 + t), w * 0.5 ** (a + 1)
+
+
+def quad_rule(d, n):
+    """Conical-product Gauss rule on the reference simplex: (bary [n^d, d+1], weights [n^d]) summing to 1,
+    exact for total degree 2n - 1."""
+    xu, wu = _gauss_jacobi01(n, 0)
+    xv, wv = _gauss_jacobi01(n, 1)
+    pts, ws = [], []
+    if d == 2:
+        for a in range(n):
+            for b in range(n):
+                x, y = xu[a] * (1 - xv[b]), xv[b]
+                pts.append([1 - x - y, x, y])
+                ws.append(2 * wu[a] * wv[b])
+    else:
+        xw, ww = _gauss_jacobi01(n, 2)
+        for a in range(n):
+            for b in range(n):
+                for c in range(n):
+                    x, y, z = xu[a] * (1 - xv[b]) * (1 - xw[c]), xv[b] * (1 - xw[c]), xw[c]
+                    pts.append([1 - x - y - z, x, y, z])
+                    ws.append(6 * wu[a] * wv[b] * ww[c])
+    return np.array(pts), np.array(ws)
+
+
+def rhs_rule(d, node, elem, bary, w, fkind=F_CONST, farg=None):
+    """Load vector with a given rule: b_i = sum_tau |tau| sum_q w_q f(p_q) lambda_i(p_q)."""
+    node, elem = _c(node, np.float64), _c(elem, np.int32)
+    bary, w, farg = _c(bary, np.float64), _c(w, np.float64), _c(farg, np.float64)
+    N = node.shape[0]
+    b = np.zeros(N, np.float64)
+    _check(_load().ora_rhs_rule(d, N, elem.shape[0], _p(node), _p(elem), w.size, _p(bary), _p(w), fkind, _p(farg),
+                                _p(b)))
+    return b

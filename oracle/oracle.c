@@ -787,3 +787,47 @@ int64_t ora_operator_triples(int d, int64_t N, int64_t NT, const double* node, c
   }
   return q;
 }
+
+/* ------------------------------------------------------------------------------------------------
+ * Load vector with a given rule ("Numerical Quadrature"): b_i += |tau| sum_q w_q f(p_q) lambda_i(p_q),
+ * p_q = sum_i bary[q][i] x_i, the rule's weights summing to 1. f kinds as ora_rhs (2: values
+ * farg[t * nq + q]). The rule itself is built by the Python layer of the oracle.
+ * ------------------------------------------------------------------------------------------------ */
+int ora_rhs_rule(int d, int64_t N, int64_t NT, const double* node, const int32_t* elem, int nq, const double* bary,
+                 const double* w, int fkind, const double* farg, double* b) {
+  if (d != 2 && d != 3) return ORA_ERR_ARG;
+  if (fkind == 2 && !farg) return ORA_ERR_ARG;
+  const int d1 = d + 1;
+  for (int64_t r = 0; r < N; ++r) b[r] = 0.0;
+  for (int64_t t = 0; t < NT; ++t) {
+    const int32_t* e = elem + d1 * t;
+    for (int i = 0; i < d1; ++i)
+      if (e[i] < 0 || e[i] >= N) return ORA_ERR_INDEX;
+    double n[4][3];
+    const double meas = element_normals(d, node, e, n);
+    if (!(meas > 0.0)) return ORA_ERR_DEGENERATE;
+    /* the points relative to an integer near the element (exact differences), so that sin(pi x) keeps
+       its relative accuracy next to the integers: sin(pi (z + k)) = (-1)^k sin(pi z) */
+    double k0[3] = {0.0, 0.0, 0.0};
+    for (int m = 0; m < d; ++m) k0[m] = floor(node[(int64_t)e[0] * d + m] + 0.5);
+    double c[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < nq; ++q) {
+      double p[3] = {0.0, 0.0, 0.0}, z[3] = {0.0, 0.0, 0.0};
+      for (int m = 0; m < d; ++m)
+        for (int i = 0; i < d1; ++i) {
+          p[m] = p[m] + bary[q * d1 + i] * node[(int64_t)e[i] * d + m];
+          z[m] = z[m] + bary[q * d1 + i] * (node[(int64_t)e[i] * d + m] - k0[m]);
+        }
+      double f;
+      if (fkind == 1) {
+        f = 1.0;
+        for (int m = 0; m < d; ++m) f = f * (fmod(k0[m], 2.0) != 0.0 ? -1.0 : 1.0) * sinpi_ref(z[m]);
+      } else {
+        f = f_eval(fkind, d, p, farg, t, q, nq);
+      }
+      for (int i = 0; i < d1; ++i) c[i] = c[i] + (w[q] * f) * bary[q * d1 + i];
+    }
+    for (int i = 0; i < d1; ++i) b[e[i]] = b[e[i]] + meas * c[i];
+  }
+  return ORA_OK;
+}

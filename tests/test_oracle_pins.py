@@ -660,3 +660,49 @@ def test_anisotropic_operator(d):
     iu = np.triu_indices(d)
     rpq, colq, vq, _ = oracle.operator(d, node @ Q.T, elem, oracle.OP_ANISO, np.tile(KQ[iu], (NT, 1)))
     assert np.all(np.abs(vq - v) <= 1e-12 * sc)
+
+
+# --- load vector with rules of any order ("Numerical Quadrature") -----------------------------------------
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_conical_rules_are_exact_to_degree_2n_minus_1(d):
+    """int over the simplex of prod lambda_i^a_i = d! prod a_i! / (|a| + d)! (relative to |tau|), for every
+    |a| <= 2n - 1; positive weights summing to 1."""
+    for n in range(1, 6):
+        bary, w = oracle.quad_rule(d, n)
+        assert bary.shape == (n ** d, d + 1) and np.all(w > 0) and abs(w.sum() - 1) <= 1e-14
+        assert np.allclose(bary.sum(axis=1), 1.0, rtol=0, atol=1e-15) and np.all(bary >= 0)
+        for a in np.ndindex(*([2 * n] * (d + 1))):
+            if sum(a) > 2 * n - 1:
+                continue
+            val = float((w * np.prod(bary ** np.array(a), axis=1)).sum())
+            exact = math.factorial(d) * np.prod([math.factorial(x) for x in a]) / math.factorial(sum(a) + d)
+            assert abs(val - exact) <= 2e-15 * max(1, n), (d, n, a)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_rule_load_vector(d):
+    """One point (the centroid) and f = 1 give |tau|/(d+1) per vertex, as the paper's rules do; for a
+    polynomial f of degree p the load is the same for every rule with 2n - 1 >= p + 1; for the sine product
+    the rules converge (n = 6 and n = 7 agree to 1e-8 on this coarse mesh)."""
+    m = _geometry(d, 3, 0.2, 81)
+    node, elem = m["node"], m["elem"]
+    NT = elem.shape[0]
+    bary1, w1 = oracle.quad_rule(d, 1)
+    b1 = oracle.rhs_rule(d, node, elem, bary1, w1, oracle.F_CONST)
+    b0 = oracle.rhs(d, node, elem, oracle.F_CONST)
+    assert np.allclose(b1, b0, rtol=1e-14, atol=0)
+
+    def poly(x):  # degree 3
+        return 1.0 + x[..., 0] ** 2 * x[..., 1] - 0.5 * x[..., d - 1] ** 3
+
+    loads = []
+    for n in (3, 4, 5):
+        bary, w = oracle.quad_rule(d, n)
+        pts = np.einsum("qi,tim->tqm", bary, node[elem])
+        loads.append(oracle.rhs_rule(d, node, elem, bary, w, oracle.F_QP, poly(pts).ravel()))
+    assert np.allclose(loads[0], loads[1], rtol=1e-13, atol=0) and np.allclose(loads[1], loads[2], rtol=1e-13, atol=0)
+    b6 = oracle.rhs_rule(d, node, elem, *oracle.quad_rule(d, 6), oracle.F_SINPROD)
+    b7 = oracle.rhs_rule(d, node, elem, *oracle.quad_rule(d, 7), oracle.F_SINPROD)
+    inner = np.abs(b7) > 1e-3 * np.abs(b7).max()
+    assert np.allclose(b6[inner], b7[inner], rtol=1e-8, atol=0)
