@@ -475,6 +475,10 @@ def run_ours(args):
         fa.get_error()
         out["operators"] = {"mass_ms": ms_mass, "mass_Melem_s": NT / (ms_mass * 1e-3) / 1e6,
                             "aniso_ms": ms_an, "aniso_Melem_s": NT / (ms_an * 1e-3) / 1e6}
+        # the load vector with the 3-point-per-direction conical rule (exact to degree 5)
+        fa.fem_assemble_rhs_rule(p, node_d, 3, f_kind, None, b)
+        ms_rule = _time_steps(lambda: fa.fem_assemble_rhs_rule(p, node_d, 3, f_kind, None, b), steps_b, flush, s)
+        out["operators"]["rhs_rule3_ms"] = ms_rule
         del K_d
     if not args.no_extras and ws == 1:
         out["extras"] = extras(fa, args, flush, value)

@@ -179,6 +179,23 @@ int fem_apply_dirichlet(fem_pattern_t p, const uint8_t* is_bd, const double* gD,
 int fem_assemble_operator(fem_pattern_t p, const double* node, int op, const double* coef, double* val,
                           fem_stream_t stream);
 
+/* ---- load vector with rules of any order ("Numerical Quadrature") ---------------------------------
+ * I_n(f) = |tau| sum_q w_q f(p_q) on each simplex, with the conical-product Gauss rule of n points per
+ * direction (n^d points, exact for total degree 2n - 1; 1 <= n <= FEM_RULE_MAX_N), built by the library
+ * from Gauss-Legendre and Gauss-Jacobi rules under the collapsed map of the unit square / cube.
+ * fem_quad_rule (HOST, no GPU needed): barycentric points bary [nq][d+1] and weights w [nq] (sum 1),
+ *   nq = n^d; any output may be NULL.
+ * fem_rule_points: the physical points of every element, pts [NT][nq][d] (device).
+ * fem_assemble_rhs_rule: b [N] (device, overwritten) with b_i = sum over elements of
+ *   |tau| sum_q w_q f(p_q) lambda_i(p_q); f_kind FEM_F_CONST (f_arg: 1 value or NULL = 1), FEM_F_SINPROD,
+ *   or FEM_F_QPVALUES (f_arg [NT][nq], the values at the points of fem_rule_points). Float-float
+ *   arithmetic, per-vertex sums in ascending element order (deterministic). Uses the pattern's scratch. */
+#define FEM_RULE_MAX_N 8
+int fem_quad_rule(int d, int n, double* bary, double* w, int* nq);
+int fem_rule_points(fem_pattern_t p, const double* node, int n, double* pts, fem_stream_t stream);
+int fem_assemble_rhs_rule(fem_pattern_t p, const double* node, int n, int f_kind, const double* f_arg, double* b,
+                          fem_stream_t stream);
+
 /* ---- Neumann and Robin sides, pure-Neumann fixes ("Boundary conditions", Sec. 3.3) --------------
  * Side j of element t is the side opposite local vertex j; bdflag [NT][d+1] (int8, device) = 2 marks it
  * Neumann, 3 Robin (du/dn + alpha u = g). Its vertices are the element's other d vertices; |s| is the

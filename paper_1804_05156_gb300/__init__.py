@@ -64,6 +64,9 @@ def lib():
             "fem_assemble_backward": (I32, [P, P, P, I32, P, P, P, P, P, P]),
             "fem_boundary_terms": (I32, [P, P, P, P, C.c_double, C.c_double, P, P, P]),
             "fem_assemble_operator": (I32, [P, P, I32, P, P, P]),
+            "fem_quad_rule": (I32, [I32, I32, P, P, P]),
+            "fem_rule_points": (I32, [P, P, I32, P, P]),
+            "fem_assemble_rhs_rule": (I32, [P, P, I32, I32, P, P, P]),
             "fem_side_points": (I32, [P, P, P, P]),
             "fem_mean_shift": (I32, [P, C.c_int64, P]),
             "fem_zero_average": (I32, [P, P, P, P, P]),
@@ -217,6 +220,31 @@ def fem_assemble_operator(p: Pattern, node, op: int, coef=None, val=None, stream
         val = torch.empty(p.nnz, dtype=torch.float64, device=node.device)
     _check(lib().fem_assemble_operator(p.handle, _ptr(node), op, _ptr(coef), _ptr(val), _stream(stream)))
     return val
+
+
+def fem_quad_rule(d: int, n: int):
+    """(bary [n^d, d+1], w [n^d]) of the library's conical-product Gauss rule (host; no GPU needed)."""
+    import numpy as np
+    nq = n ** d
+    bary = np.zeros((nq, d + 1), np.float64)
+    w = np.zeros(nq, np.float64)
+    m = C.c_int()
+    _check(lib().fem_quad_rule(d, n, bary.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p), C.byref(m)))
+    return bary, w
+
+
+def fem_rule_points(p: Pattern, node, n: int, pts=None, stream=None):
+    if pts is None:
+        pts = torch.empty((p.NT, n ** p.d, p.d), dtype=torch.float64, device=node.device)
+    _check(lib().fem_rule_points(p.handle, _ptr(node), n, _ptr(pts), _stream(stream)))
+    return pts
+
+
+def fem_assemble_rhs_rule(p: Pattern, node, n: int, f_kind=FEM_F_CONST, f_arg=None, b=None, stream=None):
+    if b is None:
+        b = torch.empty(p.N, dtype=torch.float64, device=node.device)
+    _check(lib().fem_assemble_rhs_rule(p.handle, _ptr(node), n, f_kind, _ptr(f_arg), _ptr(b), _stream(stream)))
+    return b
 
 
 def fem_boundary_terms(p: Pattern, node, bdflag, g_side=None, g_const=0.0, alpha=0.0, val=None, b=None, stream=None):

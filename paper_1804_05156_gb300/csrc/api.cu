@@ -351,6 +351,32 @@ int fem_assemble_operator(fem_pattern_t p, const double* node, int op, const dou
   return fem::assemble_tiles(&P, node, nullptr, FEM_F_CONST, nullptr, val, nullptr, (cudaStream_t)stream, op, coef);
 }
 
+int fem_quad_rule(int d, int n, double* bary, double* w, int* nq) {
+  if (d != 2 && d != 3) return set_error(FEM_ERR_ARG, "d must be 2 or 3");
+  if (n < 1 || n > FEM_RULE_MAX_N) return set_error(FEM_ERR_ARG, "n must be in [1, %d]", FEM_RULE_MAX_N);
+  return fem::quad_rule(d, n, bary, w, nq);
+}
+
+int fem_rule_points(fem_pattern_t p, const double* node, int n, double* pts, fem_stream_t stream) {
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  if (n < 1 || n > FEM_RULE_MAX_N) return set_error(FEM_ERR_ARG, "n must be in [1, %d]", FEM_RULE_MAX_N);
+  if (!node || !pts || !aligned(node, 8) || !aligned(pts, 8)) return set_error(FEM_ERR_ARG, "bad node or pts");
+  return fem::rule_points(&p->P, node, n, pts, (cudaStream_t)stream);
+}
+
+int fem_assemble_rhs_rule(fem_pattern_t p, const double* node, int n, int f_kind, const double* f_arg, double* b,
+                          fem_stream_t stream) {
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  if (n < 1 || n > FEM_RULE_MAX_N) return set_error(FEM_ERR_ARG, "n must be in [1, %d]", FEM_RULE_MAX_N);
+  if (!node || !b || !aligned(node, 8) || !aligned(b, 8) || !aligned(f_arg, 8))
+    return set_error(FEM_ERR_ARG, "bad node, b or f_arg");
+  if (f_kind != FEM_F_CONST && f_kind != FEM_F_SINPROD && f_kind != FEM_F_QPVALUES)
+    return set_error(FEM_ERR_ARG, "unknown f_kind %d", f_kind);
+  if (f_kind == FEM_F_QPVALUES && !f_arg) return set_error(FEM_ERR_ARG, "FEM_F_QPVALUES needs f_arg");
+  if (p->P.NT > 0 && !p->P.scratch) return set_error(FEM_ERR_STATE, "pattern has no scratch");
+  return fem::rhs_rule(&p->P, node, n, f_kind, f_arg, b, (cudaStream_t)stream);
+}
+
 int fem_boundary_terms(fem_pattern_t p, const double* node, const int8_t* bdflag, const double* g_side, double g_const,
                        double alpha, double* val, double* b, fem_stream_t stream) {
   if (!p) return set_error(FEM_ERR_ARG, "null pattern");

@@ -167,6 +167,9 @@ int boundary_terms(const Pattern* P, const double* node, const int8_t* bdflag, c
 int side_points(const Pattern* P, const double* node, double* pts, cudaStream_t s);
 int mean_shift(double* x, int64_t n, cudaStream_t s);
 int zero_average(const Pattern* P, const double* node, double* u, double* c_out, cudaStream_t s);
+int quad_rule(int d, int n, double* bary, double* w, int* nq);
+int rhs_rule(const Pattern* P, const double* node, int n, int f_kind, const double* f_arg, double* b, cudaStream_t s);
+int rule_points(const Pattern* P, const double* node, int n, double* pts, cudaStream_t s);
 struct BatchPlan;
 int assemble_backward(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg,
                       const double* w, const double* r, double* gnode, double* gk, cudaStream_t s);

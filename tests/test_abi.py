@@ -75,3 +75,25 @@ def test_oracle_and_product_share_no_code():
     for f in os.listdir(os.path.join(ROOT, "oracle")):
         if f.endswith((".py", ".c", ".h")):
             assert not bad_ora.search(open(os.path.join(ROOT, "oracle", f)).read()), f
+
+
+def test_library_rules_match_the_oracle_rules(libpath):
+    """The library builds its quadrature rules on the host (Newton on the Jacobi recurrence); the oracle
+    by the eigenvalues of the Jacobi matrix. Same rules to rounding, without a GPU."""
+    import numpy as np
+
+    import oracle
+    import paper_1804_05156_gb300 as fa
+    for d in (2, 3):
+        for n in range(1, 9):
+            b1, w1 = fa.fem_quad_rule(d, n)
+            b2, w2 = oracle.quad_rule(d, n)
+            # both orderings are (u, v[, w]) lexicographic with nodes ascending or descending per direction
+            k1 = np.lexsort(b1.T[::-1])
+            k2 = np.lexsort(b2.T[::-1])
+            assert np.allclose(b1[k1], b2[k2], rtol=0, atol=2e-15), (d, n)
+            assert np.allclose(w1[k1], w2[k2], rtol=1e-13, atol=0), (d, n)
+    L = fa.lib()
+    assert L.fem_quad_rule(4, 2, None, None, None) == fa.FEM_ERR_ARG
+    assert L.fem_quad_rule(2, 0, None, None, None) == fa.FEM_ERR_ARG
+    assert L.fem_quad_rule(2, 9, None, None, None) == fa.FEM_ERR_ARG

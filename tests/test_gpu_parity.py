@@ -572,3 +572,28 @@ def test_mass_and_anisotropic_operators_match_oracle(case):
     assert torch.equal(vs, vref)
     with pytest.raises(fa.FemError):
         fa.fem_assemble_operator(p, dev(node), fa.FEM_OP_ANISO, None)
+
+
+# ---- load vector with rules of any order ------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["sq37p", "kuhn5", "delaunay2", "delaunay3"])
+def test_rule_load_vector_matches_oracle(case):
+    d, node, elem, k, _ = mesh_case(case)
+    N, NT = node.shape[0], elem.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    for n in (1, 3, 5):
+        bary, w = fa.fem_quad_rule(d, n)
+        pts = fa.fem_rule_points(p, dev(node), n)
+        ref_pts = np.einsum("qi,tim->tqm", bary, node[elem])
+        assert np.allclose(host(pts), ref_pts, rtol=0, atol=1e-15)
+        vals = np.cos(3.0 * ref_pts[..., 0]) + ref_pts[..., 1]
+        for fk, farg, sarg in ((fa.FEM_F_SINPROD, None, None), (fa.FEM_F_CONST, np.array([1.5]), None),
+                               (fa.FEM_F_QPVALUES, vals.ravel(), np.abs(vals).ravel())):
+            b = fa.fem_assemble_rhs_rule(p, dev(node), n, fk, None if farg is None else dev(farg))
+            fa.get_error()
+            ok = {fa.FEM_F_SINPROD: oracle.F_SINPROD, fa.FEM_F_CONST: oracle.F_CONST, fa.FEM_F_QPVALUES: oracle.F_QP}[fk]
+            bo = oracle.rhs_rule(d, node, elem, bary, w, ok, farg)
+            scale = np.abs(oracle.rhs_rule(d, node, elem, bary, w, ok, sarg)) if sarg is not None else np.abs(bo)
+            assert_close_scaled(host(b), bo, scale + 1e-300, what="rule rhs n=%d f=%d" % (n, fk))
+            b2 = fa.fem_assemble_rhs_rule(p, dev(node), n, fk, None if farg is None else dev(farg))
+            assert torch.equal(b, b2)
