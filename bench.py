@@ -479,6 +479,22 @@ def run_ours(args):
         fa.fem_assemble_rhs_rule(p, node_d, 3, f_kind, None, b)
         ms_rule = _time_steps(lambda: fa.fem_assemble_rhs_rule(p, node_d, 3, f_kind, None, b), steps_b, flush, s)
         out["operators"]["rhs_rule3_ms"] = ms_rule
+        # y = A u matrix-free, next to a library CSR SpMV (cuSPARSE through torch) of the assembled A
+        u_d = torch.as_tensor(meshgen.normal(5, 5, N)).cuda()
+        y_d = torch.empty_like(u_d)
+        fa.fem_apply_stiffness(p, node_d, k_d, u_d, None, y_d)
+        ms_ap = _time_steps(lambda: fa.fem_apply_stiffness(p, node_d, k_d, u_d, None, y_d), steps_b, flush, s)
+        fa.fem_assemble(p, node_d, k_d, f_kind, None, val, b, variant)
+        import warnings
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore")
+            A_csr = torch.sparse_csr_tensor(p.row_ptr.long(), p.col_idx.long(), val, size=(N, N))
+        ms_sp = _time_steps(lambda: torch.mv(A_csr, u_d), steps_b, flush, s)
+        fa.get_error()
+        out["operators"]["apply_ms"] = ms_ap
+        out["operators"]["apply_Melem_s"] = NT / (ms_ap * 1e-3) / 1e6
+        out["operators"]["assembled_spmv_cusparse_ms"] = ms_sp
+        del A_csr, u_d, y_d
         del K_d
     if not args.no_extras and ws == 1:
         out["extras"] = extras(fa, args, flush, value)

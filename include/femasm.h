@@ -179,6 +179,17 @@ int fem_apply_dirichlet(fem_pattern_t p, const uint8_t* is_bd, const double* gD,
 int fem_assemble_operator(fem_pattern_t p, const double* node, int op, const double* coef, double* val,
                           fem_stream_t stream);
 
+/* ---- matrix-free operator --------------------------------------------------------------------------
+ * y = A u for the stiffness matrix with coefficient k [NT] (nullable: 1) without forming A: each element
+ * recomputes its local matrix (float-float, as fem_assemble) and adds sum_{j != i} a_ij (u_j - u_i) to
+ * row i (a_ii = -sum_{j != i} a_ij), summed per row in ascending element order (deterministic). With
+ * is_bd [N] (uint8, nullable) the operator is the Dirichlet-eliminated one of fem_apply_dirichlet:
+ * eliminated vertices contribute nothing to the free rows and their own rows give y = u. u, y [N]
+ * (device, distinct). Uses the tile plan (built on the first call if the pattern has none: synchronises)
+ * and its packet buffer. */
+int fem_apply_stiffness(fem_pattern_t p, const double* node, const double* k, const double* u, const uint8_t* is_bd,
+                        double* y, fem_stream_t stream);
+
 /* ---- load vector with rules of any order ("Numerical Quadrature") ---------------------------------
  * I_n(f) = |tau| sum_q w_q f(p_q) on each simplex, with the conical-product Gauss rule of n points per
  * direction (n^d points, exact for total degree 2n - 1; 1 <= n <= FEM_RULE_MAX_N), built by the library

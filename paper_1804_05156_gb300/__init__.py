@@ -65,6 +65,7 @@ def lib():
             "fem_boundary_terms": (I32, [P, P, P, P, C.c_double, C.c_double, P, P, P]),
             "fem_assemble_operator": (I32, [P, P, I32, P, P, P]),
             "fem_quad_rule": (I32, [I32, I32, P, P, P]),
+            "fem_apply_stiffness": (I32, [P, P, P, P, P, P, P]),
             "fem_rule_points": (I32, [P, P, I32, P, P]),
             "fem_assemble_rhs_rule": (I32, [P, P, I32, I32, P, P, P]),
             "fem_side_points": (I32, [P, P, P, P]),
@@ -220,6 +221,14 @@ def fem_assemble_operator(p: Pattern, node, op: int, coef=None, val=None, stream
         val = torch.empty(p.nnz, dtype=torch.float64, device=node.device)
     _check(lib().fem_assemble_operator(p.handle, _ptr(node), op, _ptr(coef), _ptr(val), _stream(stream)))
     return val
+
+
+def fem_apply_stiffness(p: Pattern, node, k, u, is_bd=None, y=None, stream=None):
+    """y = A u, matrix-free (the Dirichlet-eliminated operator when is_bd is given)."""
+    if y is None:
+        y = torch.empty_like(u)
+    _check(lib().fem_apply_stiffness(p.handle, _ptr(node), _ptr(k), _ptr(u), _ptr(is_bd), _ptr(y), _stream(stream)))
+    return y
 
 
 def fem_quad_rule(d: int, n: int):

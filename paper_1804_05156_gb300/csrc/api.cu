@@ -324,6 +324,8 @@ int fem_apply_dirichlet(fem_pattern_t p, const uint8_t* is_bd, const double* gD,
   return fem::apply_dirichlet(&p->P, is_bd, gD, val, b, free_node, n_free, (cudaStream_t)stream);
 }
 
+static int ensure_tile_plan(Pattern& P, cudaStream_t s);
+
 int fem_assemble_operator(fem_pattern_t p, const double* node, int op, const double* coef, double* val,
                           fem_stream_t stream) {
   if (!p) return set_error(FEM_ERR_ARG, "null pattern");
@@ -338,17 +340,40 @@ int fem_assemble_operator(fem_pattern_t p, const double* node, int op, const dou
     if (P.nnz > 0) FEM_CUDA(cudaMemsetAsync(val, 0, sizeof(double) * P.nnz, (cudaStream_t)stream));
     return FEM_OK;
   }
-  if (!P.tile.ok) {
-    fem::TilePlan T;
-    int rc = fem::build_tile_plan(&P, P.blk.order, 128, &T, (cudaStream_t)stream);
-    if (rc) return rc;
-    if (!T.ok) {
-      fem::free_tile_plan(T);
-      return set_error(FEM_ERR_STATE, "this mesh has no tile plan (a row longer than 256 entries)");
-    }
-    P.tile = T;
-  }
+  int rc = ensure_tile_plan(P, (cudaStream_t)stream);
+  if (rc) return rc;
   return fem::assemble_tiles(&P, node, nullptr, FEM_F_CONST, nullptr, val, nullptr, (cudaStream_t)stream, op, coef);
+}
+
+static int ensure_tile_plan(Pattern& P, cudaStream_t s) {
+  if (P.tile.ok) return FEM_OK;
+  fem::TilePlan T;
+  int rc = fem::build_tile_plan(&P, P.blk.order, 128, &T, s);
+  if (rc) return rc;
+  if (!T.ok) {
+    fem::free_tile_plan(T);
+    return set_error(FEM_ERR_STATE, "this mesh has no tile plan (a row longer than 256 entries)");
+  }
+  P.tile = T;
+  return FEM_OK;
+}
+
+int fem_apply_stiffness(fem_pattern_t p, const double* node, const double* k, const double* u, const uint8_t* is_bd,
+                        double* y, fem_stream_t stream) {
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  if (!node || !u || !y) return set_error(FEM_ERR_ARG, "node, u and y are required");
+  if (u == y) return set_error(FEM_ERR_ARG, "u and y must be distinct");
+  if (!aligned(node, 8) || !aligned(k, 8) || !aligned(u, 8) || !aligned(y, 8)) return set_error(FEM_ERR_ARG, "misaligned array");
+  Pattern& P = p->P;
+  if (P.N == 0) return FEM_OK;
+  if (P.NT == 0) {
+    FEM_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * P.N, (cudaStream_t)stream));
+    return FEM_OK;
+  }
+  int rc = ensure_tile_plan(P, (cudaStream_t)stream);
+  if (rc) return rc;
+  return fem::assemble_tiles(&P, node, k, FEM_F_CONST, nullptr, nullptr, nullptr, (cudaStream_t)stream, 3, nullptr, u,
+                             is_bd, y);
 }
 
 int fem_quad_rule(int d, int n, double* bary, double* w, int* nq) {

@@ -140,8 +140,10 @@ int blocked_smem_need(const BlockPlan& B, int d, bool sinprod);
 int assemble_blocked(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg,
                      double* val, double* b, cudaStream_t s);
 // op: 0 stiffness (+ load vector), 1 mass, 2 anisotropic (values only; opk: their coefficients)
+// op 3: y = A u matrix-free (the stiffness matrix with coefficient k; isbd: eliminated rows give u)
 int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg, double* val,
-                   double* b, cudaStream_t s, int op = 0, const double* opk = nullptr);
+                   double* b, cudaStream_t s, int op = 0, const double* opk = nullptr, const double* u = nullptr,
+                   const uint8_t* isbd = nullptr, double* y = nullptr);
 int tile_fused_smem(const TilePlan& T, int d);  // 0: the fused launch does not fit
 
 // scratch doubles per element: stiffness unique entries + rhs entries (+ gradient entries)

@@ -201,7 +201,7 @@ __device__ __forceinline__ bool element_df3(const VtxDF<3>* const (&V)[4], df2 k
 // Anisotropic div(K grad u): a_ij = n_i^T K n_j / (d!^2 |tau|) = |tau| grad lambda_i^T K grad lambda_j
 // (eq. (dlambda)), K symmetric given by its upper triangle; the diagonal is left to the caller (the
 // row sums vanish, as for the stiffness matrix).
-constexpr int kOpStiffness = 0, kOpMass = 1, kOpAniso = 2;
+constexpr int kOpStiffness = 0, kOpMass = 1, kOpAniso = 2, kOpApply = 3;  // kOpApply: y = A u, matrix-free
 
 template <int D>
 __device__ __forceinline__ void sym_tensor_df(const double* __restrict__ c, df2 (&K)[D][D]) {

@@ -43,8 +43,11 @@ struct TileArgs {
   const int32_t* ipos;
   float4* pk;
   int xs_bytes;
-  int op;               // kOpStiffness (with the load vector), kOpMass or kOpAniso (values only)
+  int op;               // kOpStiffness (with the load vector), kOpMass or kOpAniso (values only), kOpApply
   const double* opk;    // operator coefficients: mass c [NT] (nullable), aniso tensor [NT][d(d+1)/2]
+  const double* u;      // kOpApply: the vector A is applied to [N]
+  const uint8_t* isbd;  // kOpApply: eliminated (Dirichlet) vertices, nullable
+  int u_off;            // kOpApply: shared-memory offset of the staged u values
 };
 
 struct RowArgs {
@@ -94,6 +97,9 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
 #pragma unroll
       for (int m = 0; m < D; ++m) scs[v * D + m] = sincospi_half(x.x[m], tab);
     }
+    if (a.op == kOpApply)  // eliminated vertices contribute nothing to the free rows
+      reinterpret_cast<df2*>(sm + a.u_off)[v] =
+          (a.isbd && __ldg(a.isbd + R)) ? df2{0.0f, 0.0f} : df_from_double(__ldg(a.u + R));
   }
   __syncthreads();
   if (!act) return;
@@ -105,7 +111,7 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
 #pragma unroll
   for (int i = 0; i < D1; ++i) L.bt[i] = df2{0.0f, 0.0f};
   bool ok;
-  if (a.op != kOpStiffness) {
+  if (a.op == kOpMass || a.op == kOpAniso) {
     const VtxDF<D>* V[D1];
 #pragma unroll
     for (int i = 0; i < D1; ++i) V[i] = &xs[lv[i]];
@@ -124,6 +130,22 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
     ok = element_df3(V, kt, want_a, want_b, f_kind, fconst, f_arg, t, tab, L, false);  // diagonals: in the gather
   }
   if (!ok) report(err, FEM_ERR_DEGENERATE);
+  if (a.op == kOpApply) {
+    // (A u)_i contribution of the element: sum_{j != i} a_ij (u_j - u_i), since a_ii = -sum_{j != i} a_ij
+    const df2* ux = reinterpret_cast<const df2*>(sm + a.u_off);
+    df2 uu[D1];
+#pragma unroll
+    for (int i = 0; i < D1; ++i) uu[i] = ux[lv[i]];
+#pragma unroll
+    for (int i = 0; i < D1; ++i) {
+      df2 y = {0.0f, 0.0f};
+#pragma unroll
+      for (int jj = 0; jj < D1; ++jj)
+        if (jj != i) y = df_add(y, df_mul(L.a[pidx<D>(i, jj)], df_sub(uu[jj], uu[i])));
+      reinterpret_cast<float2*>(a.pk)[qi[i]] = make_float2(y.h, y.l);
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < D1; ++i) {
     df2 o[D];  // a_ij for the other local indices j, ascending
@@ -282,6 +304,31 @@ __global__ void __launch_bounds__(256) k_row_gather(RowArgs g, double* __restric
   rows_of_warp<D, PW, false>(g, R0, reinterpret_cast<df2*>(sm) + (size_t)wid * 32 * g.max_row, val, bvec);
 }
 
+// y = A u: per row, its element contributions in ascending element order; eliminated rows give u
+__global__ void __launch_bounds__(256) k_apply_gather(int64_t N, const int32_t* __restrict__ inc_ptr,
+                                                      const float2* __restrict__ pk, const double* __restrict__ u,
+                                                      const uint8_t* __restrict__ isbd, double* __restrict__ y) {
+  const int64_t R = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (R >= N) return;
+  if (isbd && __ldg(isbd + R)) {
+    y[R] = __ldg(u + R);
+    return;
+  }
+  df2 acc = {0.0f, 0.0f};
+  const int q1 = __ldg(inc_ptr + R + 1);
+  int q = __ldg(inc_ptr + R);
+  for (; q + 1 < q1; q += 2) {
+    const float2 a = __ldg(pk + q), b = __ldg(pk + q + 1);
+    acc = df_acc(acc, df2{a.x, a.y});
+    acc = df_acc(acc, df2{b.x, b.y});
+  }
+  if (q < q1) {
+    const float2 a = __ldg(pk + q);
+    acc = df_acc(acc, df2{a.x, a.y});
+  }
+  y[R] = df_to_double(acc);
+}
+
 constexpr int kBarrierPolls = 1 << 24;  // bounded grid-barrier wait (with a short sleep per poll)
 constexpr int kItemsPerClaim = 8;       // tiles (or row groups) taken per counter increment
 
@@ -364,7 +411,8 @@ int tile_fused_smem(const TilePlan& T, int d) {
 }
 
 int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_kind, const double* f_arg, double* val,
-                   double* b, cudaStream_t s, int op, const double* opk) {
+                   double* b, cudaStream_t s, int op, const double* opk, const double* u, const uint8_t* isbd,
+                   double* y) {
   int* err = device_error_word();
   if (!err) return set_error(FEM_ERR_OOM, "cannot allocate the device error word");
   const float4* tab = sincos_table_device();
@@ -388,6 +436,8 @@ int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_
   a.xs_bytes = ((T.max_v * vtx_bytes(D)) + 15) / 16 * 16;
   a.op = op;
   a.opk = opk;
+  a.u = u;
+  a.isbd = isbd;
   if (op != kOpStiffness) {
     b = nullptr;  // operators give values only
     f_kind = FEM_F_CONST;
@@ -401,7 +451,28 @@ int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_
   g.rdp = T.rdp;
   g.pk = T.pk;
   g.diag_in_packet = op == kOpMass;
-  const int want_a = val != nullptr, want_b = b != nullptr;
+  const int want_a = val != nullptr || op == kOpApply, want_b = b != nullptr;
+  if (op == kOpApply) {
+    a.u_off = ((tile_smem_need(T, D, false)) + 15) / 16 * 16;
+    const int smem = a.u_off + T.max_v * (int)sizeof(df2);
+#define FEM_APPLY_LAUNCH(DD, TT)                                                                              \
+  do {                                                                                                        \
+    if (smem > 48 * 1024)                                                                                     \
+      FEM_CUDA(cudaFuncSetAttribute(k_tile_elements<DD, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); \
+    FEM_LAUNCH((k_tile_elements<DD, TT>), T.ntiles, TT, smem, s, a, node, k, FEM_F_CONST, nullptr, 1, 0, tab, err); \
+  } while (0)
+    if (D == 2) {
+      if (T.TE == 128) FEM_APPLY_LAUNCH(2, 128);
+      else FEM_APPLY_LAUNCH(2, 256);
+    } else {
+      if (T.TE == 128) FEM_APPLY_LAUNCH(3, 128);
+      else FEM_APPLY_LAUNCH(3, 256);
+    }
+#undef FEM_APPLY_LAUNCH
+    FEM_LAUNCH(k_apply_gather, (int)((P->N + 255) / 256), 256, 0, s, P->N, P->inc_ptr,
+               reinterpret_cast<const float2*>(T.pk), u, isbd, y);
+    return FEM_OK;
+  }
   if (T.fused) {
     // one cooperative launch: as many CTAs as are resident at once, counters zeroed in-stream
     const int smem = tile_fused_smem(T, D);
