@@ -4,9 +4,11 @@ triangle mesh (N = 4,198,401 vertices, NT = 8,388,608 elements, lognormal k, f =
 
 A step is one pass of the value phase of the assembly on a built pattern: stiffness values and the
 load vector (one fem_assemble call), inputs resident in HBM. The pattern build (once per topology)
-is timed separately and reported as pattern_build_ms. e2e repeats the step through the same C ABI
-call with the inputs copied from pinned host memory and the outputs read back inside the timed
-region. The L2 is flushed (a 512 MB write) between timed steps, outside the timed events.
+is timed separately and reported as pattern_build_ms. e2e repeats the step through the C ABI's
+host-buffer call (fem_assemble_host): every step copies its inputs from page-locked host memory and
+its outputs (val, b) back inside the timed region, the steps pipelined within the call (the
+one-step-per-call time is reported beside it). The L2 is flushed (a 512 MB write) between timed
+steps, outside the timed events.
 
 --impl reference times the CPU oracle (the plain FP64 reference) on a bounded sample of the same
 workload, on this host's cores. Under torchrun each rank assembles its own copy of the mesh
@@ -33,11 +35,15 @@ import meshgen  # noqa: E402
 METRIC = "P1 assembly Melem/s (FP64) + % HBM peak; batched & fwd+bwd vs plain fwd"
 
 
-def peaks():
+def _measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(p):
-        j = json.load(open(p))
-        return float(j.get("hbm_gbs", 6800.0)), "measured"
+    return json.load(open(p)) if os.path.exists(p) else {}
+
+
+def peaks():
+    j = _measured_peaks()
+    if "hbm_gbs" in j:
+        return float(j["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
 
 
@@ -107,26 +113,34 @@ def _nvtx(torch):
         return (lambda name: None), (lambda: None)
 
 
-def profiled_traffic(fa, kernels, config, path, shape):
-    """DRAM bytes (read + write) per step of the step's kernels, summed from the committed ncu summaries
-    under profiles/ (lines starting 'traffic-record:'), if every kernel was captured on this config and
-    plan from the current kernel sources; else None."""
+def profiled(kernels, config, path, shape, kind="traffic", field="bytes_per_launch"):
+    """Per-step sum over the step's kernels of a per-launch ncu figure, from the committed summaries
+    under profiles/ (lines starting '<kind>-record:'), if every kernel was captured on this config and
+    plan from its current source (the record names the kernel's source file and that file's digest);
+    else None. kind "traffic": DRAM bytes read + written; kind "inst": warp instructions executed."""
     from paper_1804_05156_gb300 import buildlib
-    digest = buildlib.source_digest()
-    plan = str(path["tile_elems"]) if path["path"] == "tiles" else str(shape.get("rows_per_block"))
+    digests = {}
+
+    def current(kv):
+        src = kv.get("source")
+        if src not in digests:
+            digests[src] = buildlib.tu_digest(src) if src else buildlib.source_digest()
+        return digests[src]
+    plan = str(path["tile_elems"]) if path["path"].startswith("tiles") else str(shape.get("rows_per_block"))
     pdir = os.path.join(ROOT, "profiles")
     found = {}
+    tag = kind + "-record:"
     if os.path.isdir(pdir):
         for fn in sorted(os.listdir(pdir)):
             if not fn.endswith(".md"):
                 continue
             for line in open(os.path.join(pdir, fn)):
-                if not line.startswith("traffic-record:"):
+                if not line.startswith(tag):
                     continue
-                kv = dict(x.strip().split("=", 1) for x in line[len("traffic-record:"):].split(";") if "=" in x)
+                kv = dict(x.strip().split("=", 1) for x in line[len(tag):].split(";") if "=" in x)
                 if (kv.get("kernel") in kernels and kv.get("config") == config and kv.get("plan") == plan
-                        and kv.get("source_digest") == digest):
-                    found[kv["kernel"]] = (float(kv["bytes_per_launch"]), fn)
+                        and field in kv and kv.get("source_digest") == current(kv)):
+                    found[kv["kernel"]] = (float(kv[field]), fn)
     if kernels and all(k in found for k in kernels):
         return sum(found[k][0] for k in kernels), ", ".join(sorted({found[k][1] for k in kernels}))
     return None, "no ncu capture of these kernels on this plan and source digest under profiles/"
@@ -392,37 +406,60 @@ def run_ours(args):
     achieved = alg / (k_ms * 1e-3) / 1e9
     shape = fa.fem_pattern_launch_shape(p)
     path = fa.fem_pattern_value_path(p)
-    traffic, traffic_src = profiled_traffic(fa, names, args.config, path, shape)
+    traffic, traffic_src = profiled(names, args.config, path, shape)
+    inst, inst_src = profiled(names, args.config, path, shape, "inst", "warp_inst_per_launch")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "traffic_source": traffic_src, "kernel": " + ".join(names), "kernel_ms": k_ms,
             "peak_source": peak_kind, "algorithmic_bytes": alg, "step_algorithmic_GBs": alg / (ms * 1e-3) / 1e9,
             "kernels": {n: {"launches": c, "mean_ms": t / c, "share": (t / c) / k_ms} for n, (c, t) in kt.items()}}
+    # what does bind the step: instruction issue (the float-float arithmetic runs on the FP32/INT32 pipes).
+    # Peak = SMs x 4 schedulers x 1 warp-instruction per clock at the median SM clock sampled during the
+    # timed steps; achieved = the ncu-counted warp instructions of the step's kernels / their time.
+    clocks = clk.summary()
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = clocks.get("sm_mhz") or _measured_peaks().get("sm_max_mhz") or 2070.0
+    issue_peak = nsm * 4 * mhz * 1e6
+    roof["issue"] = {"bound": "alu", "unit": "warp-inst/s", "peak": issue_peak,
+                     "peak_basis": "%d SMs x 4 schedulers x 1 warp-instruction/clock at %.0f MHz" % (nsm, mhz),
+                     "warp_inst_per_step": inst, "source": inst_src,
+                     "achieved": (inst / (k_ms * 1e-3)) if inst else None,
+                     "frac": (inst / (k_ms * 1e-3) / issue_peak) if inst else None}
 
-    # e2e: host buffers through the same call, copies inside the timed region
+    # e2e: host buffers through the C ABI (fem_assemble_host): every step copies its inputs in from
+    # page-locked host memory and its outputs (val, b) back; the call pipelines the steps (inputs of
+    # step i+1 and outputs of step i-1 in flight while step i computes)
     node_h = torch.as_tensor(node).pin_memory()
     k_h = torch.as_tensor(k).pin_memory() if k is not None else None
-    val_h = torch.empty(p.nnz, dtype=torch.float64).pin_memory()
-    b_h = torch.empty(N, dtype=torch.float64).pin_memory()
-    e2e_steps = max(3, args.steps // 2)
-    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
-    for i in range(e2e_steps + 1):
-        flush.zero_()
-        if i > 0:
-            e_ev[i - 1][0].record(s)
-        node_d.copy_(node_h, non_blocking=True)
-        if k_h is not None:
-            k_d.copy_(k_h, non_blocking=True)
-        step()
-        val_h.copy_(val, non_blocking=True)
-        b_h.copy_(b, non_blocking=True)
-        if i > 0:
-            e_ev[i - 1][1].record(s)
+    val_hs = [torch.empty(p.nnz, dtype=torch.float64).pin_memory() for _ in range(2)]
+    b_hs = [torch.empty(N, dtype=torch.float64).pin_memory() for _ in range(2)]
+    e2e_steps = max(3, args.steps)
+    nodes_l, ks_l = [node_h] * e2e_steps, [k_h] * e2e_steps
+    vals_l = [val_hs[i % 2] for i in range(e2e_steps)]
+    bs_l = [b_hs[i % 2] for i in range(e2e_steps)]
+    fa.fem_assemble_host(p, nodes_l[:2], ks_l[:2], f_kind, None, vals_l[:2], bs_l[:2], s)  # warm-up
     torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(bb) for a, bb in e_ev) / e2e_steps
+    e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_a.record(s)
+    fa.fem_assemble_host(p, nodes_l, ks_l, f_kind, None, vals_l, bs_l, s)
+    e_b.record(s)
+    torch.cuda.synchronize()
+    e2e_ms = e_a.elapsed_time(e_b) / e2e_steps
+    # the same, one step per call (no overlap between steps)
+    one = []
+    for i in range(3):
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(s)
+        fa.fem_assemble_host(p, nodes_l[:1], ks_l[:1], f_kind, None, vals_l[:1], bs_l[:1], s)
+        a1.record(s)
+        torch.cuda.synchronize()
+        one.append(a0.elapsed_time(a1))
+    e2e_one_ms = sum(one) / len(one)
+    fa.get_error()
     if dist:
         e2e_ms = max_over_ranks(dist, e2e_ms)
+        e2e_one_ms = max_over_ranks(dist, e2e_one_ms)
     h2d = node_h.numel() * 8 + (k_h.numel() * 8 if k_h is not None else 0)
-    d2h = (val_h.numel() + b_h.numel()) * 8
+    d2h = (p.nnz + N) * 8
 
     out = {"metric": METRIC, "value": value, "unit": "Melem/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -438,9 +475,11 @@ def run_ours(args):
            "value_path": path,
            "roofline": roof,
            "e2e": {"value": NT_job / (e2e_ms * 1e-3) / 1e6, "unit": "Melem/s", "ms_per_step": e2e_ms,
-                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                   "api": "fem_assemble_host (page-locked host buffers, steps pipelined in one call)",
+                   "one_step_per_call_ms": e2e_one_ms},
            "gpu_launches": launches,
-           "clocks": clk.summary()}
+           "clocks": clocks}
     # secondary timings on the same mesh: atomic variant, boundary + Dirichlet elimination
     fa.fem_assemble(p, node_d, k_d, f_kind, None, val, b, fa.FEM_ATOMIC)
     ms_at = _time_steps(lambda: fa.fem_assemble(p, node_d, k_d, f_kind, None, val, b, fa.FEM_ATOMIC),

@@ -143,6 +143,24 @@ int fem_assemble_stiffness(fem_pattern_t p, const double* node, const double* k,
 int fem_assemble_rhs(fem_pattern_t p, const double* node, int f_kind, const double* f_arg, double* b,
                      int variant, fem_stream_t stream);
 
+/* ---- host-resident inputs and outputs -------------------------------------------------------------
+ * `steps` assemblies of one pattern from and to host memory (no counterpart in the paper, whose arrays
+ * live in one memory). Step i reads node_h[i] [N][d] and k_h[i] [NT] (k_h or k_h[i] NULL: k = 1) and
+ * writes val_h[i] [nnz] and b_h[i] [N] (val_h/b_h or an entry NULL: that output is not formed), all
+ * HOST pointers; f_kind and f_arg (a DEVICE pointer, as in fem_assemble) are shared by the steps. Each
+ * step copies its inputs to device buffers the pattern owns, runs fem_assemble (FEM_DETERMINISTIC) on
+ * `stream` and copies its outputs back: the same bits as fem_assemble on device arrays. The steps are
+ * pipelined over `stream` and two streams of the pattern's own, with two sets of device buffers: the
+ * inputs of step i+1 and the outputs of step i-1 are copied while step i computes. Page-locked host
+ * memory lets the copies overlap (pageable memory gives the same results, with less overlap). The call
+ * returns when every output is in host memory; later work on `stream` is ordered after it. The first
+ * call allocates 2 (N d + NT + nnz + N) doubles of device memory, kept until fem_pattern_destroy.
+ * Errors: FEM_ERR_ARG (null pattern or node_h entry, negative steps, misaligned pointer), FEM_ERR_OOM,
+ * those of fem_assemble, FEM_ERR_CUDA. */
+int fem_assemble_host(fem_pattern_t p, int steps, const double* const* node_h, const double* const* k_h,
+                      int f_kind, const double* f_arg, double* const* val_h, double* const* b_h,
+                      fem_stream_t stream);
+
 /* ---- boundary (Sec. 1.2, Sec. 3.3) -------------------------------------------------------------
  * is_bd [N] (uint8, overwritten) = 1 for every vertex of a Dirichlet side. Side i of element t is
  * the side opposite vertex i (2-D: vertices (i+1, i+2) mod 3; 3-D: faces [2 4 3], [1 3 4],

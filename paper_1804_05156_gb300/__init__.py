@@ -81,6 +81,7 @@ def lib():
             "fem_last_error_string": (C.c_char_p, []),
             "fem_launch_count": (I64, []),
             "fem_assemble_noalloc": (I32, [P, P, P, I32, P, P, P, P]),
+            "fem_assemble_host": (I32, [P, I32, P, P, I32, P, P, P, P]),
             "fem_timing_enable": (I32, [I32]),
             "fem_timing_report": (I32, [C.c_char_p, I64]),
         }
@@ -288,6 +289,36 @@ def fem_assemble_noalloc(p: Pattern, node, k=None, f_kind=FEM_F_CONST, f_arg=Non
     """Deterministic assembly that allocates nothing (scratch in a fixed device array; see femasm.h)."""
     _check(lib().fem_assemble_noalloc(p.handle, _ptr(node), _ptr(k), f_kind, _ptr(f_arg), _ptr(val), _ptr(b),
                                       _stream(stream)))
+
+
+def _host_ptrs(ts, steps, what):
+    """ctypes array of the data pointers of `steps` contiguous float64 host tensors (None entries: NULL)."""
+    if ts is None:
+        return None
+    if len(ts) != steps:
+        raise FemError(FEM_ERR_ARG, "%s: expected %d entries" % (what, steps))
+    out = (C.c_void_p * steps)()
+    for i, t in enumerate(ts):
+        if t is None:
+            continue
+        if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+            raise FemError(FEM_ERR_ARG, "%s[%d]: expected a contiguous float64 host tensor" % (what, i))
+        out[i] = t.data_ptr()
+    return out
+
+
+def fem_assemble_host(p: Pattern, nodes, ks=None, f_kind=FEM_F_CONST, f_arg=None, vals=None, bs=None, stream=None):
+    """len(nodes) assemblies from and to host memory, pipelined (see femasm.h): nodes[i] [N, d], ks[i] [NT]
+    (None: k = 1) in, vals[i] [nnz] and bs[i] [N] out, all float64 host tensors (page-locked for overlap);
+    f_arg a CUDA tensor or None. Returns when every output is written."""
+    steps = len(nodes)
+    for what, ts, n in (("nodes", nodes, p.N * p.d), ("ks", ks, p.NT), ("vals", vals, p.nnz), ("bs", bs, p.N)):
+        for t in (ts or []):
+            if t is not None and t.numel() != n:
+                raise FemError(FEM_ERR_ARG, "%s: expected %d values per step" % (what, n))
+    _check(lib().fem_assemble_host(p.handle, steps, _host_ptrs(nodes, steps, "nodes"), _host_ptrs(ks, steps, "ks"),
+                                   f_kind, _ptr(f_arg), _host_ptrs(vals, steps, "vals"), _host_ptrs(bs, steps, "bs"),
+                                   _stream(stream)))
 
 
 def fem_assemble_stiffness(p: Pattern, node, k, val, variant=FEM_DETERMINISTIC, stream=None):

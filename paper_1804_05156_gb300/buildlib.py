@@ -48,6 +48,21 @@ def source_digest() -> str:
     return h.hexdigest()
 
 
+def tu_digest(cu: str) -> str:
+    """sha256 over one kernel source file (by name, in csrc/), every csrc header and the ABI header: the
+    code a kernel of that file is compiled from. A profile record keyed by it stays valid while only
+    other translation units change."""
+    h = hashlib.sha256()
+    files = [os.path.join(CSRC, os.path.basename(cu))] + sorted(glob.glob(os.path.join(CSRC, "*.cuh")))
+    files.append(os.path.join(ROOT, "include", "femasm.h"))
+    for f in files:
+        h.update(os.path.basename(f).encode() + b"\0")
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+        h.update(b"\0")
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     deps = srcs + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "femasm.h"), __file__]
@@ -70,7 +85,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
 if __name__ == "__main__":
     if "--digest" in sys.argv:
-        print(source_digest())
+        i = sys.argv.index("--digest")
+        print(tu_digest(sys.argv[i + 1]) if i + 1 < len(sys.argv) else source_digest())
         sys.exit(0)
     build(force="--force" in sys.argv, verbose=True,
           extra=["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else None)

@@ -97,6 +97,7 @@ namespace {
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 void free_pattern(Pattern& P) {
+  fem::free_host_exec(P);
   fem::free_block_plan(P.blk);
   fem::free_tile_plan(P.tile);
   cudaFree(P.elem);

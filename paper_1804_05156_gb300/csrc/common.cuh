@@ -129,7 +129,9 @@ struct Pattern {
   bool one_launch = false;     // plans must run in a single launch (batched assembly under a graph)
   int* work_counter = nullptr; // [4] device counters: [0] blocked persistent launch, [1..3] fused tile launch
   uint8_t* bd_whole = nullptr;  // [N] whole-boundary vertex mask, computed on first request
+  struct HostExec* hx = nullptr;  // streams and device buffers of fem_assemble_host, made on first use
 };
+void free_host_exec(Pattern& P);
 // (Re)build P->blk, halving the block size until the packed limits hold (blk.ok false if they never do).
 int rebuild_block_plan(Pattern* P, const double* node_hint, const int32_t* group, cudaStream_t s);
 // For a pattern that must run in one launch: switch the tile plan to its fused form, or fall back to the

@@ -643,3 +643,36 @@ def test_matrix_free_apply_matches_assembled_operator(case):
     # constants are in the kernel of A
     y1 = fa.fem_apply_stiffness(p, dev(node), dev(k), dev(np.full(N, 3.0)))
     assert float(y1.abs().max()) <= 1e-12 * float(np.abs(vo).max()) * 3.0
+
+
+@pytest.mark.parametrize("case", ["sq37p", "delaunay3"])
+def test_host_steps_match_device_assembly(case):
+    """fem_assemble_host: several pipelined steps from and to host memory (pinned and pageable, with and
+    without k, with and without the load vector) give the bits of fem_assemble on device arrays, and
+    match the oracle."""
+    d, node, elem, k, _ = mesh_case(case)
+    N, NT = node.shape[0], elem.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    fa.fem_pattern_set_locality(p, dev(node))
+    rng = np.random.default_rng(77)
+    steps = 5
+    nodes = [node * (1.0 + 0.1 * i) + 0.01 * i for i in range(steps)]  # affine copies: valid meshes
+    ks = [rng.lognormal(size=NT) if i != 1 else None for i in range(steps)]
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+    node_h = [pin(x) if i != 2 else torch.as_tensor(np.ascontiguousarray(x)) for i, x in enumerate(nodes)]
+    k_h = [None if x is None else pin(x) for x in ks]
+    val_h = [torch.zeros(p.nnz, dtype=torch.float64).pin_memory() for _ in range(steps)]
+    b_h = [torch.zeros(N, dtype=torch.float64).pin_memory() if i != 3 else torch.zeros(N, dtype=torch.float64)
+           for i in range(steps)]
+    fa.fem_assemble_host(p, node_h, k_h, fa.FEM_F_SINPROD, None, val_h, b_h)
+    fa.get_error()
+    for i in range(steps):
+        v, b = fa.assemble(p, dev(nodes[i]), None if ks[i] is None else dev(ks[i]), fa.FEM_F_SINPROD)
+        assert torch.equal(val_h[i], v.cpu()) and torch.equal(b_h[i], b.cpu()), i
+        _, _, vo, so = oracle.assemble(d, nodes[i], elem, ks[i])
+        assert_close_scaled(val_h[i].numpy(), vo, so)
+    # outputs left out, one step, and no steps
+    val1 = [torch.zeros(p.nnz, dtype=torch.float64).pin_memory()]
+    fa.fem_assemble_host(p, node_h[:1], k_h[:1], fa.FEM_F_SINPROD, None, val1, None)
+    assert torch.equal(val1[0], val_h[0])
+    fa.fem_assemble_host(p, [], None, fa.FEM_F_SINPROD, None, None, None)
