@@ -333,9 +333,10 @@ constexpr int kBarrierPolls = 1 << 24;  // bounded grid-barrier wait (with a sho
 constexpr int kItemsPerClaim = 8;       // tiles (or row groups) taken per counter increment
 
 // ctr[0]: next tile, ctr[1]: CTAs past phase 1, ctr[2]: next group of TE rows (taken kItemsPerClaim at a
-// time); zeroed before the launch.
+// time); zeroed before the launch. 2-D: registers capped so that nine 128-thread CTAs are resident per
+// SM, as for the element kernel (no spills); 3-D as the element kernel.
 template <int D, int TE, typename PW>
-__global__ void __launch_bounds__(TE, (D == 3 ? 768 : TE) / TE)
+__global__ void __launch_bounds__(TE, (D == 3 ? 768 : 1152) / TE)
     k_tiles_fused(TileArgs a, RowArgs g, const double* __restrict__ node, const double* __restrict__ k, int f_kind,
                   const double* __restrict__ f_arg, double* __restrict__ val, double* __restrict__ bvec,
                   const float4* __restrict__ tab, int* __restrict__ ctr, int* __restrict__ err) {

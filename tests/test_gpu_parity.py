@@ -474,6 +474,66 @@ def test_full_size_sampled_rows(cfg, variant):
     assert np.array_equal(host(isbd), m["is_bd"])
 
 
+def test_full_size_batch_sampled_meshes():
+    """The 256-mesh batch (n ~ U{16..512}, 48.2 M triangles) in the benchmark's launch form: one launch
+    replayed from a CUDA graph. Sampled meshes (the smallest, the largest and three more) against the
+    oracle, value by value; every mesh's rows sum to zero."""
+    c4 = meshgen.make_config("c4")
+    ms_ = c4["meshes"]
+    elem_cat = np.concatenate([x["elem"] for x in ms_])
+    node_cat = np.concatenate([x["node"] for x in ms_])
+    k_cat = np.concatenate([x["coef"] for x in ms_])
+    bt = fa.Batch(2, [x["node"].shape[0] for x in ms_], [x["elem"].shape[0] for x in ms_], dev(elem_cat))
+    bt.set_locality(dev(node_cat))
+    val = torch.empty(bt.nnz_off[-1], dtype=torch.float64, device="cuda")
+    b = torch.empty(bt.node_off[-1], dtype=torch.float64, device="cuda")
+    nd, kd = dev(node_cat), dev(k_cat)
+    for _ in range(2):
+        bt.assemble(nd, kd, fa.FEM_F_SINPROD, None, val, b, fa.FEM_DETERMINISTIC, graph=True)
+    torch.cuda.synchronize()
+    fa.get_error()
+    v, bb = host(val), host(b)
+    sides = c4["sides"]
+    pick = sorted({int(np.argmin(sides)), int(np.argmax(sides))} |
+                  set(np.random.default_rng(5).choice(len(ms_), 3, replace=False).tolist()))
+    for i in pick:
+        m = ms_[i]
+        rp, col, vo, so = oracle.assemble(2, m["node"], m["elem"], m["coef"])
+        assert np.array_equal(host(bt.pattern.col_idx)[bt.nnz_off[i]:bt.nnz_off[i + 1]] - bt.node_off[i], col)
+        assert_close_scaled(v[bt.nnz_off[i]:bt.nnz_off[i + 1]], vo, so)
+        bo = oracle.rhs(2, m["node"], m["elem"], oracle.F_SINPROD)
+        assert_close_scaled(bb[bt.node_off[i]:bt.node_off[i + 1]], bo, np.abs(bo) + 1e-30, what="rhs")
+    rp = bt.pattern.row_ptr
+    Nt = bt.node_off[-1]
+    rowid = torch.repeat_interleave(torch.arange(Nt, device="cuda"), (rp[1:] - rp[:-1]).long())
+    rs = torch.zeros(Nt, dtype=torch.float64, device="cuda").index_add_(0, rowid, val)
+    ra = torch.zeros(Nt, dtype=torch.float64, device="cuda").index_add_(0, rowid, val.abs())
+    assert bool((rs.abs() <= 1e-12 * ra).all())
+
+
+def test_full_size_backward_matches_oracle_adjoint():
+    """The 64^3 Kuhn mesh (1.57 M tetrahedra), L = w.A + r.b with the benchmark's seeded weights and the
+    sine-product load: the GPU backward (tile order, as the benchmark runs it) against the oracle's
+    adjoint over the whole mesh, every node and element gradient."""
+    m = meshgen.make_config("c5")
+    node, elem, k = m["node"], m["elem"], m["coef"]
+    N, NT = node.shape[0], elem.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    fa.fem_pattern_set_locality(p, dev(node))
+    rp, col = host(p.row_ptr).astype(np.int64), host(p.col_idx).astype(np.int64)
+    slot = oracle.slots(3, N, elem, rp, col)
+    w = meshgen.normal(m["loss_seed"], meshgen.TAG_W, p.nnz)
+    r = meshgen.normal(m["loss_seed"], meshgen.TAG_R, N)
+    gn = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+    gk = torch.empty(NT, dtype=torch.float64, device="cuda")
+    val, b = fa.assemble(p, dev(node), dev(k), fa.FEM_F_SINPROD)
+    fa.fem_assemble_backward(p, dev(node), dev(k), fa.FEM_F_SINPROD, None, dev(w), dev(r), gn, gk)
+    fa.get_error()
+    gno, gko = oracle.backward(3, node, elem, k, oracle.F_SINPROD, None, slot, w, r)
+    assert np.all(np.abs(host(gn) - gno) <= 1e-10 * (np.abs(gno) + np.abs(gno).max()))
+    assert np.all(np.abs(host(gk) - gko) <= 1e-10 * (np.abs(gko) + np.abs(gko).max()))
+
+
 # ---- Neumann / Robin sides and the pure-Neumann fixes ------------------------------------------------
 
 @pytest.mark.parametrize("d", [2, 3])
