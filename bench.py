@@ -465,6 +465,9 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "strong" if (args.shard == "rows" and ws > 1) else "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "arithmetic": ("float-float on the FP32 pipe (pairs of floats, ~2^-48 relative); every FP64 output "
+                          "rounded once; within 1e-12 of the FP64 oracle" if args.variant == "deterministic"
+                          else "FP64 (atomicAdd in FP64)"),
            "config": {"workload": workload_name(args.config), "N": N, "NT": NT, "nnz": p.nnz,
                       "variant": args.variant, "l2": "flushed by a 512 MB write between steps (outside timing)",
                       "parallelism": ("single GPU" if ws == 1 else

@@ -16,6 +16,9 @@
  *  - Errors found by kernels (a degenerate element, an index out of range) are recorded in a
  *    device error word; they surface at the next fem_get_error() call.
  *  - Double arrays must be 8-byte aligned and int32 arrays 4-byte aligned (FEM_ERR_ARG otherwise).
+ *  - A pattern owns per-call device scratch (packets, work counters, host-step buffers): calls on
+ *    one pattern must be ordered (one host thread, one stream, or streams ordered by events).
+ *    Different patterns are independent.
  */
 #ifndef FEMASM_H
 #define FEMASM_H

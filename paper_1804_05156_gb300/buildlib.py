@@ -4,6 +4,7 @@ from __future__ import annotations
 import concurrent.futures as cf
 import glob
 import hashlib
+import re
 import os
 import subprocess
 import sys
@@ -48,17 +49,24 @@ def source_digest() -> str:
     return h.hexdigest()
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source with comments removed and whitespace runs collapsed."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def tu_digest(cu: str) -> str:
-    """sha256 over one kernel source file (by name, in csrc/), every csrc header and the ABI header: the
-    code a kernel of that file is compiled from. A profile record keyed by it stays valid while only
-    other translation units change."""
+    """sha256 over the code (comments and layout ignored) of one kernel source file (by name, in csrc/),
+    every csrc header and the ABI header: what a kernel of that file is compiled from. A profile record
+    keyed by it stays valid while only other translation units, or comments, change."""
     h = hashlib.sha256()
     files = [os.path.join(CSRC, os.path.basename(cu))] + sorted(glob.glob(os.path.join(CSRC, "*.cuh")))
     files.append(os.path.join(ROOT, "include", "femasm.h"))
     for f in files:
         h.update(os.path.basename(f).encode() + b"\0")
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
         h.update(b"\0")
     return h.hexdigest()
 
