@@ -85,49 +85,74 @@ __device__ __forceinline__ bool element_adjoint(const VtxDF<D>* const (&V)[D + 1
     for (int c = 0; c < D; ++c) out[i][c] = df2{0.0f, 0.0f};
   gkv = df2{0.0f, 0.0f};
   if (with_w) {
+    // h_j = sum_i Ws_ij g_i, each component one fused float-float dot product
     df2 h[D1][D];
 #pragma unroll
     for (int j = 0; j < D1; ++j)
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        df2 a = df_mul(Ws[0][j], g[0][c]);
+        df2 A[D1], B[D1];
 #pragma unroll
-        for (int i = 1; i < D1; ++i) a = df_add(a, df_mul(Ws[i][j], g[i][c]));
-        h[j][c] = a;
+        for (int i = 0; i < D1; ++i) {
+          A[i] = Ws[i][j];
+          B[i] = g[i][c];
+        }
+        h[j][c] = df_dot<D1>(A, B);
       }
-    df2 S2 = df_dot<D>(h[0], g[0]);
+    df2 S2;  // sum_j h_j . g_j
+    {
+      df2 A[D1 * D], B[D1 * D];
 #pragma unroll
-    for (int j = 1; j < D1; ++j) S2 = df_add(S2, df_dot<D>(h[j], g[j]));
+      for (int j = 0; j < D1; ++j)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          A[j * D + c] = h[j][c];
+          B[j * D + c] = g[j][c];
+        }
+      S2 = df_dot<D1 * D>(A, B);
+    }
     const df2 S = df_scale(S2, 0.5f);
     gkv = df_mul(meas, S);
     const df2 km = df_mul(kt, meas);
+    df2 P[D1][D1];  // g_j . g_m (symmetric)
 #pragma unroll
-    for (int m = 0; m < D1; ++m) {
-      df2 acc[D];
+    for (int j = 0; j < D1; ++j)
 #pragma unroll
-      for (int c = 0; c < D; ++c) acc[c] = df_mul(S, g[m][c]);
-#pragma unroll
-      for (int j = 0; j < D1; ++j) {
-        const df2 pjm = df_dot<D>(g[j], g[m]);
-#pragma unroll
-        for (int c = 0; c < D; ++c) acc[c] = df_sub(acc[c], df_mul(pjm, h[j][c]));
+      for (int m = j; m < D1; ++m) {
+        P[j][m] = df_dot<D>(g[j], g[m]);
+        P[m][j] = P[j][m];
       }
 #pragma unroll
-      for (int c = 0; c < D; ++c) out[m][c] = df_mul(km, acc[c]);
-    }
+    for (int m = 0; m < D1; ++m)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        // S g_m - sum_j P_jm h_j
+        df2 A[D1 + 1], B[D1 + 1];
+        A[0] = S;
+        B[0] = g[m][c];
+#pragma unroll
+        for (int j = 0; j < D1; ++j) {
+          A[j + 1] = df_neg(P[j][m]);
+          B[j + 1] = h[j][c];
+        }
+        out[m][c] = df_mul(km, df_dot<D1 + 1>(A, B));
+      }
   }
   if (with_r) {
-    // quadrature points: f, grad f and barycentric weights lambda_i(q)
+    // quadrature points: f, grad f; barycentric weights lambda_q(q) = lo + ld, lambda_i(q) = lo (i != q)
+    // and the point weight wqd, as float-float constants (2-D: edge midpoints, 1/2 and 0, weight 1/3;
+    // 3-D: (a, b, b, b) with a = (5 + 3 sqrt5)/20, b = (5 - sqrt5)/20, weight 1/4)
     df2 fq[D1], gf[D1][D];
-    float lam_self, lam_other, wq;
+    df2 lo, ld, wqd;
     if constexpr (D == 2) {
-      lam_self = 0.0f;
-      lam_other = 0.5f;
-      wq = 1.0f / 3.0f;
+      lo = df2{0.5f, 0.0f};
+      ld = df2{-0.5f, 0.0f};
+      wqd = df2{0.3333333432674408f, -9.9341077586e-09f};
     } else {
-      lam_self = 0.5854101777f;
-      lam_other = 0.1381966025f;
-      wq = 0.25f;
+      const df2 al = {0.58541017770767212f, 1.8917296174e-08f}, be = {0.13819660246372223f, -1.3387116971e-09f};
+      lo = be;
+      ld = df_sub(al, be);
+      wqd = df2{0.25f, 0.0f};
     }
 #pragma unroll
     for (int q = 0; q < D1; ++q)
@@ -193,29 +218,36 @@ __device__ __forceinline__ bool element_adjoint(const VtxDF<D>* const (&V)[D + 1
 #pragma unroll
       for (int q = 0; q < D1; ++q) fq[q] = c0;
     }
-    // rl_q = sum_i r_i lambda_i(q) = lam_other * sum_i r_i + (lam_self - lam_other) r_q
+    // rl_q = sum_i r_i lambda_i(q) = lo sum_i r_i + ld r_q;  Rb = sum_q w_q f_q rl_q
     df2 rs = rv[0];
 #pragma unroll
     for (int i = 1; i < D1; ++i) rs = df_add(rs, rv[i]);
     df2 rl[D1];
-    df2 Rb = df2{0.0f, 0.0f};
 #pragma unroll
-    for (int q = 0; q < D1; ++q) {
-      rl[q] = df_add(df_mul_f(rs, lam_other), df_mul_f(rv[q], lam_self - lam_other));
-      Rb = df_add(Rb, df_mul(fq[q], rl[q]));
+    for (int q = 0; q < D1; ++q) rl[q] = df_add(df_mul(rs, lo), df_mul(rv[q], ld));
+    const df2 Rb = df_mul(wqd, df_dot<D1>(fq, rl));
+    // sum_q w_q lambda_m(q) grad f(x_q) rl_q = w_q (lo sum_q gr_q + ld gr_m), gr_q = grad f(x_q) rl_q
+    df2 gr[D1][D], gs[D];
+    if (f_kind == FEM_F_SINPROD) {
+#pragma unroll
+      for (int q = 0; q < D1; ++q)
+#pragma unroll
+        for (int c = 0; c < D; ++c) gr[q][c] = df_mul(gf[q][c], rl[q]);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        df2 a = gr[0][c];
+#pragma unroll
+        for (int q = 1; q < D1; ++q) a = df_add(a, gr[q][c]);
+        gs[c] = a;
+      }
     }
-    Rb = df_mul_f(Rb, wq);
 #pragma unroll
     for (int m = 0; m < D1; ++m)
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        df2 s2 = df2{0.0f, 0.0f};
-        if (f_kind == FEM_F_SINPROD) {
-#pragma unroll
-          for (int q = 0; q < D1; ++q)
-            s2 = df_add(s2, df_mul_f(df_mul(gf[q][c], rl[q]), wq * (q == m ? lam_self : lam_other)));
-        }
-        out[m][c] = df_add(out[m][c], df_mul(meas, df_add(df_mul(g[m][c], Rb), s2)));
+        df2 v = df_mul(g[m][c], Rb);
+        if (f_kind == FEM_F_SINPROD) v = df_add(v, df_mul(wqd, df_add(df_mul(gs[c], lo), df_mul(gr[m][c], ld))));
+        out[m][c] = df_add(out[m][c], df_mul(meas, v));
       }
   }
   return ok;

@@ -293,6 +293,31 @@ def test_backward_matches_oracle_adjoint(case, f_kind):
         fa.fem_pattern_force_path(p, fa.FEM_PATH_TWO_PASS)
 
 
+@pytest.mark.parametrize("part", ["w", "r"])
+@pytest.mark.parametrize("f_kind", [fa.FEM_F_CONST, fa.FEM_F_SINPROD])
+@pytest.mark.parametrize("case", ["sq37p", "kuhn5", "delaunay3"])
+def test_backward_one_loss_part_matches_oracle_adjoint(case, f_kind, part):
+    """L = w.A alone, or L = r.b alone: each part of the adjoint on its own scale (the load part is far
+    smaller than the stiffness part when both are present, so this is where the quadrature weights of
+    the load term show their precision)."""
+    d, node, elem, k, _ = mesh_case(case)
+    N, NT = node.shape[0], elem.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    fa.fem_pattern_set_locality(p, dev(node))
+    rp, col = host(p.row_ptr).astype(np.int64), host(p.col_idx).astype(np.int64)
+    slot = oracle.slots(d, N, elem, rp, col)
+    w = meshgen.normal(1808, meshgen.TAG_W, p.nnz) if part == "w" else None
+    r = meshgen.normal(1808, meshgen.TAG_R, N) if part == "r" else None
+    gno, gko = oracle.backward(d, node, elem, k, f_kind, None, slot, w, r)
+    gn = torch.empty((N, d), dtype=torch.float64, device="cuda")
+    gk = torch.empty(NT, dtype=torch.float64, device="cuda")
+    fa.fem_assemble_backward(p, dev(node), dev(k), f_kind, None, None if w is None else dev(w),
+                             None if r is None else dev(r), gn, gk)
+    fa.get_error()
+    assert np.all(np.abs(host(gn) - gno) <= 1e-10 * (np.abs(gno) + np.abs(gno).max()))
+    assert np.all(np.abs(host(gk) - gko) <= 1e-10 * (np.abs(gko) + np.abs(gko).max()))
+
+
 def test_backward_central_fd_on_gpu():
     """Gradients of L = w.A + r.b from the GPU backward vs central differences of the GPU forward."""
     m = meshgen.kuhn_mesh(3, 0.1, 21)
