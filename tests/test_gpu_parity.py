@@ -87,6 +87,26 @@ def test_locality_plan_values_match_oracle(case):
     assert torch.equal(v3, val) and torch.equal(b3, b)
 
 
+@pytest.mark.parametrize("case", ["sq37p", "kuhn7s", "delaunay3"])
+def test_far_from_the_origin(case):
+    """The same meshes moved far from the origin (coordinates ~1e4): edge vectors stay exact (the
+    three-float split), so the stiffness values and the constant-f load still match the oracle within
+    1e-12 of their scale (the oracle's FP64 differences of nearby coordinates are exact too). The
+    sine-product load is left out here: the oracle rounds each midpoint (x_i + x_j)/2 to ~1e-12 in
+    absolute terms at this magnitude, which the float-float path does not."""
+    d, node, elem, k, _ = mesh_case(case)
+    shift = np.array([12345.0, -6789.0, 31415.0][:d])
+    far = node + shift
+    p = fa.Pattern(dev(elem), far.shape[0])
+    fa.fem_pattern_set_locality(p, dev(far))
+    v, b = fa.assemble(p, dev(far), dev(k), fa.FEM_F_CONST, dev(np.array([2.5])))
+    fa.get_error()
+    _, _, vo, so = oracle.assemble(d, far, elem, k)
+    assert_close_scaled(host(v), vo, so)
+    bo = oracle.rhs(d, far, elem, oracle.F_CONST, np.array([2.5]))
+    assert_close_scaled(host(b), bo, np.abs(bo) + 1e-300, what="rhs")
+
+
 @pytest.mark.parametrize("case", ["sq37p", "kuhn5", "delaunay2"])
 def test_every_launch_shape_gives_the_same_bits(case):
     """Deterministic means independent of the launch: all shapes, one CTA per block or persistent."""
@@ -294,7 +314,7 @@ def test_backward_matches_oracle_adjoint(case, f_kind):
 
 
 @pytest.mark.parametrize("part", ["w", "r"])
-@pytest.mark.parametrize("f_kind", [fa.FEM_F_CONST, fa.FEM_F_SINPROD])
+@pytest.mark.parametrize("f_kind", [fa.FEM_F_CONST, fa.FEM_F_SINPROD, fa.FEM_F_QPVALUES])
 @pytest.mark.parametrize("case", ["sq37p", "kuhn5", "delaunay3"])
 def test_backward_one_loss_part_matches_oracle_adjoint(case, f_kind, part):
     """L = w.A alone, or L = r.b alone: each part of the adjoint on its own scale (the load part is far
@@ -308,11 +328,12 @@ def test_backward_one_loss_part_matches_oracle_adjoint(case, f_kind, part):
     slot = oracle.slots(d, N, elem, rp, col)
     w = meshgen.normal(1808, meshgen.TAG_W, p.nnz) if part == "w" else None
     r = meshgen.normal(1808, meshgen.TAG_R, N) if part == "r" else None
-    gno, gko = oracle.backward(d, node, elem, k, f_kind, None, slot, w, r)
+    farg = meshgen.normal(7, 9, NT * (d + 1)) if f_kind == fa.FEM_F_QPVALUES else None
+    gno, gko = oracle.backward(d, node, elem, k, f_kind, farg, slot, w, r)
     gn = torch.empty((N, d), dtype=torch.float64, device="cuda")
     gk = torch.empty(NT, dtype=torch.float64, device="cuda")
-    fa.fem_assemble_backward(p, dev(node), dev(k), f_kind, None, None if w is None else dev(w),
-                             None if r is None else dev(r), gn, gk)
+    fa.fem_assemble_backward(p, dev(node), dev(k), f_kind, None if farg is None else dev(farg),
+                             None if w is None else dev(w), None if r is None else dev(r), gn, gk)
     fa.get_error()
     assert np.all(np.abs(host(gn) - gno) <= 1e-10 * (np.abs(gno) + np.abs(gno).max()))
     assert np.all(np.abs(host(gk) - gko) <= 1e-10 * (np.abs(gko) + np.abs(gko).max()))
