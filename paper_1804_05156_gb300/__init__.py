@@ -394,6 +394,29 @@ def assemble(p: Pattern, node, k=None, f_kind=FEM_F_CONST, f_arg=None, variant=F
     return val, b
 
 
+def assemble_system(node, elem, k=None, f_kind=FEM_F_CONST, f_arg=None, dirichlet=None, gD=None,
+                    variant=FEM_DETERMINISTIC, pattern=None, sparse=False):
+    """The P1 system of the Poisson problem in one call (CUDA tensors in and out): builds the pattern of
+    ``elem`` [NT, d+1] (or reuses ``pattern``) with locality plans from ``node`` [N, d], assembles the
+    stiffness matrix and the load vector, and with ``dirichlet`` eliminates the Dirichlet rows:
+    True for the whole boundary, or an int8 tensor [NT, d+1] whose 1 entries mark Dirichlet sides; gD
+    [N] gives the boundary values (None: 0). Returns (row_ptr, col_idx, val, b), or (A, b) with A a
+    torch.sparse_csr_tensor when ``sparse``."""
+    if pattern is None:
+        pattern = Pattern(elem.to(torch.int32).contiguous(), node.shape[0])
+        fem_pattern_set_locality(pattern, node)
+    val, b = assemble(pattern, node, k, f_kind, f_arg, variant)
+    if dirichlet is not None and dirichlet is not False:
+        is_bd = torch.empty(pattern.N, dtype=torch.uint8, device=node.device)
+        fem_boundary_nodes(pattern, None if dirichlet is True else dirichlet, is_bd)
+        fem_apply_dirichlet(pattern, is_bd, gD, val, b, want_count=False)
+    if sparse:
+        A = torch.sparse_csr_tensor(pattern.row_ptr.long(), pattern.col_idx.long(), val,
+                                    size=(pattern.N, pattern.N))
+        return A, b
+    return pattern.row_ptr, pattern.col_idx, val, b
+
+
 class FemAssemble(torch.autograd.Function):
     """(node [N, d], k [NT]) -> (val [nnz], b [N]); backward recomputes the basis gradients."""
 

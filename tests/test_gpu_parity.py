@@ -782,3 +782,30 @@ def test_host_steps_match_device_assembly(case):
     fa.fem_assemble_host(p, node_h[:1], k_h[:1], fa.FEM_F_SINPROD, None, val1, None)
     assert torch.equal(val1[0], val_h[0])
     fa.fem_assemble_host(p, [], None, fa.FEM_F_SINPROD, None, None, None)
+
+
+@pytest.mark.parametrize("case", ["sq37p", "kuhn5"])
+def test_assemble_system_one_call(case):
+    """assemble_system: pattern, values, load and Dirichlet elimination in one call; the same bits as the
+    calls it is made of, and the eliminated system of the oracle (bit-exact rows, values within 1e-12)."""
+    d, node, elem, k, _ = mesh_case(case)
+    N = node.shape[0]
+    gD = np.cos(3 * node[:, 0]) + node[:, 1]
+    rp, col, val, b = fa.assemble_system(dev(node), dev(elem), dev(k), fa.FEM_F_SINPROD, None,
+                                         dirichlet=True, gD=dev(gD))
+    fa.get_error()
+    p = fa.Pattern(dev(elem), N)
+    fa.fem_pattern_set_locality(p, dev(node))
+    v2, b2 = fa.assemble(p, dev(node), dev(k), fa.FEM_F_SINPROD)
+    isbd = torch.empty(N, dtype=torch.uint8, device="cuda")
+    fa.fem_boundary_nodes(p, None, isbd)
+    fa.fem_apply_dirichlet(p, isbd, dev(gD), v2, b2, want_count=False)
+    assert torch.equal(rp, p.row_ptr) and torch.equal(col, p.col_idx)
+    assert torch.equal(val, v2) and torch.equal(b, b2)
+    rpo, colo, vo, so = oracle.assemble(d, node, elem, k)
+    bo = oracle.rhs(d, node, elem, oracle.F_SINPROD)
+    vo2, bo2, _ = oracle.dirichlet(rpo, colo, vo, bo, oracle.boundary(d, N, elem), gD)
+    assert np.array_equal(host(rp), rpo) and np.array_equal(host(col), colo)
+    assert_close_scaled(host(val), vo2, so + (vo2 == 1.0))
+    A, bb = fa.assemble_system(dev(node), dev(elem), dev(k), fa.FEM_F_SINPROD, None, sparse=True)
+    assert A.layout == torch.sparse_csr and torch.equal(A.values(), fa.assemble(p, dev(node), dev(k), fa.FEM_F_SINPROD)[0])
