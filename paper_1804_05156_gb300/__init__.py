@@ -411,8 +411,11 @@ def assemble_system(node, elem, k=None, f_kind=FEM_F_CONST, f_arg=None, dirichle
         fem_boundary_nodes(pattern, None if dirichlet is True else dirichlet, is_bd)
         fem_apply_dirichlet(pattern, is_bd, gD, val, b, want_count=False)
     if sparse:
-        A = torch.sparse_csr_tensor(pattern.row_ptr.long(), pattern.col_idx.long(), val,
-                                    size=(pattern.N, pattern.N))
+        import warnings
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore")  # torch marks its CSR layout as beta
+            A = torch.sparse_csr_tensor(pattern.row_ptr.long(), pattern.col_idx.long(), val,
+                                        size=(pattern.N, pattern.N))
         return A, b
     return pattern.row_ptr, pattern.col_idx, val, b
 

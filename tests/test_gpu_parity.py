@@ -205,6 +205,39 @@ def test_long_rows_take_the_tile_path():
     assert e.value.code == fa.FEM_ERR_STATE
 
 
+def test_rows_beyond_every_plan_take_the_two_pass_path():
+    """A vertex with 300 neighbours (row of 301 entries) is beyond both locality plans: assembly and the
+    backward run on the FP64 two-pass and caller-order paths and still match the oracle; the calls that
+    need the tile plan (other operators, y = A u) refuse with FEM_ERR_STATE instead of running."""
+    node, elem = _fan(300, 6)
+    N, NT = node.shape[0], elem.shape[0]
+    k = meshgen.lognormal(6, 3, NT)
+    p = fa.Pattern(dev(elem), N)
+    fa.fem_pattern_set_locality(p, dev(node))
+    assert fa.fem_pattern_value_path(p)["path"] == "two_pass"
+    for variant in VARIANTS:
+        v, b = fa.assemble(p, dev(node), dev(k), fa.FEM_F_SINPROD, None, variant)
+        fa.get_error()
+        rp, col, vo, so = oracle.assemble(2, node, elem, k)
+        assert_close_scaled(host(v), vo, so)
+        bo = oracle.rhs(2, node, elem, oracle.F_SINPROD)
+        assert_close_scaled(host(b), bo, np.abs(bo) + 1e-300, what="rhs")
+    slot = oracle.slots(2, N, elem, rp.astype(np.int64), col.astype(np.int64))
+    w, r = meshgen.normal(3, meshgen.TAG_W, p.nnz), meshgen.normal(3, meshgen.TAG_R, N)
+    gn = torch.empty((N, 2), dtype=torch.float64, device="cuda")
+    gk = torch.empty(NT, dtype=torch.float64, device="cuda")
+    fa.fem_assemble_backward(p, dev(node), dev(k), fa.FEM_F_SINPROD, None, dev(w), dev(r), gn, gk)
+    fa.get_error()
+    gno, gko = oracle.backward(2, node, elem, k, oracle.F_SINPROD, None, slot, w, r)
+    assert np.all(np.abs(host(gn) - gno) <= 1e-10 * (np.abs(gno) + np.abs(gno).max()))
+    assert np.all(np.abs(host(gk) - gko) <= 1e-10 * (np.abs(gko) + np.abs(gko).max()))
+    for call in (lambda: fa.fem_assemble_operator(p, dev(node), fa.FEM_OP_MASS, None),
+                 lambda: fa.fem_apply_stiffness(p, dev(node), dev(k), dev(np.ones(N)))):
+        with pytest.raises(fa.FemError) as e:
+            call()
+        assert e.value.code == fa.FEM_ERR_STATE
+
+
 def test_qp_values_rhs():
     d, node, elem, k, _ = mesh_case("sq37p")
     rng = np.random.default_rng(5)
