@@ -146,28 +146,38 @@ def profiled(kernels, config, path, shape, kind="traffic", field="bytes_per_laun
     return None, "no ncu capture of these kernels on this plan and source digest under profiles/"
 
 
+def patch_sample(node, elem, k, m):
+    """A bounded sample of the mesh for the oracle: the m elements of lowest largest vertex id (a connected
+    patch, whatever the element order), in ascending element order, over their own vertices renumbered
+    (so the per-vertex share of the oracle's work is the whole mesh's). Returns (node, elem, k, vertices)."""
+    pick = np.sort(np.argsort(elem.max(axis=1), kind="stable")[:m])
+    used, sub = np.unique(elem[pick], return_inverse=True)
+    return (np.ascontiguousarray(node[used]), sub.reshape(m, -1).astype(np.int32),
+            None if k is None else k[pick], len(used))
+
+
 def cpu_baseline(mesh, f_kind, target_s=12.0):
-    """The oracle as it stands on a bounded sample (the first M elements of the same mesh), one core."""
+    """The oracle as it stands on a bounded sample (a patch of M elements of the same mesh), one core."""
     import oracle
     oracle.build()
     d, node, elem, k = mesh["d"], mesh["node"], mesh["elem"], mesh["coef"]
     NT = elem.shape[0]
 
     def run(m):
-        e, kk = elem[:m], (None if k is None else k[:m])
+        n_s, e_s, k_s, nv = patch_sample(node, elem, k, m)
         t0 = time.perf_counter()
-        oracle.assemble(d, node, e, kk)
-        oracle.rhs(d, node, e, f_kind)
-        return time.perf_counter() - t0
+        oracle.assemble(d, n_s, e_s, k_s)
+        oracle.rhs(d, n_s, e_s, f_kind)
+        return time.perf_counter() - t0, nv
 
     m = min(NT, 100_000)
-    dt = run(m)
+    dt, nv = run(m)
     m2 = int(min(NT, max(m, m * target_s / max(dt, 1e-3))))
     if m2 > m:
-        m, dt = m2, run(m2)
+        m, (dt, nv) = m2, run(m2)
     return {"value": m / dt / 1e6, "unit": "Melem/s", "cores": 1, "kind": "oracle",
-            "sample": "first %d of %d elements of the same mesh (stiffness triples + sparse summation + "
-                      "load vector), single-threaded C, %.1f s" % (m, NT, dt)}
+            "sample": "a patch of %d of the %d elements of the same mesh, over its %d vertices (stiffness "
+                      "triples + sparse summation + load vector), single-threaded C, %.1f s" % (m, NT, nv, dt)}
 
 
 def dist_init(args):
@@ -199,14 +209,7 @@ def run_reference(args):
     d, node, elem, k = mesh["d"], mesh["node"], mesh["elem"], mesh["coef"]
     oracle.build()
     m = min(elem.shape[0], args.ref_sample)
-    # the sample: the m elements of lowest largest vertex id (a connected patch of the mesh, whatever the
-    # element order), over their own vertices renumbered, so that the oracle's per-vertex work keeps the
-    # proportion it has on the whole mesh
-    pick = np.sort(np.argsort(elem.max(axis=1), kind="stable")[:m])
-    used, sub = np.unique(elem[pick], return_inverse=True)
-    e_s = sub.reshape(m, -1).astype(np.int32)
-    n_s = np.ascontiguousarray(node[used])
-    k_s = None if k is None else k[pick]
+    n_s, e_s, k_s, nv = patch_sample(node, elem, k, m)
     times = []
     for it in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -222,7 +225,7 @@ def run_reference(args):
             "config": {"workload": workload_name(args.config), "sample_elements": m},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "Melem/s",
                              "sample": "a patch of %d elements of the mesh (over its %d vertices) per step, "
-                                       "single-threaded C oracle" % (m, len(used))},
+                                       "single-threaded C oracle" % (m, nv)},
             "e2e": {"value": v, "unit": "Melem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
