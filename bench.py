@@ -421,7 +421,12 @@ def run_ours(args):
     traffic, traffic_src = profiled(names, args.config, path, shape)
     inst, inst_src = profiled(names, args.config, path, shape, "inst", "warp_inst_per_launch")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "traffic_source": traffic_src, "kernel": " + ".join(names), "kernel_ms": k_ms,
+            "traffic": traffic, "traffic_source": traffic_src,
+            # the DRAM bytes ncu counted for these kernels over their time here: the rate the memory system
+            # ran at, including the design's own traffic (packets, plan arrays), not an efficiency
+            "dram_GBs": (traffic / (k_ms * 1e-3) / 1e9) if traffic else None,
+            "dram_frac": (traffic / (k_ms * 1e-3) / 1e9 / peak) if traffic else None,
+            "kernel": " + ".join(names), "kernel_ms": k_ms,
             "peak_source": peak_kind, "algorithmic_bytes": alg, "step_algorithmic_GBs": alg / (ms * 1e-3) / 1e9,
             "kernels": {n: {"launches": c, "mean_ms": t / c, "share": (t / c) / k_ms} for n, (c, t) in kt.items()}}
     # what does bind the step: instruction issue (the float-float arithmetic runs on the FP32/INT32 pipes).
