@@ -61,6 +61,21 @@ struct RowArgs {
   bool diag_in_packet;  // the packet's last pair is the diagonal entry (mass matrix), not a load term
 };
 
+// Staged 2-D records padded to 48 bytes (three 16-byte bank groups): a warp's scattered reads of the
+// records of different vertices then fall on all eight 16-byte groups of banks instead of four.
+struct __align__(16) VtxPad2 {
+  VtxDF<2> v;
+  float pad[4];
+};
+struct __align__(16) SCPad2 {
+  SC sc[2];
+  float pad[4];
+};
+template <int D>
+__host__ __device__ constexpr int staged_vtx_bytes() { return D == 2 ? (int)sizeof(VtxPad2) : (int)sizeof(VtxDF<3>); }
+template <int D>
+__host__ __device__ constexpr int staged_sc_bytes() { return D == 2 ? (int)sizeof(SCPad2) : 0; }
+
 // Phase 1 for one tile (all TE threads of the CTA; one __syncthreads inside).
 template <int D, int TE>
 __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, unsigned char* sm,
@@ -68,8 +83,7 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
                                                  int f_kind, const double* __restrict__ f_arg, int want_a, int want_b,
                                                  const float4* __restrict__ tab, int* __restrict__ err) {
   constexpr int D1 = D + 1;
-  VtxDF<D>* xs = reinterpret_cast<VtxDF<D>*>(sm);
-  SC* scs = reinterpret_cast<SC*>(sm + a.xs_bytes);
+  VtxDF<D>* xs = reinterpret_cast<VtxDF<D>*>(sm);  // 3-D; 2-D stages VtxPad2 / SCPad2 records
   const int v0 = __ldg(a.voff + tile), nv = __ldg(a.voff + tile + 1) - v0;
   const bool sinprod2 = (D == 2) && f_kind == FEM_F_SINPROD && want_b;
   // element data first: its loads are in flight during the vertex staging
@@ -92,10 +106,15 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
     VtxDF<D> x;
 #pragma unroll
     for (int m = 0; m < D; ++m) x.x[m] = split3(__ldg(node + (size_t)R * D + m));
-    xs[v] = x;
-    if (sinprod2) {
+    if constexpr (D == 2) {
+      reinterpret_cast<VtxPad2*>(sm)[v].v = x;
+      if (sinprod2) {
+        SCPad2* scp = reinterpret_cast<SCPad2*>(sm + a.xs_bytes);
 #pragma unroll
-      for (int m = 0; m < D; ++m) scs[v * D + m] = sincospi_half(x.x[m], tab);
+        for (int m = 0; m < 2; ++m) scp[v].sc[m] = sincospi_half(x.x[m], tab);
+      }
+    } else {
+      xs[v] = x;
     }
     if (a.op == kOpApply)  // eliminated vertices contribute nothing to the free rows
       reinterpret_cast<df2*>(sm + a.u_off)[v] =
@@ -111,10 +130,13 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
 #pragma unroll
   for (int i = 0; i < D1; ++i) L.bt[i] = df2{0.0f, 0.0f};
   bool ok;
-  if (a.op == kOpMass || a.op == kOpAniso) {
-    const VtxDF<D>* V[D1];
+  const VtxDF<D>* V[D1];
 #pragma unroll
-    for (int i = 0; i < D1; ++i) V[i] = &xs[lv[i]];
+  for (int i = 0; i < D1; ++i) {
+    if constexpr (D == 2) V[i] = &reinterpret_cast<const VtxPad2*>(sm)[lv[i]].v;
+    else V[i] = &xs[lv[i]];
+  }
+  if (a.op == kOpMass || a.op == kOpAniso) {
     const double* c = (a.op == kOpMass) ? (a.opk ? a.opk + t : nullptr) : a.opk + (size_t)t * (D * D1 / 2);
     ok = element_df_operator<D>(reinterpret_cast<const VtxDF<D>* const(&)[D1]>(V), a.op, c, L);
     if (a.op == kOpMass) {
@@ -122,12 +144,13 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
       for (int i = 0; i < D1; ++i) L.bt[i] = L.a[i];  // the diagonal travels in the load slot
     }
   } else if constexpr (D == 2) {
-    const VtxDF<2>* const V[3] = {&xs[lv[0]], &xs[lv[1]], &xs[lv[2]]};
-    const SC* const S[3] = {&scs[lv[0] * 2], &scs[lv[1] * 2], &scs[lv[2] * 2]};
-    ok = element_df2(V, S, kt, want_a, want_b, f_kind, fconst, f_arg, t, L, false);  // diagonals: in the gather
+    const SCPad2* scp = reinterpret_cast<const SCPad2*>(sm + a.xs_bytes);
+    const VtxDF<2>* const V2[3] = {V[0], V[1], V[2]};
+    const SC* const S[3] = {scp[lv[0]].sc, scp[lv[1]].sc, scp[lv[2]].sc};
+    ok = element_df2(V2, S, kt, want_a, want_b, f_kind, fconst, f_arg, t, L, false);  // diagonals: in the gather
   } else {
-    const VtxDF<3>* const V[4] = {&xs[lv[0]], &xs[lv[1]], &xs[lv[2]], &xs[lv[3]]};
-    ok = element_df3(V, kt, want_a, want_b, f_kind, fconst, f_arg, t, tab, L, false);  // diagonals: in the gather
+    const VtxDF<3>* const V3[4] = {V[0], V[1], V[2], V[3]};
+    ok = element_df3(V3, kt, want_a, want_b, f_kind, fconst, f_arg, t, tab, L, false);  // diagonals: in the gather
   }
   if (!ok) report(err, FEM_ERR_DEGENERATE);
   if (a.op == kOpApply) {
@@ -284,10 +307,10 @@ __device__ __forceinline__ void rows_of_warp(const RowArgs& g, int64_t R0, df2* 
   __syncwarp();
 }
 
-// 3-D: registers capped so that 768 threads (six 128-thread tiles) fit an SM; a few spilled bytes cost
-// less than the lost occupancy.
+// Registers capped so that 1152 threads (nine 128-thread tiles, 2-D; no spills) or 768 threads (six, 3-D;
+// a few spilled bytes cost less than the lost occupancy) fit an SM.
 template <int D, int TE>
-__global__ void __launch_bounds__(TE, (D == 3 ? 768 : TE) / TE)
+__global__ void __launch_bounds__(TE, (D == 3 ? 768 : 1152) / TE)
     k_tile_elements(TileArgs a, const double* __restrict__ node, const double* __restrict__ k, int f_kind,
                     const double* __restrict__ f_arg, int want_a, int want_b, const float4* __restrict__ tab,
                     int* __restrict__ err) {
@@ -399,8 +422,8 @@ int gather_warps(int max_row) {
 }  // namespace
 
 int tile_smem_need(const TilePlan& T, int d, bool sinprod) {
-  const int xs = ((T.max_v * vtx_bytes(d)) + 15) / 16 * 16;
-  return xs + ((sinprod && d == 2) ? T.max_v * d * (int)sizeof(SC) : 0);
+  const int xs = ((T.max_v * (d == 2 ? staged_vtx_bytes<2>() : staged_vtx_bytes<3>())) + 15) / 16 * 16;
+  return xs + ((sinprod && d == 2) ? T.max_v * staged_sc_bytes<2>() : 0);
 }
 
 // Shared memory of the fused kernel (staging of phase 1 or row copies of phase 2, whichever is larger);
@@ -434,7 +457,7 @@ int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_
   a.vlist = T.vlist;
   a.ipos = T.ipos;
   a.pk = T.pk;
-  a.xs_bytes = ((T.max_v * vtx_bytes(D)) + 15) / 16 * 16;
+  a.xs_bytes = ((T.max_v * (D == 2 ? staged_vtx_bytes<2>() : staged_vtx_bytes<3>())) + 15) / 16 * 16;
   a.op = op;
   a.opk = opk;
   a.u = u;
