@@ -5,8 +5,9 @@
 //   tile's vertices are staged in shared memory once (exact three-float splits; for the 2-D
 //   sine-product load also sin/cos(pi x/2) per coordinate), then each thread computes one element's
 //   local stiffness and load entries (element_df.cuh: Sec. 3.1.3, eq. (dlambda), Sec. 3.2) and writes,
-//   for each local row i, one packet of float pairs to the slot of incidence (t, i):
-//     2-D: (a_ij, a_ik, b_i), 24 bytes;  3-D: (a_ij, a_ik, a_il, b_i), 32 bytes,
+//   for each local row i, one packet of float pairs to the slot q of incidence (t, i):
+//     2-D: (a_ij, a_ik) 16 bytes at pair array [q] and b_i 8 bytes at load array [q] (24 bytes, both
+//          stores aligned: no divergent paths);  3-D: (a_ij, a_ik, a_il, b_i), 32 bytes,
 //   with j < k < l the other local indices. The diagonal is re-formed from the packet in phase 2 exactly
 //   as the element routine forms it (2-D a_ii = -(a_ij + a_ik), 3-D ((0 - a_ij) - a_ik) - a_il), so it
 //   costs no bytes.
@@ -58,6 +59,7 @@ struct RowArgs {
   const void* pw;
   const uint8_t* rdp;
   const float4* pk;
+  const float2* pkb;    // 2-D: the load (or mass-diagonal) terms, one pair per incidence
   bool diag_in_packet;  // the packet's last pair is the diagonal entry (mass matrix), not a load term
 };
 
@@ -177,15 +179,9 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
     for (int jj = 0; jj < D1; ++jj)
       if (jj != i) o[c++] = L.a[pidx<D>(i, jj)];
     if constexpr (D == 2) {
-      // 24-byte packet (a_ij, a_ik, b_i): one 16-byte and one 8-byte store, aligned by the slot's parity
-      float2* dst = reinterpret_cast<float2*>(a.pk) + 3 * (size_t)qi[i];
-      if ((qi[i] & 1) == 0) {
-        *reinterpret_cast<float4*>(dst) = make_float4(o[0].h, o[0].l, o[1].h, o[1].l);
-        dst[2] = make_float2(L.bt[i].h, L.bt[i].l);
-      } else {
-        dst[0] = make_float2(o[0].h, o[0].l);
-        *reinterpret_cast<float4*>(dst + 1) = make_float4(o[1].h, o[1].l, L.bt[i].h, L.bt[i].l);
-      }
+      // 2-D packet in two arrays: (a_ij, a_ik) 16 bytes at pk[q], b_i 8 bytes at the load array's [q]
+      a.pk[qi[i]] = make_float4(o[0].h, o[0].l, o[1].h, o[1].l);
+      reinterpret_cast<float2*>(a.pk + a.NT * 3)[qi[i]] = make_float2(L.bt[i].h, L.bt[i].l);
     } else {
       float4* dst = a.pk + 2 * (size_t)qi[i];
       dst[0] = make_float4(o[0].h, o[0].l, o[1].h, o[1].l);
@@ -234,25 +230,14 @@ __device__ __forceinline__ float2 load_pair(const float2* p) {
   if constexpr (FRESH) return __ldcg(p);
   else return __ldg(p);
 }
-// packet q as (p0, p1): 2-D three float pairs (24 bytes: a_ij, a_ik, b_i), 3-D four (32 bytes)
+// packet q as (p0, p1): 2-D (a_ij, a_ik) and b_i from their two arrays, 3-D four pairs (32 bytes)
 template <int D, bool FRESH>
-__device__ __forceinline__ void load_packet(const float4* pk, int64_t q, float4& p0, float4& p1) {
+__device__ __forceinline__ void load_packet(const float4* pk, const float2* pkb, int64_t q, float4& p0, float4& p1) {
   if constexpr (D == 2) {
-    const float2* b = reinterpret_cast<const float2*>(pk) + 3 * q;
-    if (FRESH && (q & 1) == 0) {  // through L2: fewer, wider loads where the slot is 16-byte aligned
-      p0 = load_packet_half<FRESH>(reinterpret_cast<const float4*>(b));
-      const float2 z = load_pair<FRESH>(b + 2);
-      p1 = make_float4(z.x, z.y, 0.0f, 0.0f);
-    } else if (FRESH) {
-      const float2 x = load_pair<FRESH>(b);
-      const float4 yz = load_packet_half<FRESH>(reinterpret_cast<const float4*>(b + 1));
-      p0 = make_float4(x.x, x.y, yz.x, yz.y);
-      p1 = make_float4(yz.z, yz.w, 0.0f, 0.0f);
-    } else {
-      const float2 x = load_pair<FRESH>(b), y = load_pair<FRESH>(b + 1), z = load_pair<FRESH>(b + 2);
-      p0 = make_float4(x.x, x.y, y.x, y.y);
-      p1 = make_float4(z.x, z.y, 0.0f, 0.0f);
-    }
+    // (a_ij, a_ik) from the pair array, b_i from the load array: two aligned loads
+    p0 = load_packet_half<FRESH>(pk + q);
+    const float2 z = load_pair<FRESH>(pkb + q);
+    p1 = make_float4(z.x, z.y, 0.0f, 0.0f);
   } else {
     p0 = load_packet_half<FRESH>(pk + 2 * q);
     p1 = load_packet_half<FRESH>(pk + 2 * q + 1);
@@ -287,7 +272,7 @@ __device__ __forceinline__ void rows_of_warp(const RowArgs& g, int64_t R0, df2* 
       uint32_t w[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        load_packet<D, FRESH>(g.pk, q + u, x0[u], x1[u]);
+        load_packet<D, FRESH>(g.pk, g.pkb, q + u, x0[u], x1[u]);
         w[u] = (uint32_t)__ldg(pw + q + u);
       }
 #pragma unroll
@@ -295,7 +280,7 @@ __device__ __forceinline__ void rows_of_warp(const RowArgs& g, int64_t R0, df2* 
     }
     for (; q < q1; ++q) {
       float4 x0, x1;
-      load_packet<D, FRESH>(g.pk, q, x0, x1);
+      load_packet<D, FRESH>(g.pk, g.pkb, q, x0, x1);
       add_packet<D>(x0, x1, (uint32_t)__ldg(pw + q), o, acc, dacc, bacc, want_a, want_b, g.diag_in_packet);
     }
     if (want_a && rl > 0) acc[o + __ldg(g.rdp + R)] = dacc;
@@ -474,6 +459,7 @@ int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_
   g.pw = T.pw;
   g.rdp = T.rdp;
   g.pk = T.pk;
+  g.pkb = reinterpret_cast<const float2*>(T.pk + P->NT * 3);
   g.diag_in_packet = op == kOpMass;
   const int want_a = val != nullptr || op == kOpApply, want_b = b != nullptr;
   if (op == kOpApply) {
