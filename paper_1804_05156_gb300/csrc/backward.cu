@@ -18,6 +18,7 @@
 
 #include "common.cuh"
 #include "element_df.cuh"
+#include "packet.cuh"
 
 namespace fem {
 
@@ -362,8 +363,9 @@ __global__ void __launch_bounds__(TE, 512 / TE) k_backward_tiles(
 #pragma unroll
   for (int m = 0; m < D1; ++m) {
     float4* dst = pk + 2 * (size_t)qi[m];
-    dst[0] = make_float4(out[m][0].h, out[m][0].l, out[m][1].h, out[m][1].l);
-    if constexpr (D == 3) dst[1] = make_float4(out[m][2].h, out[m][2].l, 0.0f, 0.0f);
+    const float4 p0 = make_float4(out[m][0].h, out[m][0].l, out[m][1].h, out[m][1].l);
+    if constexpr (D == 3) store_packet32(dst, p0, make_float4(out[m][2].h, out[m][2].l, 0.0f, 0.0f));
+    else dst[0] = p0;
   }
 }
 
@@ -379,13 +381,12 @@ __global__ void __launch_bounds__(256) k_backward_gather_tiles(const int32_t* __
   for (int c = 0; c < D; ++c) acc[c] = df2{0.0f, 0.0f};
   const int q1 = __ldg(inc_ptr + v + 1);
   for (int q = __ldg(inc_ptr + v); q < q1; ++q) {
-    const float4 a = __ldg(pk + 2 * (size_t)q);
+    float4 a, b;
+    if constexpr (D == 3) load_packet32<false>(pk + 2 * (size_t)q, a, b);
+    else a = __ldg(pk + 2 * (size_t)q);
     acc[0] = df_acc(acc[0], df2{a.x, a.y});
     acc[1] = df_acc(acc[1], df2{a.z, a.w});
-    if constexpr (D == 3) {
-      const float4 b = __ldg(pk + 2 * (size_t)q + 1);
-      acc[2] = df_acc(acc[2], df2{b.x, b.y});
-    }
+    if constexpr (D == 3) acc[2] = df_acc(acc[2], df2{b.x, b.y});
   }
 #pragma unroll
   for (int c = 0; c < D; ++c) gnode[v * D + c] = df_to_double(acc[c]);
@@ -429,7 +430,7 @@ int assemble_backward(const Pattern* P, const double* node, const double* k, int
     return FEM_OK;
   }
   const TilePlan& T = P->tile;
-  if (T.ok && T.pk && (T.TE == 128 || T.TE == 256)) {
+  if (T.ok && T.pk && (T.TE == 128 || T.TE == 256) && (reinterpret_cast<uintptr_t>(T.pk) & 31) == 0) {
     const int smem = ((T.max_v * vtx_bytes(P->d)) + 15) / 16 * 16;
     const int g2 = (N + 255) / 256;
 #define FEM_BWD_TILES(DD, TT)                                                                                      \

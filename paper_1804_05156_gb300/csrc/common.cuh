@@ -105,8 +105,8 @@ struct TilePlan {
   int32_t* ipos = nullptr;     // [(d+1)][NT] packet (incidence) index of (elist[j], i)
   void* pw = nullptr;          // [NT*(d+1)] per incidence: other columns' in-row positions (uint16 2-D, uint32 3-D)
   uint8_t* rdp = nullptr;      // [N] in-row position of the diagonal
-  float4* pk = nullptr;        // packets, 32 bytes per incidence: 3-D [NT*4][2] float4; 2-D a pair array
-                               // [NT*3] float4 then a load array [NT*3] float2
+  float4* pk = nullptr;        // packets, 32 bytes per incidence: 3-D and fused 2-D [NT*(d+1)][2] float4;
+                               // two-launch 2-D a pair array [NT*3] float4 then a load array [NT*3] float2
 };
 void free_tile_plan(TilePlan& T);
 int build_tile_plan(const struct Pattern* P, const int32_t* order, int TE, TilePlan* out, cudaStream_t s);

@@ -7,7 +7,9 @@
 //   local stiffness and load entries (element_df.cuh: Sec. 3.1.3, eq. (dlambda), Sec. 3.2) and writes,
 //   for each local row i, one packet of float pairs to the slot q of incidence (t, i):
 //     2-D: (a_ij, a_ik) 16 bytes at pair array [q] and b_i 8 bytes at load array [q] (24 bytes, both
-//          stores aligned: no divergent paths);  3-D: (a_ij, a_ik, a_il, b_i), 32 bytes,
+//          stores aligned: no divergent paths); in the fused form, where the gather reads the packets
+//          back through L2 in the same launch, (a_ij, a_ik, b_i, unused) as 32 bytes in one 256-bit store;
+//     3-D: (a_ij, a_ik, a_il, b_i), 32 bytes in one 256-bit store,
 //   with j < k < l the other local indices. The diagonal is re-formed from the packet in phase 2 exactly
 //   as the element routine forms it (2-D a_ii = -(a_ij + a_ik), 3-D ((0 - a_ij) - a_ik) - a_il), so it
 //   costs no bytes.
@@ -27,6 +29,7 @@
 
 #include "common.cuh"
 #include "element_df.cuh"
+#include "packet.cuh"
 
 namespace fem {
 
@@ -79,7 +82,7 @@ template <int D>
 __host__ __device__ constexpr int staged_sc_bytes() { return D == 2 ? (int)sizeof(SCPad2) : 0; }
 
 // Phase 1 for one tile (all TE threads of the CTA; one __syncthreads inside).
-template <int D, int TE>
+template <int D, int TE, bool FUSED = false>
 __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, unsigned char* sm,
                                                  const double* __restrict__ node, const double* __restrict__ k,
                                                  int f_kind, const double* __restrict__ f_arg, int want_a, int want_b,
@@ -180,12 +183,16 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
       if (jj != i) o[c++] = L.a[pidx<D>(i, jj)];
     if constexpr (D == 2) {
       // 2-D packet in two arrays: (a_ij, a_ik) 16 bytes at pk[q], b_i 8 bytes at the load array's [q]
-      a.pk[qi[i]] = make_float4(o[0].h, o[0].l, o[1].h, o[1].l);
-      reinterpret_cast<float2*>(a.pk + a.NT * 3)[qi[i]] = make_float2(L.bt[i].h, L.bt[i].l);
+      if constexpr (FUSED) {  // read back through L2 in the same launch: one 256-bit access per packet
+        store_packet32(a.pk + 2 * (size_t)qi[i], make_float4(o[0].h, o[0].l, o[1].h, o[1].l),
+                       make_float4(L.bt[i].h, L.bt[i].l, 0.0f, 0.0f));
+      } else {
+        a.pk[qi[i]] = make_float4(o[0].h, o[0].l, o[1].h, o[1].l);
+        reinterpret_cast<float2*>(a.pk + a.NT * 3)[qi[i]] = make_float2(L.bt[i].h, L.bt[i].l);
+      }
     } else {
-      float4* dst = a.pk + 2 * (size_t)qi[i];
-      dst[0] = make_float4(o[0].h, o[0].l, o[1].h, o[1].l);
-      dst[1] = make_float4(o[2].h, o[2].l, L.bt[i].h, L.bt[i].l);
+      store_packet32(a.pk + 2 * (size_t)qi[i], make_float4(o[0].h, o[0].l, o[1].h, o[1].l),
+                     make_float4(o[2].h, o[2].l, L.bt[i].h, L.bt[i].l));
     }
   }
 }
@@ -233,14 +240,16 @@ __device__ __forceinline__ float2 load_pair(const float2* p) {
 // packet q as (p0, p1): 2-D (a_ij, a_ik) and b_i from their two arrays, 3-D four pairs (32 bytes)
 template <int D, bool FRESH>
 __device__ __forceinline__ void load_packet(const float4* pk, const float2* pkb, int64_t q, float4& p0, float4& p1) {
-  if constexpr (D == 2) {
-    // (a_ij, a_ik) from the pair array, b_i from the load array: two aligned loads
+  if constexpr (D == 2 && FRESH) {
+    // fused form: 32-byte packets (a_ij, a_ik, b_i, unused) in one 256-bit load
+    load_packet32<FRESH>(pk + 2 * q, p0, p1);
+  } else if constexpr (D == 2) {
+    // two-launch form: (a_ij, a_ik) from the pair array, b_i from the load array: two aligned loads
     p0 = load_packet_half<FRESH>(pk + q);
     const float2 z = load_pair<FRESH>(pkb + q);
     p1 = make_float4(z.x, z.y, 0.0f, 0.0f);
   } else {
-    p0 = load_packet_half<FRESH>(pk + 2 * q);
-    p1 = load_packet_half<FRESH>(pk + 2 * q + 1);
+    load_packet32<FRESH>(pk + 2 * q, p0, p1);
   }
 }
 
@@ -360,7 +369,7 @@ __global__ void __launch_bounds__(TE, (D == 3 ? 768 : 1152) / TE)
     const int last = min(first + kItemsPerClaim, a.ntiles);
     for (int tile = first; tile < last; ++tile) {
       if (tile > first) __syncthreads();  // staging of the next tile overwrites shared memory
-      elements_of_tile<D, TE>(a, tile, sm, node, k, f_kind, f_arg, want_a, want_b, tab, err);
+      elements_of_tile<D, TE, true>(a, tile, sm, node, k, f_kind, f_arg, want_a, want_b, tab, err);
     }
   }
   // grid-wide barrier: every packet of every tile is written before any row reads one
@@ -433,6 +442,7 @@ int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_
     if (b && P->N > 0) FEM_CUDA(cudaMemsetAsync(b, 0, sizeof(double) * P->N, s));
     return FEM_OK;
   }
+  if (reinterpret_cast<uintptr_t>(T.pk) & 31) return set_error(FEM_ERR_STATE, "packet buffer not 32-byte aligned");
   TileArgs a;
   a.NT = P->NT;
   a.ntiles = T.ntiles;
