@@ -12,7 +12,8 @@
 namespace fem {
 
 // FRESH: the packet was written earlier in the same launch, so read it through L2 (.cg); otherwise
-// through the read-only path (.nc)
+// through the read-only path (.nc), without allocating it in L1: every 32-byte packet is read once, so
+// an L1 copy is never used again and only costs the L1 the allocation
 template <bool FRESH>
 __device__ __forceinline__ void load_packet32(const float4* p, float4& a, float4& b) {
   if constexpr (FRESH)
@@ -20,7 +21,7 @@ __device__ __forceinline__ void load_packet32(const float4* p, float4& a, float4
                  : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
                  : "l"(p));
   else
-    asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+    asm volatile("ld.global.nc.L1::no_allocate.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                  : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
                  : "l"(p));
 }
