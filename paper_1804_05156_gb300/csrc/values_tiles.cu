@@ -301,10 +301,10 @@ __device__ __forceinline__ void rows_of_warp(const RowArgs& g, int64_t R0, df2* 
   __syncwarp();
 }
 
-// Registers capped so that 1152 threads (nine 128-thread tiles, 2-D; no spills) or 768 threads (six, 3-D;
+// Registers capped so that 1280 threads (ten 128-thread tiles, 2-D; no spills) or 896 threads (seven, 3-D;
 // a few spilled bytes cost less than the lost occupancy) fit an SM.
 template <int D, int TE>
-__global__ void __launch_bounds__(TE, (D == 3 ? 768 : 1152) / TE)
+__global__ void __launch_bounds__(TE, (D == 3 ? 896 : 1280) / TE)
     k_tile_elements(TileArgs a, const double* __restrict__ node, const double* __restrict__ k, int f_kind,
                     const double* __restrict__ f_arg, int want_a, int want_b, const float4* __restrict__ tab,
                     int* __restrict__ err) {
@@ -350,10 +350,10 @@ constexpr int kBarrierPolls = 1 << 24;  // bounded grid-barrier wait (with a sho
 constexpr int kItemsPerClaim = 8;       // tiles (or row groups) taken per counter increment
 
 // ctr[0]: next tile, ctr[1]: CTAs past phase 1, ctr[2]: next group of TE rows (taken kItemsPerClaim at a
-// time); zeroed before the launch. 2-D: registers capped so that nine 128-thread CTAs are resident per
-// SM, as for the element kernel (no spills); 3-D as the element kernel.
+// time); zeroed before the launch. 2-D: registers capped so that ten 128-thread CTAs are resident per
+// SM, as for the element kernel; 3-D six.
 template <int D, int TE, typename PW>
-__global__ void __launch_bounds__(TE, (D == 3 ? 768 : 1152) / TE)
+__global__ void __launch_bounds__(TE, (D == 3 ? 768 : 1280) / TE)
     k_tiles_fused(TileArgs a, RowArgs g, const double* __restrict__ node, const double* __restrict__ k, int f_kind,
                   const double* __restrict__ f_arg, double* __restrict__ val, double* __restrict__ bvec,
                   const float4* __restrict__ tab, int* __restrict__ ctr, int* __restrict__ err) {
