@@ -337,7 +337,10 @@ def run_ours(args):
     dist, rank, ws = dist_init(args)
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    fa.build()
+    if rank == 0:
+        fa.build()  # one build (a no-op when the library is current); the other ranks wait for it
+    if dist:
+        dist.barrier()
     mesh = meshgen.make_config(args.config)
     d, node, elem, k = mesh["d"], mesh["node"], mesh["elem"], mesh["coef"]
     NT_job = elem.shape[0] * ws  # weak scaling: every rank assembles its own copy of the workload
