@@ -293,16 +293,22 @@ void fem_batch_destroy(fem_batch_t bt);
  * memory while they assemble. One example is an application that hands all device memory to its own
  * pool at start-up. Another is a loop with a fixed latency budget, where the implicit device
  * synchronisation of an allocation is unacceptable.
- * Same result and arguments as fem_assemble with FEM_DETERMINISTIC (bitwise the same values). It
- * calls no cudaMalloc, cudaFree or other allocating routine. Its per-element scratch lives in a
- * fixed device array of FEM_NOALLOC_SCRATCH_DOUBLES doubles (16 MiB), compiled into the library.
- * Every GPU that loads the library holds that array until the process exits.
+ * Arguments as fem_assemble with FEM_DETERMINISTIC. It always runs the FP64 two-pass kernels (per-element
+ * FP64 values into the scratch, then per-slot FP64 sums in ascending element order), so its values are
+ * bitwise those of fem_assemble on the same pattern after fem_pattern_force_path(FEM_PATH_TWO_PASS),
+ * bitwise the same from call to call, and within the parity tolerance (1e-12 of each entry's magnitude)
+ * of fem_assemble's default float-float paths, whose bits differ. It calls no cudaMalloc, cudaFree or
+ * other allocating routine. Its per-element scratch lives in a fixed device array of
+ * FEM_NOALLOC_SCRATCH_DOUBLES doubles (16 MiB), compiled into the library. Every GPU that loads the
+ * library holds that array until the process exits.
  *  - Size limit: d = 2 meshes up to FEM_NOALLOC_SCRATCH_DOUBLES / 9 = 233,016 elements, d = 3 up to
  *    FEM_NOALLOC_SCRATCH_DOUBLES / 14 = 149,796 elements. Larger meshes return FEM_ERR_ARG and
  *    launch nothing.
- *  - Set-up: the first call on a device (with that device current) looks up the array's device
- *    address with cudaGetSymbolAddress and caches it. Make that first call before any stream capture.
- *  - The pattern p must have been built on the current device (FEM_ERR_STATE otherwise).
+ *  - Set-up, two preconditions: (1) the pattern p was built (fem_mesh_build_pattern) on the current
+ *    device, which also makes the device error word this call reports through (FEM_ERR_STATE
+ *    otherwise); (2) the first call on a device (with that device current) looks up the array's device
+ *    address with cudaGetSymbolAddress and caches it. Build the pattern and make that first call before
+ *    any stream capture.
  *  - Sharing: all calls on a device share the one array, which keeps the last call's contents.
  *    Every call overwrites the scratch it reads, and val/b are cleared before they are
  *    accumulated. Calls that overlap on the GPU (for example on two streams at once) race on the

@@ -55,7 +55,7 @@ def _load():
         lib.ora_dirichlet.restype = I32
         lib.ora_dirichlet.argtypes = [I64, P, P, P, P, P, P, P, P]
         lib.ora_backward.restype = I32
-        lib.ora_backward.argtypes = [I32, I64, I64, P, P, P, I32, P, P, P, P, P, P]
+        lib.ora_backward.argtypes = [I32, I64, I64, P, P, P, I32, P, P, P, P, P, P, P, P]
         lib.ora_local_affine.restype = I32
         lib.ora_local_affine.argtypes = [P, P]
         lib.ora_boundary_terms.restype = I32
@@ -193,16 +193,20 @@ def dirichlet(row_ptr, col, val, b, is_bd, gD=None):
     return val, b, fn[: int(nf[0])].copy()
 
 
-def backward(d, node, elem, k, fkind, farg, slot, w, r):
-    """(gnode [N, d], gk [NT]) of L = w . A + r . b."""
+def backward(d, node, elem, k, fkind, farg, slot, w, r, with_scale=False):
+    """(gnode [N, d], gk [NT]) of L = w . A + r . b; with_scale=True also returns the per-entry magnitudes
+    (gnode_mag, gk_mag): the same sums with every term replaced by its absolute value, the scale the
+    parity tolerance of each gradient entry is relative to."""
     node, elem, k = _c(node, np.float64), _c(elem, np.int32), _c(k, np.float64)
     farg, slot, w, r = _c(farg, np.float64), _c(slot, np.int64), _c(w, np.float64), _c(r, np.float64)
     N, NT = node.shape[0], elem.shape[0]
     gn = np.zeros((N, d), np.float64)
     gk = np.zeros(NT, np.float64)
+    gnm = np.zeros((N, d), np.float64) if with_scale else None
+    gkm = np.zeros(NT, np.float64) if with_scale else None
     _check(_load().ora_backward(d, N, NT, _p(node), _p(elem), _p(k), fkind, _p(farg), _p(slot), _p(w), _p(r),
-                                _p(gn), _p(gk)))
-    return gn, gk
+                                _p(gn), _p(gk), _p(gnm), _p(gkm)))
+    return (gn, gk, gnm, gkm) if with_scale else (gn, gk)
 
 
 def local_affine(p):

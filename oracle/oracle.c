@@ -505,10 +505,12 @@ static void f_grad(int kind, int d, const double* p, double* g) {
 
 int ora_backward(int d, int64_t N, int64_t NT, const double* node, const int32_t* elem, const double* k,
                  int fkind, const double* farg, const int64_t* slot, const double* w, const double* r,
-                 double* gnode, double* gk) {
+                 double* gnode, double* gk, double* gnode_mag, double* gk_mag) {
   if (d != 2 && d != 3) return ORA_ERR_ARG;
   int d1 = d + 1;
   for (int64_t p = 0; p < N * d; ++p) gnode[p] = 0.0;
+  if (gnode_mag)
+    for (int64_t p = 0; p < N * d; ++p) gnode_mag[p] = 0.0;
   double dfact = (d == 2) ? 2.0 : 6.0;
   for (int64_t t = 0; t < NT; ++t) {
     const int32_t* e = elem + d1 * t;
@@ -526,6 +528,15 @@ int ora_backward(int d, int64_t N, int64_t NT, const double* node, const int32_t
     for (int i = 0; i < d1; ++i)
       for (int j = 0; j < d1; ++j) S = S + W[i][j] * dot(g[i], g[j], d);
     if (gk) gk[t] = meas * S;
+    /* magnitudes: the same expressions with every term replaced by its absolute value and every basis
+       gradient component by the magnitude of the terms that form it (normal_magnitudes) */
+    double nm[4][3], ga[4][3], Sa = 0.0;
+    normal_magnitudes(d, node, e, nm);
+    for (int i = 0; i < d1; ++i)
+      for (int m = 0; m < d; ++m) ga[i][m] = nm[i][m] / (dfact * meas);
+    for (int i = 0; i < d1; ++i)
+      for (int j = 0; j < d1; ++j) Sa = Sa + fabs(W[i][j]) * dot(ga[i], ga[j], d);
+    if (gk_mag) gk_mag[t] = meas * Sa;
     /* rhs part */
     double pts[4][3], lam[4][4], fq[4], gf[4][3];
     int nq = ora_quad_points(d, node, e, pts, lam);
@@ -534,31 +545,45 @@ int ora_backward(int d, int64_t N, int64_t NT, const double* node, const int32_t
       fq[q] = f_eval(fkind, d, pts[q], farg, t, q, nq);
       f_grad(fkind, d, pts[q], gf[q]);
     }
-    double Rb = 0.0;  /* sum_i r_i sum_q w_q f_q lambda_i(q) */
+    double Rb = 0.0, Rba = 0.0;  /* sum_i r_i sum_q w_q f_q lambda_i(q), and its magnitude */
     if (r)
       for (int i = 0; i < d1; ++i) {
-        double s = 0.0;
-        for (int q = 0; q < nq; ++q) s = s + wq * fq[q] * lam[q][i];
+        double s = 0.0, sa = 0.0;
+        for (int q = 0; q < nq; ++q) {
+          s = s + wq * fq[q] * lam[q][i];
+          sa = sa + wq * fabs(fq[q]) * lam[q][i];
+        }
         Rb = Rb + r[e[i]] * s;
+        Rba = Rba + fabs(r[e[i]]) * sa;
       }
     for (int mm = 0; mm < d1; ++mm) {
-      double out[3];
+      double out[3], outa[3];
       for (int c = 0; c < d; ++c) {
-        double acc = S * g[mm][c];
+        double acc = S * g[mm][c], acca = Sa * ga[mm][c];
         for (int i = 0; i < d1; ++i)
-          for (int j = 0; j < d1; ++j)
+          for (int j = 0; j < d1; ++j) {
             acc = acc - W[i][j] * (dot(g[mm], g[j], d) * g[i][c] + dot(g[mm], g[i], d) * g[j][c]);
+            acca = acca + fabs(W[i][j]) * (dot(ga[mm], ga[j], d) * ga[i][c] + dot(ga[mm], ga[i], d) * ga[j][c]);
+          }
         out[c] = kt * meas * acc;
+        outa[c] = fabs(kt) * meas * acca;
       }
       if (r) {
         for (int c = 0; c < d; ++c) {
-          double s2 = 0.0;
+          double s2 = 0.0, s2a = 0.0;
           for (int i = 0; i < d1; ++i)
-            for (int q = 0; q < nq; ++q) s2 = s2 + r[e[i]] * wq * lam[q][i] * lam[q][mm] * gf[q][c];
+            for (int q = 0; q < nq; ++q) {
+              s2 = s2 + r[e[i]] * wq * lam[q][i] * lam[q][mm] * gf[q][c];
+              s2a = s2a + fabs(r[e[i]]) * wq * lam[q][i] * lam[q][mm] * fabs(gf[q][c]);
+            }
           out[c] = out[c] + meas * g[mm][c] * Rb + meas * s2;
+          outa[c] = outa[c] + meas * ga[mm][c] * Rba + meas * s2a;
         }
       }
       for (int c = 0; c < d; ++c) gnode[(int64_t)e[mm] * d + c] = gnode[(int64_t)e[mm] * d + c] + out[c];
+      if (gnode_mag)
+        for (int c = 0; c < d; ++c)
+          gnode_mag[(int64_t)e[mm] * d + c] = gnode_mag[(int64_t)e[mm] * d + c] + outa[c];
     }
   }
   return ORA_OK;

@@ -6,6 +6,7 @@ import meshgen
 import oracle
 
 TOL = 1e-12  # relative to the per-slot magnitude scale returned by the oracle
+BWD_TOL = 1e-10  # gradients: relative to the per-entry magnitude of the adjoint's terms (oracle with_scale)
 
 
 def dev(a):

@@ -9,7 +9,7 @@ import torch
 
 import meshgen
 import oracle
-from tests._common import TOL, assert_close_scaled, dev, gpu_slot_to_tij, host, mesh_case, sample_rows
+from tests._common import BWD_TOL, TOL, assert_close_scaled, dev, gpu_slot_to_tij, host, mesh_case, sample_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -228,9 +228,9 @@ def test_rows_beyond_every_plan_take_the_two_pass_path():
     gk = torch.empty(NT, dtype=torch.float64, device="cuda")
     fa.fem_assemble_backward(p, dev(node), dev(k), fa.FEM_F_SINPROD, None, dev(w), dev(r), gn, gk)
     fa.get_error()
-    gno, gko = oracle.backward(2, node, elem, k, oracle.F_SINPROD, None, slot, w, r)
-    assert np.all(np.abs(host(gn) - gno) <= 1e-10 * (np.abs(gno) + np.abs(gno).max()))
-    assert np.all(np.abs(host(gk) - gko) <= 1e-10 * (np.abs(gko) + np.abs(gko).max()))
+    gno, gko, gnm, gkm = oracle.backward(2, node, elem, k, oracle.F_SINPROD, None, slot, w, r, with_scale=True)
+    assert_close_scaled(host(gn), gno, gnm, tol=BWD_TOL, what="node gradient")
+    assert_close_scaled(host(gk), gko, gkm, tol=BWD_TOL, what="k gradient")
     for call in (lambda: fa.fem_assemble_operator(p, dev(node), fa.FEM_OP_MASS, None),
                  lambda: fa.fem_apply_stiffness(p, dev(node), dev(k), dev(np.ones(N)))):
         with pytest.raises(fa.FemError) as e:
@@ -330,10 +330,8 @@ def test_backward_matches_oracle_adjoint(case, f_kind):
     w = meshgen.normal(1808, meshgen.TAG_W, p.nnz)
     r = meshgen.normal(1808, meshgen.TAG_R, N)
     farg = meshgen.normal(7, 9, NT * (d + 1)) if f_kind == fa.FEM_F_QPVALUES else None
-    gno, gko = oracle.backward(d, node, elem, k, f_kind, farg, slot, w, r)
-    # magnitude scale: the same adjoint with |w|, |r| bounds no cancellation; use max-based scale per array
-    sn = 1e-10 * (np.abs(gno) + np.abs(gno).max())
-    sk = 1e-10 * (np.abs(gko) + np.abs(gko).max())
+    # per-entry scale: the same adjoint with every term replaced by its magnitude
+    gno, gko, gnm, gkm = oracle.backward(d, node, elem, k, f_kind, farg, slot, w, r, with_scale=True)
     # tile order (the pattern has a tile plan), then the caller's order (no plan)
     for _ in range(2):
         gn = torch.empty((N, d), dtype=torch.float64, device="cuda")
@@ -341,8 +339,8 @@ def test_backward_matches_oracle_adjoint(case, f_kind):
         fa.fem_assemble_backward(p, dev(node), dev(k), f_kind, None if farg is None else dev(farg), dev(w), dev(r),
                                  gn, gk)
         fa.get_error()
-        assert np.all(np.abs(host(gn) - gno) <= sn)
-        assert np.all(np.abs(host(gk) - gko) <= sk)
+        assert_close_scaled(host(gn), gno, gnm, tol=BWD_TOL, what="node gradient")
+        assert_close_scaled(host(gk), gko, gkm, tol=BWD_TOL, what="k gradient")
         fa.fem_pattern_force_path(p, fa.FEM_PATH_TWO_PASS)
 
 
@@ -362,14 +360,14 @@ def test_backward_one_loss_part_matches_oracle_adjoint(case, f_kind, part):
     w = meshgen.normal(1808, meshgen.TAG_W, p.nnz) if part == "w" else None
     r = meshgen.normal(1808, meshgen.TAG_R, N) if part == "r" else None
     farg = meshgen.normal(7, 9, NT * (d + 1)) if f_kind == fa.FEM_F_QPVALUES else None
-    gno, gko = oracle.backward(d, node, elem, k, f_kind, farg, slot, w, r)
+    gno, gko, gnm, gkm = oracle.backward(d, node, elem, k, f_kind, farg, slot, w, r, with_scale=True)
     gn = torch.empty((N, d), dtype=torch.float64, device="cuda")
     gk = torch.empty(NT, dtype=torch.float64, device="cuda")
     fa.fem_assemble_backward(p, dev(node), dev(k), f_kind, None if farg is None else dev(farg),
                              None if w is None else dev(w), None if r is None else dev(r), gn, gk)
     fa.get_error()
-    assert np.all(np.abs(host(gn) - gno) <= 1e-10 * (np.abs(gno) + np.abs(gno).max()))
-    assert np.all(np.abs(host(gk) - gko) <= 1e-10 * (np.abs(gko) + np.abs(gko).max()))
+    assert_close_scaled(host(gn), gno, gnm, tol=BWD_TOL, what="node gradient")
+    assert_close_scaled(host(gk), gko, gkm, tol=BWD_TOL, what="k gradient")
 
 
 def test_backward_central_fd_on_gpu():
@@ -608,9 +606,9 @@ def test_full_size_backward_matches_oracle_adjoint():
     val, b = fa.assemble(p, dev(node), dev(k), fa.FEM_F_SINPROD)
     fa.fem_assemble_backward(p, dev(node), dev(k), fa.FEM_F_SINPROD, None, dev(w), dev(r), gn, gk)
     fa.get_error()
-    gno, gko = oracle.backward(3, node, elem, k, oracle.F_SINPROD, None, slot, w, r)
-    assert np.all(np.abs(host(gn) - gno) <= 1e-10 * (np.abs(gno) + np.abs(gno).max()))
-    assert np.all(np.abs(host(gk) - gko) <= 1e-10 * (np.abs(gko) + np.abs(gko).max()))
+    gno, gko, gnm, gkm = oracle.backward(3, node, elem, k, oracle.F_SINPROD, None, slot, w, r, with_scale=True)
+    assert_close_scaled(host(gn), gno, gnm, tol=BWD_TOL, what="node gradient")
+    assert_close_scaled(host(gk), gko, gkm, tol=BWD_TOL, what="k gradient")
 
 
 # ---- Neumann / Robin sides and the pure-Neumann fixes ------------------------------------------------

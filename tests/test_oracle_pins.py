@@ -454,6 +454,30 @@ def test_backward_invariants(d):
     assert abs(float(k @ gk) - L) <= 1e-12 * (abs(L) + float(np.abs(k * gk).sum()))
 
 
+@pytest.mark.parametrize("d", [2, 3])
+def test_backward_magnitudes(d):
+    """The per-entry magnitudes the gradient tolerance is relative to: never below the gradient itself,
+    and equal to it where every term is nonnegative (2-D, w = 1 on the diagonal slots only, r = 0:
+    dL/dk_t = |tau| sum_i |grad lambda_i|^2, a sum of squares)."""
+    m = meshgen.square_mesh(5, 0.2, 16) if d == 2 else meshgen.kuhn_mesh(3, 0.1, 16)
+    node, elem = m["node"], m["elem"]
+    N, NT = node.shape[0], elem.shape[0]
+    k = meshgen.lognormal(16, 3, NT)
+    rp, col = oracle.pattern(d, N, elem)
+    slot = oracle.slots(d, N, elem, rp, col)
+    w, r = meshgen.normal(17, 4, rp[-1]), meshgen.normal(17, 5, N)
+    gn, gk, gnm, gkm = oracle.backward(d, node, elem, k, oracle.F_SINPROD, None, slot, w, r, with_scale=True)
+    assert np.all(gnm >= np.abs(gn)) and np.all(gkm >= np.abs(gk))
+    assert np.all(gnm > 0) and np.all(gkm > 0)
+    if d == 2:
+        wd = np.zeros(rp[-1])
+        for row in range(N):
+            wd[rp[row] + np.searchsorted(col[rp[row]:rp[row + 1]], row)] = 1.0
+        _, gk1, _, gkm1 = oracle.backward(d, node, elem, k, oracle.F_CONST, None, slot, wd, None, with_scale=True)
+        assert np.all(gk1 > 0)
+        assert np.allclose(gkm1, gk1, rtol=1e-14, atol=0)
+
+
 # --- Neumann / Robin sides and the pure-Neumann fixes (Sec. 3.3 and "Boundary conditions") --------
 
 def _geometry(d, n, jitter, seed):
@@ -710,6 +734,73 @@ def test_rule_load_vector(d):
     b7 = oracle.rhs_rule(d, node, elem, *oracle.quad_rule(d, 7), oracle.F_SINPROD)
     inner = np.abs(b7) > 1e-3 * np.abs(b7).max()
     assert np.allclose(b6[inner], b7[inner], rtol=1e-8, atol=0)
+
+
+def _exact_sine_load(d, node, elem):
+    """b_i = sum over elements of the integral of prod_m sin(pi x_m) lambda_i over the element, by an
+    independent brute force: 2-D adaptive quadrature (scipy.integrate.dblquad) over the reference
+    triangle, 3-D a 24^3-point tensor Gauss-Legendre rule (numpy.polynomial.legendre.leggauss) over the
+    unit cube mapped onto the reference tetrahedron by the collapsed (Duffy) map with its Jacobian
+    (1-v)(1-w)^2 written out. f is evaluated as numpy's sin of pi times the physical coordinate, with no
+    integer shift and no sign flip."""
+    from scipy.integrate import dblquad
+    b = np.zeros(node.shape[0])
+    if d == 3:
+        g, gw = np.polynomial.legendre.leggauss(24)
+        g, gw = 0.5 * (g + 1.0), 0.5 * gw
+        U, V, W = np.meshgrid(g, g, g, indexing="ij")
+        WT = (gw[:, None, None] * gw[None, :, None] * gw[None, None, :]) * (1 - V) * (1 - W) ** 2
+        # (u, v, w) in the unit cube -> reference tetrahedron point (x, y, z), x + y + z <= 1
+        X, Y, Z = U * (1 - V) * (1 - W), V * (1 - W), W
+        lam = [1 - X - Y - Z, X, Y, Z]
+    for e in elem:
+        P = node[e]
+        J = P[1:] - P[0]
+        det = abs(np.linalg.det(J))
+        for i in range(d + 1):
+            if d == 2:
+                def fl(y, x, i=i):
+                    p = P[0] + x * J[0] + y * J[1]
+                    li = (1 - x - y, x, y)[i]
+                    return np.sin(np.pi * p[0]) * np.sin(np.pi * p[1]) * li
+                val, _ = dblquad(fl, 0.0, 1.0, 0.0, lambda x: 1.0 - x, epsabs=1e-15, epsrel=1e-13)
+            else:
+                pts = P[0] + X[..., None] * J[0] + Y[..., None] * J[1] + Z[..., None] * J[2]
+                f = np.prod(np.sin(np.pi * pts), axis=-1)
+                val = float((WT * f * lam[i]).sum())
+            b[e[i]] += det * val
+    return b
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_rule_sine_product_branch(d):
+    """The sine-product branch of the rule load vector (the points are shifted by an integer near the
+    element and the sign follows its parity) pinned two ways that do not use that branch:
+    (1) against the exact integrals by an independent brute force (adaptive 2-D quadrature, a tensor
+    Gauss-Legendre rule in 3-D) on a mesh moved by an integer vector of odd sum, so that the branch's
+    shift is nonzero and its sign flips: the 8-point conical rule (exact to degree 15, h = 1/4) agrees to
+    1e-12; (2) the periodicity sin(pi (x + s)) = (-1)^s sin(pi x): moving the mesh by an integer vector s
+    multiplies the load by (-1)^(sum s)."""
+    m = _geometry(d, 4 if d == 2 else 2, 0.2 if d == 2 else 0.1, 83)
+    node, elem = m["node"], m["elem"]
+    if d == 3:
+        node = node * 0.5  # h = 1/4
+    shift = np.array([3.0, -2.0] if d == 2 else [3.0, -2.0, 2.0])  # odd sum: the load changes sign
+    moved = node + shift
+    bary, w = oracle.quad_rule(d, 8)
+    b_rule = oracle.rhs_rule(d, moved, elem, bary, w, oracle.F_SINPROD)
+    b_exact = _exact_sine_load(d, moved, elem)
+    scale = _exact_sine_load(d, node, elem)  # the same integrals unmoved: b_exact = -scale up to rounding
+    assert np.all(np.abs(b_exact + scale) <= 1e-12 * np.abs(scale).max())
+    assert np.all(np.abs(b_rule - b_exact) <= 1e-12 * np.abs(b_exact).max()), np.abs(b_rule - b_exact).max()
+    # periodicity with a rule of modest order, several shifts of both parities
+    bary3, w3 = oracle.quad_rule(d, 3)
+    b0 = oracle.rhs_rule(d, node, elem, bary3, w3, oracle.F_SINPROD)
+    shifts = ([1, 0], [0, -3], [2, 2], [5, 1], [-4, 7]) if d == 2 else ([1, 0, 0], [0, 2, 1], [-3, 1, 1], [2, 2, -2])
+    for s in shifts:
+        bs = oracle.rhs_rule(d, node + np.array(s, float), elem, bary3, w3, oracle.F_SINPROD)
+        sign = -1.0 if sum(s) % 2 else 1.0
+        assert np.all(np.abs(bs - sign * b0) <= 1e-12 * np.abs(b0).max()), (s, np.abs(bs - sign * b0).max())
 
 
 # --- the whole method: assemble, eliminate the Dirichlet rows, solve ---------------------------------
