@@ -250,7 +250,7 @@ def _time_steps(fn, steps, flush, s):
 
 
 def extras(fa, args, flush, plain_melem):
-    """Secondary rows of the metric: 3-D, atomic variant, Dirichlet, batched (C4), fwd+bwd (C5)."""
+    """Secondary rows of the metric: 3-D (C3), batched (C4), fwd+bwd (C5), the CG solve on C5, and C1."""
     import torch
     s = torch.cuda.current_stream()
     out = {}
@@ -326,6 +326,37 @@ def extras(fa, args, flush, plain_melem):
     out["c5_fwd_bwd_64cube"] = {"fwd_ms": ms_f, "fwd_bwd_ms": ms_fb, "NT": NT,
                                 "fwd_Melem_s": NT / (ms_f * 1e-3) / 1e6, "fwd_bwd_Melem_s": NT / (ms_fb * 1e-3) / 1e6,
                                 "fwd_bwd_vs_plain_fwd": ms_f / ms_fb}
+    # the reduced Dirichlet solve on the same mesh (Sec. 3.3) by matrix-free CG: whole boundary, g_D = 0
+    isbd = torch.empty(p.N, dtype=torch.uint8, device="cuda")
+    fa.fem_boundary_nodes(p, None, isbd)
+    fwd()
+    u = torch.empty(p.N, dtype=torch.float64, device="cuda")
+    fa.fem_cg_solve(p, nd, kd, isbd, b, None, u, max_iter=16, rtol=1e-8)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, its, rel = fa.fem_cg_solve(p, nd, kd, isbd, b, None, u, max_iter=5000, rtol=1e-8)
+    torch.cuda.synchronize()
+    cg_ms = 1e3 * (time.perf_counter() - t0)
+    fa.get_error()
+    out["c5_cg_solve_64cube"] = {"iterations": its, "relres": rel, "rtol": 1e-8, "ms": cg_ms,
+                                 "ms_per_iteration": cg_ms / max(its, 1),
+                                 "operator": "matrix-free fem_apply_stiffness (Dirichlet-eliminated), FP64 vectors"}
+    del p, val, b, gn, gk, w, r, nd, kd, u, isbd
+    torch.cuda.empty_cache()
+    # the small, launch-bound end of the metric: 64 x 64 uniform, k = 1, f = 1 (C1)
+    m = meshgen.make_config("c1")
+    nd = torch.as_tensor(m["node"]).cuda()
+    p = fa.Pattern(torch.as_tensor(m["elem"]).cuda(), m["node"].shape[0])
+    fa.fem_pattern_set_locality(p, nd)
+    val = torch.empty(p.nnz, dtype=torch.float64, device="cuda")
+    b = torch.empty(p.N, dtype=torch.float64, device="cuda")
+    f = lambda: fa.fem_assemble(p, nd, None, fa.FEM_F_CONST, None, val, b, fa.FEM_DETERMINISTIC)
+    for _ in range(3):
+        f()
+    ms = _time_steps(f, max(steps, 20), flush, s)
+    NT = m["elem"].shape[0]
+    out["c1_2d_64sq"] = {"ms": ms, "Melem_s": NT / (ms * 1e-3) / 1e6, "NT": NT, "nnz": p.nnz,
+                         "path": fa.fem_pattern_value_path(p)}
     fa.get_error()
     return out
 

@@ -62,8 +62,13 @@ typedef void* fem_stream_t; /* cudaStream_t */
  * and the vertex-to-element incidence lists used by the deterministic reduction.
  * `elem` is read during the call only; the pattern keeps its own copy of the topology, so later
  * value calls take no `elem` argument. Synchronises `stream` (twice: after validation, and to size
- * col_idx). Errors: FEM_ERR_ARG (d, N, NT out of range: N < 2^31, NT*(d+1)^2 < 2^31),
- * FEM_ERR_INDEX (bad vertex id), FEM_ERR_OOM, FEM_ERR_CUDA. NT = 0 gives an empty pattern. */
+ * col_idx). Each row is formed by one warp from its K = D (d+1) candidate columns, D the number of
+ * elements at the row's vertex: duplicates are found by comparing candidates pairwise (O(K^2) work per
+ * row) in a shared-memory stage of 5 K bytes per warp, so a vertex may be in at most 40,960 / (d+1)
+ * elements (13,653 in 2-D, 10,240 in 3-D) and very high degrees build slowly.
+ * Errors: FEM_ERR_ARG (d, N, NT out of range: N < 2^31, NT*(d+1)^2 < 2^31; a vertex degree beyond the
+ * limit above; more than 2^31 - 1 structural entries), FEM_ERR_INDEX (bad vertex id), FEM_ERR_OOM,
+ * FEM_ERR_CUDA. NT = 0 gives an empty pattern. */
 int fem_mesh_build_pattern(int d, int64_t N, int64_t NT, const int32_t* elem, fem_pattern_t* out,
                            fem_stream_t stream);
 
@@ -119,6 +124,17 @@ int fem_pattern_value_path(fem_pattern_t p, int* path, int* tile_elems, float* t
  * the current one (synchronises `stream`; FEM_ERR_STATE if a row has more than 256 entries, or for
  * TILES_FUSED if its shared memory does not fit). fem_pattern_force_launch selects BLOCKED. */
 int fem_pattern_force_path(fem_pattern_t p, int path, int tile_elems, fem_stream_t stream);
+
+/* Fault injection for tests of the bounded wait in FEM_PATH_TILES_FUSED (no counterpart in the paper).
+ * The fused launch orders its two phases with a grid-wide barrier: each CTA counts its arrival and
+ * polls the count (with a short sleep per poll) until every CTA of the launch has arrived, at most
+ * max_polls times; a CTA that gives up records FEM_ERR_TIMEOUT in the device error word and returns
+ * without its second phase (val and b are then incomplete). With extra_arrivals > 0 the barrier waits
+ * for that many CTAs more than the launch has, arrivals that never come, so every CTA gives up after
+ * max_polls polls: the error path can be exercised without a hang. (0, 0) restores the defaults (no
+ * extra arrivals; 2^24 polls). The setting belongs to the pattern and applies to its later fused
+ * launches. FEM_ERR_ARG for a null pattern or a negative setting. */
+int fem_pattern_barrier_fault(fem_pattern_t p, int extra_arrivals, int max_polls);
 
 /* Sizes and library-owned device arrays of a pattern (valid until fem_pattern_destroy):
  * row_ptr [N+1], col_idx [nnz], slot [(d+1)^2 * NT] (layout above). Any output pointer may be NULL. */
@@ -210,6 +226,26 @@ int fem_assemble_operator(fem_pattern_t p, const double* node, int op, const dou
  * and its packet buffer. */
 int fem_apply_stiffness(fem_pattern_t p, const double* node, const double* k, const double* u, const uint8_t* is_bd,
                         double* y, fem_stream_t stream);
+
+/* ---- reduced solve by conjugate gradients (Sec. 3.3) ------------------------------------------------
+ * The paper ends with u(freeNode) = A(freeNode, freeNode) \ b(freeNode) after the boundary lift
+ * b <- b - A u_D. This call solves that system by conjugate gradients with the matrix-free operator
+ * (fem_apply_stiffness): A is never formed. With u_D = gD on boundary vertices (is_bd [N] uint8, e.g.
+ * from fem_boundary_nodes; gD [N] nullable = 0) and 0 elsewhere, it forms r = b - A u_D on the free rows
+ * (b [N]: the load vector of fem_assemble, boundary entries ignored; k [NT] nullable = 1), starts from
+ * u = u_D and iterates CG on the eliminated operator until ||r||_2 <= rtol ||r_0||_2 or max_iter
+ * iterations. u [N] (device, overwritten; distinct from b and gD) receives gD on boundary vertices and
+ * the CG iterate on the free ones. Outputs (HOST, nullable): iters = iterations taken, relres =
+ * ||r||_2 / ||r_0||_2 (0 when r_0 = 0). Every dot product is a fixed-shape FP64 reduction whose shape
+ * depends on N only, so the iterates are bitwise reproducible. Synchronises `stream` every 8 iterations
+ * to test convergence; allocates (stream-ordered) and frees 3 N doubles of workspace per call.
+ * Errors: FEM_ERR_ARG (null or misaligned arrays, aliasing, max_iter < 0, rtol < 0), FEM_ERR_STATE
+ * (breakdown: p.Ap <= 0, i.e. the operator is not positive definite on the free vertices, as for a
+ * mesh piece with no boundary vertex; u holds the last iterate), those of fem_apply_stiffness. Element
+ * errors of the operator (FEM_ERR_DEGENERATE) surface at fem_get_error. */
+int fem_cg_solve(fem_pattern_t p, const double* node, const double* k, const uint8_t* is_bd, const double* b,
+                 const double* gD, double* u, int max_iter, double rtol, int* iters, double* relres,
+                 fem_stream_t stream);
 
 /* ---- load vector with rules of any order ("Numerical Quadrature") ---------------------------------
  * I_n(f) = |tau| sum_q w_q f(p_q) on each simplex, with the conical-product Gauss rule of n points per

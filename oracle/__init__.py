@@ -193,6 +193,23 @@ def dirichlet(row_ptr, col, val, b, is_bd, gD=None):
     return val, b, fn[: int(nf[0])].copy()
 
 
+def solve_reduced(row_ptr, col, val, b, is_bd, gD=None):
+    """Sec. 3.3: u = g_D on the boundary, u(freeNode) = A(freeNode, freeNode) \ (b - A u_D)(freeNode), with A
+    the assembled CSR matrix (before elimination) and a direct sparse solve (scipy.sparse.linalg.spsolve)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    N = len(row_ptr) - 1
+    A = sp.csr_matrix((np.asarray(val, np.float64), np.asarray(col), np.asarray(row_ptr)), shape=(N, N))
+    bd = np.asarray(is_bd).astype(bool)
+    uD = np.where(bd, 0.0 if gD is None else np.asarray(gD, np.float64), 0.0)
+    free = np.nonzero(~bd)[0]
+    rhs = np.asarray(b, np.float64) - A @ uD
+    u = uD.copy()
+    if free.size:
+        u[free] = spla.spsolve(A[free][:, free].tocsc(), rhs[free])
+    return u
+
+
 def backward(d, node, elem, k, fkind, farg, slot, w, r, with_scale=False):
     """(gnode [N, d], gk [NT]) of L = w . A + r . b; with_scale=True also returns the per-entry magnitudes
     (gnode_mag, gk_mag): the same sums with every term replaced by its absolute value, the scale the

@@ -55,6 +55,7 @@ def lib():
             "fem_pattern_force_launch": (I32, [P, I32, I32, I32]),
             "fem_pattern_value_path": (I32, [P, P, P, P]),
             "fem_pattern_force_path": (I32, [P, I32, I32, P]),
+            "fem_pattern_barrier_fault": (I32, [P, I32, I32]),
             "fem_pattern_destroy": (None, [P]),
             "fem_assemble": (I32, [P, P, P, I32, P, P, P, I32, P]),
             "fem_assemble_stiffness": (I32, [P, P, P, P, I32, P]),
@@ -66,6 +67,7 @@ def lib():
             "fem_assemble_operator": (I32, [P, P, I32, P, P, P]),
             "fem_quad_rule": (I32, [I32, I32, P, P, P]),
             "fem_apply_stiffness": (I32, [P, P, P, P, P, P, P]),
+            "fem_cg_solve": (I32, [P, P, P, P, P, P, P, I32, C.c_double, P, P, P]),
             "fem_rule_points": (I32, [P, P, I32, P, P]),
             "fem_assemble_rhs_rule": (I32, [P, P, I32, I32, P, P, P]),
             "fem_side_points": (I32, [P, P, P, P]),
@@ -215,6 +217,11 @@ def fem_pattern_force_path(p: Pattern, path: int, tile_elems: int = 256, stream=
     _check(lib().fem_pattern_force_path(p.handle, path, tile_elems, _stream(stream)))
 
 
+def fem_pattern_barrier_fault(p: Pattern, extra_arrivals: int, max_polls: int):
+    """Fault injection for the fused launch's bounded grid barrier (see include/femasm.h)."""
+    _check(lib().fem_pattern_barrier_fault(p.handle, int(extra_arrivals), int(max_polls)))
+
+
 def fem_assemble_operator(p: Pattern, node, op: int, coef=None, val=None, stream=None):
     """Values [nnz] of the mass matrix (FEM_OP_MASS, coef c [NT] or None), of -div(K grad) (FEM_OP_ANISO,
     coef [NT, d(d+1)/2] upper triangles) or of the stiffness matrix (FEM_OP_STIFFNESS, coef k [NT])."""
@@ -230,6 +237,16 @@ def fem_apply_stiffness(p: Pattern, node, k, u, is_bd=None, y=None, stream=None)
         y = torch.empty_like(u)
     _check(lib().fem_apply_stiffness(p.handle, _ptr(node), _ptr(k), _ptr(u), _ptr(is_bd), _ptr(y), _stream(stream)))
     return y
+
+
+def fem_cg_solve(p: Pattern, node, k, is_bd, b, gD=None, u=None, max_iter=10000, rtol=1e-10, stream=None):
+    """Reduced Dirichlet solve by matrix-free conjugate gradients: returns (u [N], iterations, relres)."""
+    if u is None:
+        u = torch.empty(p.N, dtype=torch.float64, device=node.device)
+    it, rr = C.c_int(), C.c_double()
+    _check(lib().fem_cg_solve(p.handle, _ptr(node), _ptr(k), _ptr(is_bd), _ptr(b), _ptr(gD), _ptr(u), int(max_iter),
+                              float(rtol), C.byref(it), C.byref(rr), _stream(stream)))
+    return u, it.value, rr.value
 
 
 def fem_quad_rule(d: int, n: int):

@@ -226,6 +226,14 @@ int fem_pattern_value_path(fem_pattern_t p, int* path, int* tile_elems, float* t
   return FEM_OK;
 }
 
+int fem_pattern_barrier_fault(fem_pattern_t p, int extra_arrivals, int max_polls) {
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  if (extra_arrivals < 0 || max_polls < 0) return set_error(FEM_ERR_ARG, "negative fault-injection setting");
+  p->P.bar_extra = extra_arrivals;
+  p->P.bar_polls = max_polls;
+  return FEM_OK;
+}
+
 int fem_pattern_force_path(fem_pattern_t p, int path, int tile_elems, fem_stream_t stream) {
   if (!p) return set_error(FEM_ERR_ARG, "null pattern");
   Pattern& P = p->P;

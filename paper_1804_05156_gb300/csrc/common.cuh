@@ -131,6 +131,8 @@ struct Pattern {
   int* work_counter = nullptr; // [4] device counters: [0] blocked persistent launch, [1..3] fused tile launch
   uint8_t* bd_whole = nullptr;  // [N] whole-boundary vertex mask, computed on first request
   struct HostExec* hx = nullptr;  // streams and device buffers of fem_assemble_host, made on first use
+  int bar_extra = 0;           // fault injection: arrivals the fused grid barrier waits for beyond the grid
+  int bar_polls = 0;           // fault injection: poll limit of the fused grid barrier (0: the default)
 };
 void free_host_exec(Pattern& P);
 // (Re)build P->blk, halving the block size until the packed limits hold (blk.ok false if they never do).

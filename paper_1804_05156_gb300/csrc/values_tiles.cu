@@ -52,6 +52,8 @@ struct TileArgs {
   const double* u;      // kOpApply: the vector A is applied to [N]
   const uint8_t* isbd;  // kOpApply: eliminated (Dirichlet) vertices, nullable
   int u_off;            // kOpApply: shared-memory offset of the staged u values
+  int bar_extra;        // fused form: arrivals the grid barrier waits for beyond the launch's CTAs (0)
+  int bar_polls;        // fused form: polls before the grid barrier gives up
 };
 
 struct RowArgs {
@@ -378,12 +380,13 @@ __global__ void __launch_bounds__(TE, (D == 3 ? 768 : 1280) / TE)
     __threadfence();
     atomicAdd(&ctr[1], 1);
     int polls = 0;
-    while (*(volatile int*)&ctr[1] < (int)gridDim.x && polls < kBarrierPolls) {
+    const int target = (int)gridDim.x + a.bar_extra;
+    while (*(volatile int*)&ctr[1] < target && polls < a.bar_polls) {
       __nanosleep(64);
       ++polls;
     }
     __threadfence();
-    s_item = (polls < kBarrierPolls) ? 0 : -1;
+    s_item = (polls < a.bar_polls) ? 0 : -1;
   }
   __syncthreads();
   if (s_item < 0) {
@@ -457,6 +460,8 @@ int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_
   a.opk = opk;
   a.u = u;
   a.isbd = isbd;
+  a.bar_extra = P->bar_extra;
+  a.bar_polls = P->bar_polls > 0 ? P->bar_polls : kBarrierPolls;
   if (op != kOpStiffness) {
     b = nullptr;  // operators give values only
     f_kind = FEM_F_CONST;

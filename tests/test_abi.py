@@ -59,6 +59,7 @@ def test_host_side_argument_checks(libpath):
     assert L.fem_mesh_build_pattern(2, 10, 5, C.c_void_p(16), None, None) == fa.FEM_ERR_ARG  # null out
     assert L.fem_assemble(None, None, None, 0, None, None, None, 0, None) == fa.FEM_ERR_ARG
     assert L.fem_batch_plan(2, 0, None, None, None, C.byref(h), None) == fa.FEM_ERR_ARG
+    assert L.fem_pattern_barrier_fault(None, 1, 16) == fa.FEM_ERR_ARG
     assert L.fem_launch_count() >= 0
 
 

@@ -187,6 +187,69 @@ def test_all_value_paths_give_the_same_bits(case):
     assert_close_scaled(host(v2), vo, so)
 
 
+@pytest.mark.parametrize("d", [2, 3])
+def test_fused_grid_barrier_gives_up_with_a_timeout(d):
+    """The fused launch's grid barrier waits for one CTA more than the launch has (an arrival that never
+    comes, set by fem_pattern_barrier_fault) and a short poll limit: every CTA gives up, the device error
+    word reads FEM_ERR_TIMEOUT, and the context stays usable: with the defaults restored the next launch
+    on the same pattern gives the oracle's values."""
+    d_, node, elem, k, _ = mesh_case("sq37p" if d == 2 else "kuhn7s")
+    N = node.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    fa.fem_pattern_set_locality(p, dev(node))
+    fa.fem_pattern_force_path(p, fa.FEM_PATH_TILES_FUSED, 128)
+    fa.fem_pattern_barrier_fault(p, 1, 4096)
+    val, b = fa.assemble(p, dev(node), dev(k), fa.FEM_F_SINPROD, None, fa.FEM_DETERMINISTIC)
+    with pytest.raises(fa.FemError) as e:
+        fa.get_error()
+    assert e.value.code == fa.FEM_ERR_TIMEOUT
+    fa.get_error()  # the word was cleared by the read
+    fa.fem_pattern_barrier_fault(p, 0, 0)
+    val, b = fa.assemble(p, dev(node), dev(k), fa.FEM_F_SINPROD, None, fa.FEM_DETERMINISTIC)
+    fa.get_error()
+    _, _, vo, so = oracle.assemble(d, node, elem, k)
+    assert_close_scaled(host(val), vo, so)
+    bo = oracle.rhs(d, node, elem, oracle.F_SINPROD)
+    assert_close_scaled(host(b), bo, np.abs(bo) + 1e-300, what="rhs")
+    with pytest.raises(fa.FemError) as e:
+        fa.fem_pattern_barrier_fault(p, -1, 0)
+    assert e.value.code == fa.FEM_ERR_ARG
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_row_shards_on_the_gpu_give_the_global_rows_bit_for_bit(d):
+    """The row-ownership sharding of the multi-rank path, run through the CUDA library on one GPU: each
+    shard's sub-mesh (every element touching the rank's vertex range, global order kept) gets its own
+    pattern, locality plan and assembly, and its owned rows equal the whole-mesh GPU rows bit for bit
+    (pattern, values, load vector) for 2 and 3 ranks: no exchange of data is needed."""
+    from paper_1804_05156_gb300 import partition
+    m = meshgen.square_mesh(48, 0.2, 61, permute=True) if d == 2 else meshgen.kuhn_mesh(9, 0.1, 62)
+    node, elem = m["node"], m["elem"]
+    N, NT = node.shape[0], elem.shape[0]
+    k = meshgen.lognormal(63, meshgen.TAG_COEF, NT)
+    p = fa.Pattern(dev(elem), N)
+    fa.fem_pattern_set_locality(p, dev(node))
+    val, b = fa.assemble(p, dev(node), dev(k), fa.FEM_F_SINPROD, None, fa.FEM_DETERMINISTIC)
+    fa.get_error()
+    rp, col, val, b = host(p.row_ptr), host(p.col_idx), host(val), host(b)
+    for P in (2, 3):
+        got = []
+        for lo, hi in partition.row_ranges(N, P, elem):
+            sh = partition.shard_mesh(elem, lo, hi)
+            sub_node = np.ascontiguousarray(node[sh["vert_ids"]])
+            q = fa.Pattern(dev(sh["elem_local"]), sub_node.shape[0])
+            fa.fem_pattern_set_locality(q, dev(sub_node))
+            sv, sb = fa.assemble(q, dev(sub_node), dev(k[sh["elem_ids"]]), fa.FEM_F_SINPROD, None,
+                                 fa.FEM_DETERMINISTIC)
+            fa.get_error()
+            got.append(partition.owned_rows(sh, host(q.row_ptr), host(q.col_idx), host(sv), host(sb)))
+        assert np.array_equal(np.concatenate([g[0] for g in got]), np.arange(N))
+        assert np.array_equal(np.concatenate([g[1] for g in got]), np.diff(rp))
+        assert np.array_equal(np.concatenate([g[2] for g in got]), col)
+        assert np.array_equal(np.concatenate([g[3] for g in got]).view(np.uint64), val.view(np.uint64))
+        assert np.array_equal(np.concatenate([g[4] for g in got]).view(np.uint64), b.view(np.uint64))
+
+
 def test_long_rows_take_the_tile_path():
     """A vertex with 40 neighbours (row of 41 entries) is beyond the owner-computes records (32 per
     row) but within the tile path's (256)."""
@@ -861,3 +924,76 @@ def test_gpu_system_solves_poisson_at_second_order(d):
         errs.append(float(np.abs(u - np.prod(np.sin(np.pi * node), axis=1) / (d * np.pi ** 2)).max()))
     rates = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
     assert all(3.5 < r < 4.5 for r in rates), (errs, rates)
+
+
+# ---- reduced solve by matrix-free conjugate gradients (Sec. 3.3) ----------------------------------------
+
+def _cg_case(d, n, seed):
+    m = meshgen.square_mesh(n, 0.2, seed, permute=True) if d == 2 else meshgen.kuhn_mesh(n, 0.1, seed)
+    node, elem = m["node"], m["elem"]
+    k = meshgen.lognormal(seed, meshgen.TAG_COEF, elem.shape[0])
+    return node, elem, k
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_cg_matches_the_direct_reduced_solve(d):
+    """fem_cg_solve (matrix-free operator, nonzero g_D, lognormal k, sine-product load from the GPU)
+    against the oracle's direct solve of the same reduced system: boundary values exact, free values
+    within the CG tolerance; a second solve gives the same bits and iteration count."""
+    node, elem, k = _cg_case(d, 24 if d == 2 else 6, 91 + d)
+    N = node.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    fa.fem_pattern_set_locality(p, dev(node))
+    val, b = fa.assemble(p, dev(node), dev(k), fa.FEM_F_SINPROD)
+    fa.get_error()
+    isbd = torch.empty(N, dtype=torch.uint8, device="cuda")
+    fa.fem_boundary_nodes(p, None, isbd)
+    gD = 0.5 + node @ np.arange(1.0, d + 1.0)
+    u, it, rel = fa.fem_cg_solve(p, dev(node), dev(k), isbd, b, dev(gD), rtol=1e-13)
+    fa.get_error()
+    assert 0 < it < 10 * N and rel <= 1e-13
+    rp, col, vo, _ = oracle.assemble(d, node, elem, k)
+    uo = oracle.solve_reduced(rp, col, vo, host(b), host(isbd), gD)
+    bd = host(isbd).astype(bool)
+    assert np.array_equal(host(u)[bd], gD[bd])
+    assert np.abs(host(u) - uo).max() <= 1e-10 * np.abs(uo).max(), np.abs(host(u) - uo).max()
+    u2, it2, rel2 = fa.fem_cg_solve(p, dev(node), dev(k), isbd, b, dev(gD), rtol=1e-13)
+    assert torch.equal(u, u2) and it == it2 and rel == rel2
+    # a zero iteration budget leaves the lift; an exact start stops at once
+    u0, it0, _ = fa.fem_cg_solve(p, dev(node), dev(k), isbd, b, dev(gD), max_iter=0)
+    assert it0 == 0 and np.array_equal(host(u0)[bd], gD[bd]) and not host(u0)[~bd].any()
+    uz, itz, relz = fa.fem_cg_solve(p, dev(node), dev(k), isbd, torch.zeros_like(b), None)
+    assert itz == 0 and relz == 0.0 and not host(uz).any()
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_cg_solution_converges_at_second_order(d):
+    """-Laplace u = sin-product with u = 0 on the boundary, solved on the GPU by the load vector and the
+    matrix-free CG: the nodal error against f / (d pi^2) falls by about 4 per halving of h."""
+    errs = []
+    for n in ((8, 16, 32) if d == 2 else (4, 8, 16)):
+        m = meshgen.square_mesh(n) if d == 2 else meshgen.kuhn_mesh(n)
+        node, elem = m["node"], m["elem"]
+        N = node.shape[0]
+        p = fa.Pattern(dev(elem), N)
+        _, b = fa.assemble(p, dev(node), None, fa.FEM_F_SINPROD)
+        isbd = torch.empty(N, dtype=torch.uint8, device="cuda")
+        fa.fem_boundary_nodes(p, None, isbd)
+        u, it, rel = fa.fem_cg_solve(p, dev(node), None, isbd, b, None, rtol=1e-12)
+        fa.get_error()
+        errs.append(float(np.abs(host(u) - np.prod(np.sin(np.pi * node), axis=1) / (d * np.pi ** 2)).max()))
+    rates = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert all(3.5 < r < 4.5 for r in rates), (errs, rates)
+
+
+def test_cg_reports_breakdown():
+    """Vertices that no element touches have a zero operator row: with a nonzero right side there, the
+    first step finds p.Ap = 0 and the call reports the breakdown (FEM_ERR_STATE) instead of dividing by 0."""
+    p = fa.Pattern(torch.zeros((0, 3), dtype=torch.int32, device="cuda"), 4)
+    node = dev(np.zeros((4, 2)))
+    isbd = dev(np.array([1, 0, 0, 0], np.uint8))
+    b = dev(np.ones(4))
+    with pytest.raises(fa.FemError) as e:
+        fa.fem_cg_solve(p, node, None, isbd, b, None, max_iter=10)
+    assert e.value.code == fa.FEM_ERR_STATE
+    assert b"breakdown" in fa.lib().fem_last_error_string()

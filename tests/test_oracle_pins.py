@@ -806,6 +806,32 @@ def test_rule_sine_product_branch(d):
 # --- the whole method: assemble, eliminate the Dirichlet rows, solve ---------------------------------
 
 @pytest.mark.parametrize("d", [2, 3])
+def test_reduced_solve_by_lift_equals_eliminated_solve_and_reproduces_linear_data(d):
+    """Sec. 3.3 two ways: oracle.solve_reduced (lift b - A u_D, solve on freeNode) and the symmetric
+    eliminated system of oracle.dirichlet solved whole give the same u; with f = 0, k = 1 and a linear g_D
+    both reproduce the linear function (P1 contains it)."""
+    sp = pytest.importorskip("scipy.sparse")
+    spla = pytest.importorskip("scipy.sparse.linalg")
+    m = meshgen.square_mesh(9, 0.2, 71, True) if d == 2 else meshgen.kuhn_mesh(4, 0.1, 71)
+    node, elem = m["node"], m["elem"]
+    N, NT = node.shape[0], elem.shape[0]
+    k = meshgen.lognormal(71, 3, NT)
+    isbd = oracle.boundary(d, N, elem)
+    gD = 1.0 + node @ np.arange(1.0, d + 1.0)
+    rp, col, val, _ = oracle.assemble(d, node, elem, k)
+    b = oracle.rhs(d, node, elem, oracle.F_SINPROD)
+    u1 = oracle.solve_reduced(rp, col, val, b, isbd, gD)
+    v2, b2, _ = oracle.dirichlet(rp, col, val, b, isbd, gD)
+    u2 = spla.spsolve(sp.csr_matrix((v2, col, rp), shape=(N, N)).tocsc(), b2)
+    assert np.allclose(u1, u2, rtol=0, atol=1e-12 * np.abs(u2).max())
+    assert np.array_equal(u1[isbd.astype(bool)], gD[isbd.astype(bool)])
+    rp, col, val1, _ = oracle.assemble(d, node, elem, None)
+    ul = oracle.solve_reduced(rp, col, val1, np.zeros(N), isbd, gD)
+    assert np.allclose(ul, gD, rtol=0, atol=1e-12 * np.abs(gD).max())
+
+
+
+@pytest.mark.parametrize("d", [2, 3])
 def test_poisson_solution_converges_at_second_order(d):
     """-Laplace u = f on the unit square / cube with u = 0 on the boundary and f the sine product: the
     exact solution is f / (d pi^2). Solving the oracle's eliminated system on uniform meshes halving h,
