@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libfemasm.so")
 FEM_OK = 0
 FEM_ERR_ARG, FEM_ERR_INDEX, FEM_ERR_DEGENERATE, FEM_ERR_CUDA, FEM_ERR_OOM, FEM_ERR_TIMEOUT, FEM_ERR_STATE = (
     -1, -2, -3, -4, -5, -6, -7)
+FEM_ERR_RANGE = -8
 FEM_DETERMINISTIC, FEM_ATOMIC = 0, 1
 FEM_F_CONST, FEM_F_SINPROD, FEM_F_QPVALUES = 0, 1, 2
 FEM_PATH_TWO_PASS, FEM_PATH_BLOCKED, FEM_PATH_TILES, FEM_PATH_TILES_FUSED = 0, 1, 2, 3

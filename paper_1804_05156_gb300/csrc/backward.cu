@@ -26,29 +26,31 @@ const float4* sincos_table_device();  // values_blocked.cu
 
 namespace {
 
-// Adjoint of one element: out[m][c] = dL/dx_{m,c} contributions and gkv = dL/dk_t, from the exact
-// coordinate splits V, the coefficient kt, the symmetrised loss weights Ws = W + W^T (with_w) and the
-// load-vector weights rv of the element's vertices (with_r).
+// Adjoint of one element: out[m][c] = dL/dx_{m,c} contributions and gkv = dL/dk_t, from the staged
+// coordinates V, the coefficient kt, the symmetrised loss weights Ws = W + W^T (with_w) and the
+// load-vector weights rv of the element's vertices (with_r). Returns FEM_OK, FEM_ERR_DEGENERATE or
+// FEM_ERR_RANGE (element_df.cuh).
+// The geometry is that of the value kernels: FP64 edges, the element scaled by 2^-s, so that g_i, |tau|
+// and every product of them stay of order one; each term is scaled back by its degree of homogeneity
+// in the coordinates: dL/dk and the stiffness part of dL/dx by 2^(d-2)s and 2^(d-3)s, the load part's
+// |tau| g_m term by 2^(d-1)s and its |tau| grad f term by 2^ds.
 // Stiffness part in the form that needs the fewest products: h_j = sum_i Ws_ij g_i, then
 // S = (1/2) sum_j h_j . g_j and sum_i Q_im g_i = sum_j (g_j . g_m) h_j.
 template <int D>
-__device__ __forceinline__ bool element_adjoint(const VtxDF<D>* const (&V)[D + 1], int t, df2 kt, bool with_w,
-                                                const df2 (&Ws)[D + 1][D + 1], bool with_r, const df2 (&rv)[D + 1],
-                                                int f_kind, const double* __restrict__ f_arg,
-                                                const float4* __restrict__ tab, df2 (&out)[D + 1][D], df2& gkv) {
+__device__ __forceinline__ int element_adjoint(const VtxDF<D>* const (&V)[D + 1], int t, df2 kt, bool with_w,
+                                               const df2 (&Ws)[D + 1][D + 1], bool with_r, const df2 (&rv)[D + 1],
+                                               int f_kind, const double* __restrict__ f_arg,
+                                               const float4* __restrict__ tab, df2 (&out)[D + 1][D], df2& gkv) {
   constexpr int D1 = D + 1;
-  // scaled inward normals n_i and the positive measure |tau| (d! |tau| = signed 2-D area x 2, 3-D vol x 6)
+  // scaled inward normals n_i and the positive measure |tau| (d! |tau| = signed 2-D area x 2, 3-D vol x 6),
+  // in the element's frame scaled by 2^-s
   df2 n[D1][D];
-  df2 dmeas;  // d! |tau|
+  df2 dmeas;  // d! |tau| times 2^-ds
+  int s;
   if constexpr (D == 2) {
     df2 ev[3][2];
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      ev[0][m] = f3_diff(V[2]->x[m], V[1]->x[m]);
-      ev[1][m] = f3_diff(V[0]->x[m], V[2]->x[m]);
-      ev[2][m] = f3_diff(V[1]->x[m], V[0]->x[m]);
-    }
-    dmeas = df_sub(df_mul(ev[1][0], ev[2][1]), df_mul(ev[1][1], ev[2][0]));
+    s = tri_edges(V, ev);
+    dmeas = df_dot2m(ev[1][0], ev[2][1], ev[1][1], ev[2][0]);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       n[i][0] = df_neg(ev[i][1]);
@@ -56,23 +58,14 @@ __device__ __forceinline__ bool element_adjoint(const VtxDF<D>* const (&V)[D + 1
     }
   } else {
     df2 ed[3][3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-#pragma unroll
-      for (int m = 0; m < 3; ++m) ed[q][m] = f3_diff(V[q + 1]->x[m], V[0]->x[m]);
-    df_cross(ed[1], ed[2], n[1]);
-    df_cross(ed[2], ed[0], n[2]);
-    df_cross(ed[0], ed[1], n[3]);
-    df2 u[3], v[3];
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      u[m] = f3_diff(V[3]->x[m], V[1]->x[m]);
-      v[m] = f3_diff(V[2]->x[m], V[1]->x[m]);
-    }
-    df_cross(u, v, n[0]);
+    s = tet_frame(V, ed, n);
     dmeas = df_dot<3>(n[3], ed[2]);
   }
-  const bool ok = dmeas.h > 0.0f && dmeas.h < INFINITY;
+  int st = (dmeas.h > 0.0f && dmeas.h < INFINITY) ? FEM_OK : FEM_ERR_DEGENERATE;
+  const int eA = (D - 3) * s, eK = (D - 2) * s, e1 = (D - 1) * s, e2 = D * s;
+  if (!(scale_in_range(eA) && scale_in_range(e2))) st = worst(st, FEM_ERR_RANGE);
+  const int sA = scale_in_range(eA) ? eA : 0, sK = scale_in_range(eK) ? eK : 0;
+  const int s1 = scale_in_range(e1) ? e1 : 0, s2 = scale_in_range(e2) ? e2 : 0;
   const df2 inv = df_recip(dmeas);
   const df2 meas = (D == 2) ? df_scale(dmeas, 0.5f) : df_mul(dmeas, df2{0.1666666716337204f, -4.9670538793e-09f});
   df2 g[D1][D];
@@ -113,7 +106,7 @@ __device__ __forceinline__ bool element_adjoint(const VtxDF<D>* const (&V)[D + 1
       S2 = df_dot<D1 * D>(A, B);
     }
     const df2 S = df_scale(S2, 0.5f);
-    gkv = df_mul(meas, S);
+    gkv = df_ldexp(df_mul(meas, S), sK);
     const df2 km = df_mul(kt, meas);
     df2 P[D1][D1];  // g_j . g_m (symmetric)
 #pragma unroll
@@ -136,7 +129,7 @@ __device__ __forceinline__ bool element_adjoint(const VtxDF<D>* const (&V)[D + 1
           A[j + 1] = df_neg(P[j][m]);
           B[j + 1] = h[j][c];
         }
-        out[m][c] = df_mul(km, df_dot<D1 + 1>(A, B));
+        out[m][c] = df_ldexp(df_mul(km, df_dot<D1 + 1>(A, B)), sA);
       }
   }
   if (with_r) {
@@ -166,7 +159,7 @@ __device__ __forceinline__ bool element_adjoint(const VtxDF<D>* const (&V)[D + 1
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-          for (int m = 0; m < 2; ++m) sc[i][m] = sincospi_half(V[i]->x[m], tab);
+          for (int m = 0; m < 2; ++m) sc[i][m] = sincospi_half(split3(V[i]->x[m]), tab);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const int u = (q + 1) % 3, v = (q + 2) % 3;
@@ -180,13 +173,13 @@ __device__ __forceinline__ bool element_adjoint(const VtxDF<D>* const (&V)[D + 1
         const df2 al = {0.58541017770767212f, 1.8917296174e-08f}, be = {0.13819660246372223f, -1.3387116971e-09f};
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-          const float nn = rintf(V[0]->x[m].a);
+          const float nn = rintf(lead_float(V[0]->x[m]));
+          const double nd = f2d_bits(nn);
           df2 y[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
-            y[i] = df_add(two_sum(V[i]->x[m].a, -nn), fast_two_sum(V[i]->x[m].b, V[i]->x[m].c));
+          for (int i = 0; i < 4; ++i) y[i] = df_from_double_shift(__dsub_rn(V[i]->x[m], nd), 0);
           const df2 sy = df_add(df_add(y[0], y[1]), df_add(y[2], y[3]));
-          const float sgn = (__float2int_rn(nn) & 1) ? -1.0f : 1.0f;
+          const float sgn = int_parity(nn) ? -1.0f : 1.0f;
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             df_sincospi(df_add(df_mul(be, sy), df_mul(df_sub(al, be), y[q])), tab, sn[q][m], cs[q][m]);
@@ -246,12 +239,20 @@ __device__ __forceinline__ bool element_adjoint(const VtxDF<D>* const (&V)[D + 1
     for (int m = 0; m < D1; ++m)
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        df2 v = df_mul(g[m][c], Rb);
-        if (f_kind == FEM_F_SINPROD) v = df_add(v, df_mul(wqd, df_add(df_mul(gs[c], lo), df_mul(gr[m][c], ld))));
-        out[m][c] = df_add(out[m][c], df_mul(meas, v));
+        // |tau| g_m Rb (degree d - 1) and |tau| sum_q w_q lambda_m(q) grad f(x_q) rl_q (degree d)
+        df2 v = df_ldexp(df_mul(meas, df_mul(g[m][c], Rb)), s1);
+        if (f_kind == FEM_F_SINPROD)
+          v = df_add(v, df_ldexp(df_mul(meas, df_mul(wqd, df_add(df_mul(gs[c], lo), df_mul(gr[m][c], ld)))), s2));
+        out[m][c] = df_add(out[m][c], v);
       }
   }
-  return ok;
+  if (!df_in_range(gkv)) st = worst(st, FEM_ERR_RANGE);
+#pragma unroll
+  for (int m = 0; m < D1; ++m)
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+      if (!df_in_range(out[m][c])) st = worst(st, FEM_ERR_RANGE);
+  return st;
 }
 
 // Ws = W + W^T of element t from the loss weights on its slots (pairs summed in FP64, then split)
@@ -289,21 +290,22 @@ __global__ void __launch_bounds__(128, 4) k_backward_df(const int32_t* __restric
 #pragma unroll
   for (int i = 0; i < D1; ++i)
 #pragma unroll
-    for (int m = 0; m < D; ++m) X[i].x[m] = split3(__ldg(node + (size_t)e[i] * D + m));
+    for (int m = 0; m < D; ++m) X[i].x[m] = __ldg(node + (size_t)e[i] * D + m);
   df2 Ws[D1][D1], rv[D1];
   if (w) sym_weights<D>(slot, NT, t, w, Ws);
   if (r) {
 #pragma unroll
     for (int i = 0; i < D1; ++i) rv[i] = df_from_double_fast(__ldg(r + e[i]));
   }
-  const df2 kt = k ? df_from_double_fast(__ldg(k + t)) : df2{1.0f, 0.0f};
+  int st = FEM_OK;
+  const df2 kt = k ? coef_df(__ldg(k + t), st) : df2{1.0f, 0.0f};
   const VtxDF<D>* V[D1];
 #pragma unroll
   for (int i = 0; i < D1; ++i) V[i] = &X[i];
   df2 out[D1][D], gkv;
-  if (!element_adjoint<D>(reinterpret_cast<const VtxDF<D>* const(&)[D1]>(V), t, kt, w != nullptr, Ws, r != nullptr,
-                          rv, f_kind, f_arg, tab, out, gkv))
-    report(err, FEM_ERR_DEGENERATE);
+  st = worst(st, element_adjoint<D>(reinterpret_cast<const VtxDF<D>* const(&)[D1]>(V), t, kt, w != nullptr, Ws,
+                                    r != nullptr, rv, f_kind, f_arg, tab, out, gkv));
+  if (st != FEM_OK) report(err, st);
   if (gk) gk[t] = df_to_double(gkv);
 #pragma unroll
   for (int m = 0; m < D1; ++m)
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(TE, 512 / TE) k_backward_tiles(
     const int R = __ldg(vlist + v0 + v);
     VtxDF<D> x;
 #pragma unroll
-    for (int m = 0; m < D; ++m) x.x[m] = split3(__ldg(node + (size_t)R * D + m));
+    for (int m = 0; m < D; ++m) x.x[m] = __ldg(node + (size_t)R * D + m);
     xs[v] = x;
   }
   __syncthreads();
@@ -351,14 +353,15 @@ __global__ void __launch_bounds__(TE, 512 / TE) k_backward_tiles(
 #pragma unroll
     for (int i = 0; i < D1; ++i) rv[i] = df_from_double_fast(__ldg(r + __ldg(vlist + v0 + lv[i])));
   }
-  const df2 kt = k ? df_from_double_fast(__ldg(k + t)) : df2{1.0f, 0.0f};
+  int st = FEM_OK;
+  const df2 kt = k ? coef_df(__ldg(k + t), st) : df2{1.0f, 0.0f};
   const VtxDF<D>* V[D1];
 #pragma unroll
   for (int i = 0; i < D1; ++i) V[i] = &xs[lv[i]];
   df2 out[D1][D], gkv;
-  if (!element_adjoint<D>(reinterpret_cast<const VtxDF<D>* const(&)[D1]>(V), t, kt, w != nullptr, Ws, r != nullptr,
-                          rv, f_kind, f_arg, tab, out, gkv))
-    report(err, FEM_ERR_DEGENERATE);
+  st = worst(st, element_adjoint<D>(reinterpret_cast<const VtxDF<D>* const(&)[D1]>(V), t, kt, w != nullptr, Ws,
+                                    r != nullptr, rv, f_kind, f_arg, tab, out, gkv));
+  if (st != FEM_OK) report(err, st);
   if (gk) gk[t] = df_to_double(gkv);
 #pragma unroll
   for (int m = 0; m < D1; ++m) {

@@ -159,6 +159,57 @@ __device__ __forceinline__ df2 df_from_double_fast(double x) {
   return fast_two_sum(a, sign ? -r : r);
 }
 
+// ---- element-frame conversions ----------------------------------------------------------------------
+
+// |x| as an ordered integer: the IEEE high word without the sign (compares like |x| to 2^-20 relative).
+__device__ __forceinline__ uint32_t abs_hiword(double x) { return (uint32_t)__double2hiint(x) & 0x7fffffffu; }
+
+// Unbiased exponent of the largest magnitude among doubles whose abs_hiword maximum is m (m = 0: all
+// zero, gives -1023).
+__device__ __forceinline__ int exponent_of_hiword(uint32_t m) { return (int)(m >> 20) - 1023; }
+
+// x * 2^-s as a float pair, from the IEEE bits with integer operations only: the leading part is the
+// top 24 significant bits (truncated, exponent shifted by s), the trailing part the remaining 29 bits
+// through one int32 -> float conversion (rounded to 24 bits), so the pair carries x 2^-s to 2^-47
+// relative. Both parts have the sign of x and |lo| < ulp(hi). Gives 0 when x 2^-s is below 2^-126 (for
+// the element's own edges, which are scaled so that the largest component is in [1, 2), that is below
+// 2^-126 of the element's size).
+__device__ __forceinline__ df2 df_from_double_shift(double x, int s) {
+  const uint32_t hw = (uint32_t)__double2hiint(x), lw = (uint32_t)__double2loint(x);
+  const int E = (int)((hw >> 20) & 0x7ffu);
+  const int fe = E - s - 896;  // float exponent field of the leading part
+  const uint32_t sg = hw & 0x80000000u;
+  df2 r = {0.0f, 0.0f};
+  if (E != 0 && fe > 0 && fe < 255) {
+    r.h = __uint_as_float(sg | ((uint32_t)fe << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+    const int pe = fe - 52;  // float exponent field of the weight of the double's last bit
+    if (pe > 0) r.l = __fmul_rn(__uint2float_rn(lw & 0x1fffffffu), __uint_as_float(sg | ((uint32_t)pe << 23)));
+  }
+  return r;
+}
+
+// v * 2^e for a float pair (exact while both parts stay normal); e in [-126, 127].
+__device__ __forceinline__ df2 df_ldexp(df2 v, int e) {
+  const float p = __int_as_float((e + 127) << 23);
+  return {__fmul_rn(v.h, p), __fmul_rn(v.l, p)};
+}
+
+// The range the float-float results keep their precision in. A result's trailing part may be far below
+// its leading part; once it leaves the normal float range (2^-126) it is lost, an absolute error of up to
+// 2^-126, which is below 2^-42 of a result of magnitude 2^-84 or more. So a result is in range when its
+// leading part is 0 or of magnitude in [2^-84, 2^120] (sums of a row's contributions then stay finite);
+// a product of nonzero factors must not be 0 (it flushed). Scale exponents (the power of two an element's
+// normalised result is multiplied by) are kept within [-100, 100].
+__device__ __forceinline__ bool df_in_range(df2 v) {
+  const float a = fabsf(v.h);
+  return a <= 0x1p120f && (a == 0.0f || a >= 0x1p-84f);
+}
+__device__ __forceinline__ bool df_prod_in_range(df2 v, bool nonzero_factors) {
+  const float a = fabsf(v.h);
+  return a <= 0x1p120f && (a >= 0x1p-84f || (a == 0.0f && !nonzero_factors));
+}
+__device__ __forceinline__ bool scale_in_range(int e) { return e >= -100 && e <= 100; }
+
 // xj - xi as df, from exact three-float splits: the difference of the leading parts and of the
 // middle parts are formed exactly with two-sum, so the result is accurate to ~2^-47 of |xj - xi|
 // however close xi and xj are.
@@ -216,7 +267,7 @@ __device__ __forceinline__ void df_sincospi_small(df2 r, const float4* __restric
   const float tail = __fadd_rn(-0.5f * sq.l, __fmul_rn(__fmul_rn(t2, t2), 1.0f / 24.0f));
   const df2 cs = fast_two_sum(one_m.h, __fadd_rn(one_m.l, tail));
   const int k = (int)kf;
-  const int ak = k < 0 ? -k : k;
+  const int ak = min(k < 0 ? -k : k, kSinTabN);  // |r| <= 1/2 gives |k| <= 1024; the bound keeps the read in the table
   const float4 e = tab[ak];
   df2 Sk = {e.x, e.y}, Ck = {e.z, e.w};
   if (k < 0) Sk = df_neg(Sk);

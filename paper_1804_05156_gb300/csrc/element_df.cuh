@@ -2,15 +2,23 @@
 //
 // Same formulas as element.cuh (Sec. 3.1.3, eq. (dlambda) and the a_ij formula below it; Sec. 3.2),
 // arranged for the FP32 pipe:
-//  * coordinates arrive as exact three-float splits, so every edge vector is formed to ~2^-47 of its
-//    own length (f3_diff);
+//  * staged vertices are the coordinates as doubles, and every edge vector is one FP64 subtraction of
+//    its own two endpoints: rounded once, to 2^-53 of the edge however far the element is from the
+//    origin (the edge the FP64 formula itself starts from);
+//  * the element is then scaled by 2^-s, s the exponent of its largest edge component, as the edges
+//    are converted to float pairs (df_from_double_shift, integer operations only): every product below
+//    is of order one whatever the element's size, and each result is scaled back exactly by the power
+//    of two its degree of homogeneity in the coordinates gives (2-D stiffness 0, 3-D stiffness 1,
+//    measure d);
 //  * 2-D: ve_0 = x3 - x2, ve_1 = x1 - x3, ve_2 = x2 - x1 (1-based vertices), 2 area = ve_1 x ve_2,
 //    a_ij = s ve_i.ve_j, s = k / (2 |2 area|) (the paper's abs() of the area);
 //  * 3-D: with e_m = x_{m+1} - x_1, n_1 = e_2 x e_3, n_2 = e_3 x e_1, n_3 = e_1 x e_2 (the paper's faces
-//    [1 3 4], [1 4 2], [1 2 3]) and n_0 = (x_4 - x_2) x (x_3 - x_2) (face [2 4 3]); every edge is
-//    formed from its own endpoints, so each normal's rounding stays relative to its own face; volume = n_3 . e_3 / 6 (signed);
-//    a_ij = s n_i.n_j, s = k / (36 volume);
+//    [1 3 4], [1 4 2], [1 2 3]) and n_0 = (x_4 - x_2) x (x_3 - x_2) (face [2 4 3]); every edge is formed
+//    from its own endpoints, so each normal's rounding stays relative to its own face; 6 volume =
+//    n_3 . e_3 (signed); a_ij = s n_i.n_j, s = k / (36 volume);
 //  * diagonals are minus the off-diagonal row sums (sum_i n_i = 0).
+// The element routines return FEM_OK, FEM_ERR_DEGENERATE (zero 2-D area, non-positive 3-D volume) or
+// FEM_ERR_RANGE (a coefficient, scale or result outside the float-float range, see dfloat.cuh).
 #pragma once
 
 #include "dfloat.cuh"
@@ -18,11 +26,10 @@
 
 namespace fem {
 
-// Staged vertex: exact splits of the coordinates, and for the sine-product load the values
-// sin(pi x/2), cos(pi x/2) of each coordinate (df).
+// Staged vertex: the coordinates.
 template <int D>
 struct __align__(16) VtxDF {  // 16-byte aligned: staged vertices are read with 128-bit accesses
-  f3 x[D];
+  double x[D];
 };
 struct __align__(16) SC {
   df2 s, c;
@@ -36,16 +43,32 @@ struct LocalDF {
   df2 bt[D + 1];
 };
 
-// sin(pi x/2) and cos(pi x/2) from the exact split of x: x/2 = n + r with n = rint(a/2), r exact to
-// ~2^-47 of |r| (so values near the zeros of the sine keep their relative accuracy).
+__device__ __forceinline__ int worst(int st, int code) { return st != FEM_OK ? st : code; }
+
+// A per-element coefficient (k, c) as a float pair: the exact split for |v| in [2^-80, 2^96] (or 0);
+// anything else (outside the float-float range, or not finite) sets FEM_ERR_RANGE.
+__device__ __forceinline__ df2 coef_df(double v, int& st) {
+  const int E = (int)((abs_hiword(v) >> 20) & 0x7ffu);
+  if (v != 0.0 && (E < 1023 - 80 || E > 1023 + 96)) st = worst(st, FEM_ERR_RANGE);
+  return df_from_double(v);
+}
+
+__device__ __forceinline__ int int_parity(float n) { return fabsf(n) < 16777216.0f ? (__float2int_rn(n) & 1) : 0; }
+
+// sin(pi x/2) and cos(pi x/2) from the exact split x = a + b + c: each half-part is reduced by its own
+// nearest integer (exactly: every remainder is at most 1/2), the three remainders are added in float-float
+// and reduced once more, so x/2 = n + r with |r| <= 1/2 and r exact to ~2^-47 of |r| for any x (values near
+// the zeros of the sine keep their relative accuracy; large x keep every bit of x).
 __device__ __forceinline__ SC sincospi_half(const f3& x, const float4* __restrict__ tab) {
   const float ah = 0.5f * x.a, bh = 0.5f * x.b, ch = 0.5f * x.c;
-  const float n = rintf(ah);
-  const df2 r0 = two_sum(__fsub_rn(ah, n), bh);
-  const df2 r = fast_two_sum(r0.h, __fadd_rn(r0.l, ch));
+  const float na = rintf(ah), nb = rintf(bh), nc = rintf(ch);
+  const df2 r0 = two_sum(__fsub_rn(ah, na), __fsub_rn(bh, nb));
+  df2 r = df_add(r0, df2{__fsub_rn(ch, nc), 0.0f});
+  const float n3 = rintf(r.h);
+  r = fast_two_sum(__fsub_rn(r.h, n3), r.l);
   SC o;
   df_sincospi_small(r, tab, o.s, o.c);
-  if (__float2int_rn(n) & 1) {
+  if ((int_parity(na) + int_parity(nb) + int_parity(nc) + int_parity(n3)) & 1) {
     o.s = df_neg(o.s);
     o.c = df_neg(o.c);
   }
@@ -55,26 +78,97 @@ __device__ __forceinline__ SC sincospi_half(const f3& x, const float4* __restric
 // sin(pi (u + v)/2) = sin(pi u/2) cos(pi v/2) + cos(pi u/2) sin(pi v/2)
 __device__ __forceinline__ df2 sin_mid(const SC& u, const SC& v) { return df_add(df_mul(u.s, v.c), df_mul(u.c, v.s)); }
 
-// want_diag = false leaves L.a[0..2] (the diagonals) unset, for callers that re-form them.
-__device__ __forceinline__ bool element_df2(const VtxDF<2>* const (&V)[3], const SC* const (&S)[3], df2 kt, bool want_a,
-                                            bool want_b, int f_kind, df2 fconst, const double* __restrict__ f_arg,
-                                            int t, LocalDF<2>& L, bool want_diag = true) {
-  // side vectors ve_i (side opposite vertex i), each formed from its own endpoints
-  df2 e[3][2];
+// x - n as a float pair for an integer n near x, and the parity of n: n = rint of the leading float of
+// x (truncated), the subtraction in FP64 (rounded once, to 2^-53 of the difference), so sin(pi x) =
+// (-1)^n sin(pi (x - n)) keeps its relative accuracy next to the integers. Coordinates up to 2^96.
+__device__ __forceinline__ float lead_float(double x) {
+  const uint32_t hw = (uint32_t)__double2hiint(x), lw = (uint32_t)__double2loint(x);
+  const int fe = (int)((hw >> 20) & 0x7ffu) - 896;
+  return (fe > 0 && fe < 255) ? __uint_as_float((hw & 0x80000000u) | ((uint32_t)fe << 23) | ((hw & 0xfffffu) << 3) |
+                                                (lw >> 29))
+                              : 0.0f;
+}
+
+// ---- element frames: FP64 edges, scaled by 2^-s --------------------------------------------------
+
+// Triangle: side vectors ve_i (opposite vertex i) as float pairs scaled by 2^-s; returns s.
+__device__ __forceinline__ int tri_edges(const VtxDF<2>* const (&V)[3], df2 (&e)[3][2]) {
+  double ed[3][2];
 #pragma unroll
   for (int m = 0; m < 2; ++m) {
-    e[0][m] = f3_diff(V[2]->x[m], V[1]->x[m]);
-    e[1][m] = f3_diff(V[0]->x[m], V[2]->x[m]);
-    e[2][m] = f3_diff(V[1]->x[m], V[0]->x[m]);
+    ed[0][m] = __dsub_rn(V[2]->x[m], V[1]->x[m]);
+    ed[1][m] = __dsub_rn(V[0]->x[m], V[2]->x[m]);
+    ed[2][m] = __dsub_rn(V[1]->x[m], V[0]->x[m]);
   }
-  const df2 a2 = df_dot2m(e[1][0], e[2][1], e[1][1], e[2][0]);  // twice the signed area
+  uint32_t mx = 0;
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int m = 0; m < 2; ++m) mx = max(mx, abs_hiword(ed[q][m]));
+  const int s = exponent_of_hiword(mx);
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int m = 0; m < 2; ++m) e[q][m] = df_from_double_shift(ed[q][m], s);
+  return s;
+}
+
+__device__ __forceinline__ void df_cross(const df2 (&u)[3], const df2 (&v)[3], df2 (&o)[3]) {
+  o[0] = df_dot2m(u[1], v[2], u[2], v[1]);
+  o[1] = df_dot2m(u[2], v[0], u[0], v[2]);
+  o[2] = df_dot2m(u[0], v[1], u[1], v[0]);
+}
+
+// Tetrahedron: edges e_m = x_{m+1} - x_0 and the scaled inward face normals n_i, from edges scaled by
+// 2^-s (normals by 2^-2s); returns s.
+__device__ __forceinline__ int tet_frame(const VtxDF<3>* const (&V)[4], df2 (&e)[3][3], df2 (&n)[4][3]) {
+  double ed[3][3], ud[3], vd[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) ed[q][m] = __dsub_rn(V[q + 1]->x[m], V[0]->x[m]);
+    ud[m] = __dsub_rn(V[3]->x[m], V[1]->x[m]);  // x_3 - x_1 and x_2 - x_1 (0-based): the edges of face [2 4 3]
+    vd[m] = __dsub_rn(V[2]->x[m], V[1]->x[m]);
+  }
+  uint32_t mx = 0;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) mx = max(mx, abs_hiword(ed[q][m]));
+    mx = max(mx, max(abs_hiword(ud[m]), abs_hiword(vd[m])));
+  }
+  const int s = exponent_of_hiword(mx);
+  df2 u[3], v[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) e[q][m] = df_from_double_shift(ed[q][m], s);
+    u[m] = df_from_double_shift(ud[m], s);
+    v[m] = df_from_double_shift(vd[m], s);
+  }
+  df_cross(e[1], e[2], n[1]);
+  df_cross(e[2], e[0], n[2]);
+  df_cross(e[0], e[1], n[3]);
+  df_cross(u, v, n[0]);
+  return s;
+}
+
+// want_diag = false sets L.a[0..2] (the diagonals) to 0, for callers that form them from row sums.
+__device__ __forceinline__ int element_df2(const VtxDF<2>* const (&V)[3], const SC* const (&S)[3], df2 kt, bool want_a,
+                                           bool want_b, int f_kind, df2 fconst, const double* __restrict__ f_arg,
+                                           int t, LocalDF<2>& L, bool want_diag = true) {
+  df2 e[3][2];
+  const int s = tri_edges(V, e);
+  const df2 a2 = df_dot2m(e[1][0], e[2][1], e[1][1], e[2][0]);  // twice the signed area, times 2^-2s
   const df2 a2abs = a2.h < 0.0f ? df_neg(a2) : a2;
-  const bool ok = a2abs.h > 0.0f && a2abs.h < INFINITY;
+  int st = (a2abs.h > 0.0f && a2abs.h < INFINITY) ? FEM_OK : FEM_ERR_DEGENERATE;
   if (want_a) {
-    const df2 s = df_mul(kt, df_recip(df_scale(a2abs, 2.0f)));
-    const df2 a01 = df_mul(s, df_dot<2>(e[0], e[1]));
-    const df2 a02 = df_mul(s, df_dot<2>(e[0], e[2]));
-    const df2 a12 = df_mul(s, df_dot<2>(e[1], e[2]));
+    // the 2-D stiffness is homogeneous of degree 0: the scaled frame gives the values themselves
+    // (k in [2^-80, 2^96], checked where it is read, keeps every entry in range: no per-entry checks)
+    const df2 sc = df_mul(kt, df_recip(df_scale(a2abs, 2.0f)));
+    const df2 a01 = df_mul(sc, df_dot<2>(e[0], e[1]));
+    const df2 a02 = df_mul(sc, df_dot<2>(e[0], e[2]));
+    const df2 a12 = df_mul(sc, df_dot<2>(e[1], e[2]));
     L.a[3] = a01;
     L.a[4] = a02;
     L.a[5] = a12;
@@ -82,10 +176,13 @@ __device__ __forceinline__ bool element_df2(const VtxDF<2>* const (&V)[3], const
       L.a[0] = df_neg(df_add(a01, a02));
       L.a[1] = df_neg(df_add(a01, a12));
       L.a[2] = df_neg(df_add(a02, a12));
+    } else {
+      L.a[0] = L.a[1] = L.a[2] = df2{0.0f, 0.0f};
     }
   }
   if (want_b) {
-    const df2 meas = df_scale(a2abs, 0.5f);
+    if (!scale_in_range(2 * s)) st = worst(st, FEM_ERR_RANGE);
+    const df2 meas = df_ldexp(df_scale(a2abs, 0.5f), scale_in_range(2 * s) ? 2 * s : 0);  // |tau|
     df2 f[3];
     if (f_kind == FEM_F_SINPROD) {
 #pragma unroll
@@ -102,50 +199,36 @@ __device__ __forceinline__ bool element_df2(const VtxDF<2>* const (&V)[3], const
     }
     const df2 w = df_mul(meas, df2{0.1666666716337204f, -4.9670538793e-09f});  // |tau| / 6
 #pragma unroll
-    for (int i = 0; i < 3; ++i) L.bt[i] = df_mul(w, df_add(f[(i + 1) % 3], f[(i + 2) % 3]));
-  }
-  return ok;
-}
-
-__device__ __forceinline__ void df_cross(const df2 (&u)[3], const df2 (&v)[3], df2 (&o)[3]) {
-  o[0] = df_dot2m(u[1], v[2], u[2], v[1]);
-  o[1] = df_dot2m(u[2], v[0], u[0], v[2]);
-  o[2] = df_dot2m(u[0], v[1], u[1], v[0]);
-}
-
-// want_diag = false leaves L.a[0..3] (the diagonals) unset, for callers that re-form them.
-__device__ __forceinline__ bool element_df3(const VtxDF<3>* const (&V)[4], df2 kt, bool want_a, bool want_b,
-                                            int f_kind, df2 fconst, const double* __restrict__ f_arg, int t,
-                                            const float4* __restrict__ tab, LocalDF<3>& L, bool want_diag = true) {
-  df2 e[3][3];  // e[m-1] = x_m - x_0
-#pragma unroll
-  for (int q = 0; q < 3; ++q)
-#pragma unroll
-    for (int m = 0; m < 3; ++m) e[q][m] = f3_diff(V[q + 1]->x[m], V[0]->x[m]);
-  df2 n[4][3];
-  df_cross(e[1], e[2], n[1]);
-  df_cross(e[2], e[0], n[2]);
-  df_cross(e[0], e[1], n[3]);
-  {
-    df2 u[3], v[3];  // x_3 - x_1 and x_2 - x_1 (0-based), the edges of face [2 4 3]
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      u[m] = f3_diff(V[3]->x[m], V[1]->x[m]);
-      v[m] = f3_diff(V[2]->x[m], V[1]->x[m]);
+    for (int i = 0; i < 3; ++i) {
+      const df2 fs = df_add(f[(i + 1) % 3], f[(i + 2) % 3]);
+      L.bt[i] = df_mul(w, fs);
+      if (!df_prod_in_range(L.bt[i], w.h != 0.0f && fs.h != 0.0f)) st = worst(st, FEM_ERR_RANGE);
     }
-    df_cross(u, v, n[0]);
   }
-  const df2 vol6 = df_dot<3>(n[3], e[2]);  // 6 * signed volume
-  const bool ok = vol6.h > 0.0f && vol6.h < INFINITY;
+  return st;
+}
+
+// want_diag = false leaves L.a[0..3] (the diagonals) 0, for callers that form them from row sums.
+__device__ __forceinline__ int element_df3(const VtxDF<3>* const (&V)[4], df2 kt, bool want_a, bool want_b,
+                                           int f_kind, df2 fconst, const double* __restrict__ f_arg, int t,
+                                           const float4* __restrict__ tab, LocalDF<3>& L, bool want_diag = true) {
+  df2 e[3][3], n[4][3];
+  const int s = tet_frame(V, e, n);
+  const df2 vol6 = df_dot<3>(n[3], e[2]);  // 6 x signed volume, times 2^-3s
+  int st = (vol6.h > 0.0f && vol6.h < INFINITY) ? FEM_OK : FEM_ERR_DEGENERATE;
   if (want_a) {
-    const df2 s = df_mul(kt, df_recip(df_mul_f(vol6, 6.0f)));  // k / (36 vol)
+    // k / (36 vol) times 2^s: the 3-D stiffness is homogeneous of degree 1; k 2^s within [2^-80, 2^100]
+    // keeps every entry in range (no per-entry checks)
+    const int ke = (int)((__float_as_uint(kt.h) >> 23) & 0xffu) - 127;
+    if (!scale_in_range(s) || (kt.h != 0.0f && (ke + s < -80 || ke + s > 100))) st = worst(st, FEM_ERR_RANGE);
+    const df2 sc = df_ldexp(df_mul(kt, df_recip(df_mul_f(vol6, 6.0f))), scale_in_range(s) ? s : 0);
 #pragma unroll
     for (int i = 0; i < 4; ++i) L.a[i] = df2{0.0f, 0.0f};
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = i + 1; j < 4; ++j) {
-        const df2 aij = df_mul(s, df_dot<3>(n[i], n[j]));
+        const df2 aij = df_mul(sc, df_dot<3>(n[i], n[j]));
         L.a[pidx<3>(i, j)] = aij;
         if (want_diag) {
           L.a[i] = df_sub(L.a[i], aij);
@@ -154,7 +237,8 @@ __device__ __forceinline__ bool element_df3(const VtxDF<3>* const (&V)[4], df2 k
       }
   }
   if (want_b) {
-    const df2 vol = df_mul(vol6, df2{0.1666666716337204f, -4.9670538793e-09f});
+    if (!scale_in_range(3 * s)) st = worst(st, FEM_ERR_RANGE);
+    const df2 vol = df_ldexp(df_mul(vol6, df2{0.1666666716337204f, -4.9670538793e-09f}), scale_in_range(3 * s) ? 3 * s : 0);
     df2 f[4];
     if (f_kind == FEM_F_SINPROD) {
       // points x_q = sum_i lambda_i(q) x_i; per coordinate, shifted by an integer n near the element
@@ -164,15 +248,13 @@ __device__ __forceinline__ bool element_df3(const VtxDF<3>* const (&V)[4], df2 k
       for (int q = 0; q < 4; ++q) f[q] = df_from(1.0f);
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
-        const float nn = rintf(V[0]->x[m].a);
+        const float nn = rintf(lead_float(V[0]->x[m]));
+        const double nd = f2d_bits(nn);
         df2 y[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const df2 ya = two_sum(V[i]->x[m].a, -nn);
-          y[i] = df_add(ya, fast_two_sum(V[i]->x[m].b, V[i]->x[m].c));
-        }
+        for (int i = 0; i < 4; ++i) y[i] = df_from_double_shift(__dsub_rn(V[i]->x[m], nd), 0);
         const df2 sy = df_add(df_add(y[0], y[1]), df_add(y[2], y[3]));
-        const float sgn = (__float2int_rn(nn) & 1) ? -1.0f : 1.0f;
+        const float sgn = int_parity(nn) ? -1.0f : 1.0f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const df2 xq = df_add(df_mul(be, sy), df_mul(df_sub(al, be), y[q]));
@@ -191,9 +273,13 @@ __device__ __forceinline__ bool element_df3(const VtxDF<3>* const (&V)[4], df2 k
     const df2 fs = df_add(df_add(f[0], f[1]), df_add(f[2], f[3]));
     const df2 w = df_scale(vol, 0.25f);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) L.bt[i] = df_mul(w, df_add(df_mul(be, fs), df_mul(df_sub(al, be), f[i])));
+    for (int i = 0; i < 4; ++i) {
+      const df2 fi = df_add(df_mul(be, fs), df_mul(df_sub(al, be), f[i]));
+      L.bt[i] = df_mul(w, fi);
+      if (!df_prod_in_range(L.bt[i], w.h != 0.0f && fi.h != 0.0f)) st = worst(st, FEM_ERR_RANGE);
+    }
   }
-  return ok;
+  return st;
 }
 
 // ---- other second-order operators on the same element (values only) --------------------------------
@@ -204,18 +290,18 @@ __device__ __forceinline__ bool element_df3(const VtxDF<3>* const (&V)[4], df2 k
 constexpr int kOpStiffness = 0, kOpMass = 1, kOpAniso = 2, kOpApply = 3;  // kOpApply: y = A u, matrix-free
 
 template <int D>
-__device__ __forceinline__ void sym_tensor_df(const double* __restrict__ c, df2 (&K)[D][D]) {
+__device__ __forceinline__ void sym_tensor_df(const double* __restrict__ c, df2 (&K)[D][D], int& st) {
   if constexpr (D == 2) {
-    K[0][0] = df_from_double(__ldg(c));
-    K[0][1] = K[1][0] = df_from_double(__ldg(c + 1));
-    K[1][1] = df_from_double(__ldg(c + 2));
+    K[0][0] = coef_df(__ldg(c), st);
+    K[0][1] = K[1][0] = coef_df(__ldg(c + 1), st);
+    K[1][1] = coef_df(__ldg(c + 2), st);
   } else {
-    K[0][0] = df_from_double(__ldg(c));
-    K[0][1] = K[1][0] = df_from_double(__ldg(c + 1));
-    K[0][2] = K[2][0] = df_from_double(__ldg(c + 2));
-    K[1][1] = df_from_double(__ldg(c + 3));
-    K[1][2] = K[2][1] = df_from_double(__ldg(c + 4));
-    K[2][2] = df_from_double(__ldg(c + 5));
+    K[0][0] = coef_df(__ldg(c), st);
+    K[0][1] = K[1][0] = coef_df(__ldg(c + 1), st);
+    K[0][2] = K[2][0] = coef_df(__ldg(c + 2), st);
+    K[1][1] = coef_df(__ldg(c + 3), st);
+    K[1][2] = K[2][1] = coef_df(__ldg(c + 4), st);
+    K[2][2] = coef_df(__ldg(c + 5), st);
   }
 }
 
@@ -228,73 +314,67 @@ __device__ __forceinline__ df2 df_quad(const df2 (&n)[D], const df2 (&K)[D][D], 
   return df_dot<D>(n, Km);
 }
 
-// scaled normals n_i and d! |tau| (2-D: |2 area|, the paper's abs(); 3-D: 6 x signed volume)
+// Scaled normals n_i and d! |tau| (2-D: |2 area|, the paper's abs(); 3-D: 6 x signed volume) in the
+// element's frame scaled by 2^-s (normals times 2^-(d-1)s, the measure times 2^-ds); returns s.
 template <int D>
-__device__ __forceinline__ df2 element_normals_df(const VtxDF<D>* const (&V)[D + 1], df2 (&n)[D + 1][D]) {
+__device__ __forceinline__ int element_normals_df(const VtxDF<D>* const (&V)[D + 1], df2 (&n)[D + 1][D], df2& dm) {
   if constexpr (D == 2) {
     df2 e[3][2];
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      e[0][m] = f3_diff(V[2]->x[m], V[1]->x[m]);
-      e[1][m] = f3_diff(V[0]->x[m], V[2]->x[m]);
-      e[2][m] = f3_diff(V[1]->x[m], V[0]->x[m]);
-    }
+    const int s = tri_edges(V, e);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       n[i][0] = df_neg(e[i][1]);
       n[i][1] = e[i][0];
     }
     const df2 a2 = df_dot2m(e[1][0], e[2][1], e[1][1], e[2][0]);
-    return a2.h < 0.0f ? df_neg(a2) : a2;
+    dm = a2.h < 0.0f ? df_neg(a2) : a2;
+    return s;
   } else {
     df2 e[3][3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-#pragma unroll
-      for (int m = 0; m < 3; ++m) e[q][m] = f3_diff(V[q + 1]->x[m], V[0]->x[m]);
-    df_cross(e[1], e[2], n[1]);
-    df_cross(e[2], e[0], n[2]);
-    df_cross(e[0], e[1], n[3]);
-    df2 u[3], v[3];
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      u[m] = f3_diff(V[3]->x[m], V[1]->x[m]);
-      v[m] = f3_diff(V[2]->x[m], V[1]->x[m]);
-    }
-    df_cross(u, v, n[0]);
-    return df_dot<3>(n[3], e[2]);
+    const int s = tet_frame(V, e, n);
+    dm = df_dot<3>(n[3], e[2]);
+    return s;
   }
 }
 
 // Local matrix of operator op (kOpMass or kOpAniso) into L.a (pidx order; mass: every entry; aniso: the
 // off-diagonal entries). coef: mass c_t (nullable: 1), aniso the tensor's upper triangle of element t.
 template <int D>
-__device__ __forceinline__ bool element_df_operator(const VtxDF<D>* const (&V)[D + 1], int op,
-                                                    const double* __restrict__ coef, LocalDF<D>& L) {
+__device__ __forceinline__ int element_df_operator(const VtxDF<D>* const (&V)[D + 1], int op,
+                                                   const double* __restrict__ coef, LocalDF<D>& L) {
   constexpr int D1 = D + 1;
-  df2 n[D1][D];
-  const df2 dm = element_normals_df<D>(V, n);  // d! |tau|
-  const bool ok = dm.h > 0.0f && dm.h < INFINITY;
+  df2 n[D1][D], dm;
+  const int s = element_normals_df<D>(V, n, dm);  // d! |tau| times 2^-ds
+  int st = (dm.h > 0.0f && dm.h < INFINITY) ? FEM_OK : FEM_ERR_DEGENERATE;
   if (op == kOpMass) {
-    // c |tau| / ((d+1)(d+2)) = c d! |tau| / (2 * 12) in 2-D, / (6 * 20) in 3-D
+    // c |tau| / ((d+1)(d+2)) = c d! |tau| / (2 * 12) in 2-D, / (6 * 20) in 3-D; homogeneous of degree d
+    if (!scale_in_range(D * s)) st = worst(st, FEM_ERR_RANGE);
     const df2 inv = (D == 2) ? df2{0.041666667908430099f, -1.2417634e-09f} : df2{0.0083333337679505348f, -4.3461720e-10f};
-    const df2 c = coef ? df_from_double(__ldg(coef)) : df2{1.0f, 0.0f};
-    const df2 off = df_mul(c, df_mul(dm, inv));
+    const df2 c = coef ? coef_df(__ldg(coef), st) : df2{1.0f, 0.0f};
+    const df2 off = df_ldexp(df_mul(c, df_mul(dm, inv)), scale_in_range(D * s) ? D * s : 0);
     const df2 dia = df_scale(off, 2.0f);
+    if (!df_prod_in_range(dia, c.h != 0.0f)) st = worst(st, FEM_ERR_RANGE);
 #pragma unroll
     for (int i = 0; i < D1; ++i) L.a[i] = dia;
 #pragma unroll
     for (int c2 = D1; c2 < D1 * (D1 + 1) / 2; ++c2) L.a[c2] = off;
   } else {
+    // 1 / (d!^2 |tau|) in the scaled frame, times 2^(d-2)s: homogeneous of degree d - 2
     df2 K[D][D];
-    sym_tensor_df<D>(coef, K);
-    const df2 s = df_recip(D == 2 ? df_scale(dm, 2.0f) : df_mul_f(dm, 6.0f));  // 1 / (d!^2 |tau|)
+    sym_tensor_df<D>(coef, K, st);
+    if (!scale_in_range((D - 2) * s)) st = worst(st, FEM_ERR_RANGE);
+    const df2 sc = df_ldexp(df_recip(D == 2 ? df_scale(dm, 2.0f) : df_mul_f(dm, 6.0f)),
+                            scale_in_range((D - 2) * s) ? (D - 2) * s : 0);
 #pragma unroll
     for (int i = 0; i < D1; ++i)
 #pragma unroll
-      for (int j = i + 1; j < D1; ++j) L.a[pidx<D>(i, j)] = df_mul(s, df_quad<D>(n[i], K, n[j]));
+      for (int j = i + 1; j < D1; ++j) {
+        const df2 q = df_quad<D>(n[i], K, n[j]);
+        L.a[pidx<D>(i, j)] = df_mul(sc, q);
+        if (!df_prod_in_range(L.a[pidx<D>(i, j)], q.h != 0.0f)) st = worst(st, FEM_ERR_RANGE);
+      }
   }
-  return ok;
+  return st;
 }
 
 }  // namespace fem

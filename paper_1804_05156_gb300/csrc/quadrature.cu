@@ -135,23 +135,26 @@ __global__ void __launch_bounds__(128) k_rhs_rule(int64_t NT, const int32_t* __r
   for (int i = 0; i < D1; ++i) {
     const int v = __ldg(elem + t * D1 + i);
 #pragma unroll
-    for (int m = 0; m < D; ++m) X[i].x[m] = split3(__ldg(node + (size_t)v * D + m));
+    for (int m = 0; m < D; ++m) X[i].x[m] = __ldg(node + (size_t)v * D + m);
     V[i] = &X[i];
   }
-  df2 n[D1][D];
-  const df2 dm = element_normals_df<D>(reinterpret_cast<const VtxDF<D>* const(&)[D1]>(V), n);  // d! |tau|
-  if (!(dm.h > 0.0f && dm.h < INFINITY)) report(err, FEM_ERR_DEGENERATE);
-  const df2 meas = (D == 2) ? df_scale(dm, 0.5f) : df_mul(dm, df2{0.1666666716337204f, -4.9670538793e-09f});
-  // coordinates shifted by an integer near the element, exactly, so that sin(pi x) keeps its relative
-  // accuracy next to integers
+  df2 n[D1][D], dm;
+  const int s = element_normals_df<D>(reinterpret_cast<const VtxDF<D>* const(&)[D1]>(V), n, dm);  // d! |tau| 2^-ds
+  int st = (dm.h > 0.0f && dm.h < INFINITY) ? FEM_OK : FEM_ERR_DEGENERATE;
+  if (!scale_in_range(D * s)) st = worst(st, FEM_ERR_RANGE);
+  const df2 meas = df_ldexp((D == 2) ? df_scale(dm, 0.5f) : df_mul(dm, df2{0.1666666716337204f, -4.9670538793e-09f}),
+                            scale_in_range(D * s) ? D * s : 0);
+  // coordinates shifted by an integer near the element (one FP64 subtraction each), so that sin(pi x)
+  // keeps its relative accuracy next to integers
   df2 y[D1][D];
   float sgn = 1.0f;
 #pragma unroll
   for (int m = 0; m < D; ++m) {
-    const float nn = rintf(X[0].x[m].a);
-    if (__float2int_rn(nn) & 1) sgn = -sgn;
+    const float nn = rintf(lead_float(X[0].x[m]));
+    if (int_parity(nn)) sgn = -sgn;
+    const double nd = f2d_bits(nn);
 #pragma unroll
-    for (int i = 0; i < D1; ++i) y[i][m] = df_add(two_sum(X[i].x[m].a, -nn), fast_two_sum(X[i].x[m].b, X[i].x[m].c));
+    for (int i = 0; i < D1; ++i) y[i][m] = df_from_double_shift(__dsub_rn(X[i].x[m], nd), 0);
   }
   const df2 fc = (f_kind == FEM_F_CONST && f_arg) ? df_from_double(__ldg(f_arg)) : df2{1.0f, 0.0f};
   df2 c[D1];
@@ -181,8 +184,10 @@ __global__ void __launch_bounds__(128) k_rhs_rule(int64_t NT, const int32_t* __r
 #pragma unroll
   for (int i = 0; i < D1; ++i) {
     const df2 v = df_mul(meas, c[i]);
+    if (!df_prod_in_range(v, c[i].h != 0.0f)) st = worst(st, FEM_ERR_RANGE);
     contrib[t * D1 + i] = make_float2(v.h, v.l);
   }
+  if (st != FEM_OK) report(err, st);
 }
 
 __global__ void __launch_bounds__(256) k_rhs_gather(int64_t N, const int32_t* __restrict__ inc_ptr,

@@ -132,11 +132,11 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
     const int R = a.vlist[v0 + v];
     VtxDF<D> x;
 #pragma unroll
-    for (int m = 0; m < D; ++m) x.x[m] = split3(__ldg(node + (size_t)R * D + m));
+    for (int m = 0; m < D; ++m) x.x[m] = __ldg(node + (size_t)R * D + m);
     xs[v] = x;
     if (sinprod2) {
 #pragma unroll
-      for (int m = 0; m < D; ++m) scs[v * D + m] = sincospi_half(x.x[m], tab);
+      for (int m = 0; m < D; ++m) scs[v * D + m] = sincospi_half(split3(x.x[m]), tab);
     }
   }
   // the block's records and element data, loaded once, coalesced (their latency overlaps the staging)
@@ -209,18 +209,18 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
       int lv[D1];
 #pragma unroll
       for (int i = 0; i < D1; ++i) lv[i] = slv[el * D1 + i];
-      const df2 kt = want_k ? df_from_double(sk[el]) : df2{1.0f, 0.0f};
+      int st = FEM_OK;
+      const df2 kt = want_k ? coef_df(sk[el], st) : df2{1.0f, 0.0f};
       LocalDF<D> L;
-      bool ok;
       if constexpr (D == 2) {
         const VtxDF<2>* const V[3] = {&xs[lv[0]], &xs[lv[1]], &xs[lv[2]]};
         const SC* const S[3] = {&scs[lv[0] * 2], &scs[lv[1] * 2], &scs[lv[2] * 2]};
-        ok = element_df2(V, S, kt, want_a, want_b, f_kind, fconst, f_arg, t, L);
+        st = worst(st, element_df2(V, S, kt, want_a, want_b, f_kind, fconst, f_arg, t, L));
       } else {
         const VtxDF<3>* const V[4] = {&xs[lv[0]], &xs[lv[1]], &xs[lv[2]], &xs[lv[3]]};
-        ok = element_df3(V, kt, want_a, want_b, f_kind, fconst, f_arg, t, tab, L);
+        st = worst(st, element_df3(V, kt, want_a, want_b, f_kind, fconst, f_arg, t, tab, L));
       }
-      if (!ok) report(err, FEM_ERR_DEGENERATE);
+      if (st != FEM_OK) report(err, st);
       df2* dst = ev + e * W;
       if (want_a) {
 #pragma unroll

@@ -68,20 +68,15 @@ struct RowArgs {
   bool diag_in_packet;  // the packet's last pair is the diagonal entry (mass matrix), not a load term
 };
 
-// Staged 2-D records padded to 48 bytes (three 16-byte bank groups): a warp's scattered reads of the
-// records of different vertices then fall on all eight 16-byte groups of banks instead of four.
-struct __align__(16) VtxPad2 {
+// Staged 2-D record: the coordinates and, for the sine-product load, sin/cos(pi x/2) of each coordinate,
+// 48 bytes (three 16-byte bank groups): a warp's scattered reads of the records of different vertices
+// fall on all eight 16-byte groups of banks instead of four.
+struct __align__(16) Vtx2 {
   VtxDF<2> v;
-  float pad[4];
-};
-struct __align__(16) SCPad2 {
   SC sc[2];
-  float pad[4];
 };
 template <int D>
-__host__ __device__ constexpr int staged_vtx_bytes() { return D == 2 ? (int)sizeof(VtxPad2) : (int)sizeof(VtxDF<3>); }
-template <int D>
-__host__ __device__ constexpr int staged_sc_bytes() { return D == 2 ? (int)sizeof(SCPad2) : 0; }
+__host__ __device__ constexpr int staged_vtx_bytes() { return D == 2 ? (int)sizeof(Vtx2) : (int)sizeof(VtxDF<3>); }
 
 // Phase 1 for one tile (all TE threads of the CTA; one __syncthreads inside).
 template <int D, int TE, bool FUSED = false>
@@ -112,13 +107,13 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
     const int R = __ldg(a.vlist + v0 + v);
     VtxDF<D> x;
 #pragma unroll
-    for (int m = 0; m < D; ++m) x.x[m] = split3(__ldg(node + (size_t)R * D + m));
+    for (int m = 0; m < D; ++m) x.x[m] = __ldg(node + (size_t)R * D + m);
     if constexpr (D == 2) {
-      reinterpret_cast<VtxPad2*>(sm)[v].v = x;
+      Vtx2* rec = reinterpret_cast<Vtx2*>(sm) + v;
+      rec->v = x;
       if (sinprod2) {
-        SCPad2* scp = reinterpret_cast<SCPad2*>(sm + a.xs_bytes);
 #pragma unroll
-        for (int m = 0; m < 2; ++m) scp[v].sc[m] = sincospi_half(x.x[m], tab);
+        for (int m = 0; m < 2; ++m) rec->sc[m] = sincospi_half(split3(x.x[m]), tab);
       }
     } else {
       xs[v] = x;
@@ -129,37 +124,37 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
   }
   __syncthreads();
   if (!act) return;
-  const df2 kt = (k && want_a) ? df_from_double(kd) : df2{1.0f, 0.0f};
+  int st = FEM_OK;
+  const df2 kt = (k && want_a) ? coef_df(kd, st) : df2{1.0f, 0.0f};
   const df2 fconst = (f_kind == FEM_F_CONST && f_arg) ? df_from_double(__ldg(f_arg)) : df2{1.0f, 0.0f};
   LocalDF<D> L;
 #pragma unroll
   for (int c = 0; c < D1 * (D1 + 1) / 2; ++c) L.a[c] = df2{0.0f, 0.0f};
 #pragma unroll
   for (int i = 0; i < D1; ++i) L.bt[i] = df2{0.0f, 0.0f};
-  bool ok;
   const VtxDF<D>* V[D1];
 #pragma unroll
   for (int i = 0; i < D1; ++i) {
-    if constexpr (D == 2) V[i] = &reinterpret_cast<const VtxPad2*>(sm)[lv[i]].v;
+    if constexpr (D == 2) V[i] = &(reinterpret_cast<const Vtx2*>(sm) + lv[i])->v;
     else V[i] = &xs[lv[i]];
   }
   if (a.op == kOpMass || a.op == kOpAniso) {
     const double* c = (a.op == kOpMass) ? (a.opk ? a.opk + t : nullptr) : a.opk + (size_t)t * (D * D1 / 2);
-    ok = element_df_operator<D>(reinterpret_cast<const VtxDF<D>* const(&)[D1]>(V), a.op, c, L);
+    st = worst(st, element_df_operator<D>(reinterpret_cast<const VtxDF<D>* const(&)[D1]>(V), a.op, c, L));
     if (a.op == kOpMass) {
 #pragma unroll
       for (int i = 0; i < D1; ++i) L.bt[i] = L.a[i];  // the diagonal travels in the load slot
     }
   } else if constexpr (D == 2) {
-    const SCPad2* scp = reinterpret_cast<const SCPad2*>(sm + a.xs_bytes);
+    const Vtx2* rec = reinterpret_cast<const Vtx2*>(sm);
     const VtxDF<2>* const V2[3] = {V[0], V[1], V[2]};
-    const SC* const S[3] = {scp[lv[0]].sc, scp[lv[1]].sc, scp[lv[2]].sc};
-    ok = element_df2(V2, S, kt, want_a, want_b, f_kind, fconst, f_arg, t, L, false);  // diagonals: in the gather
+    const SC* const S[3] = {rec[lv[0]].sc, rec[lv[1]].sc, rec[lv[2]].sc};
+    st = worst(st, element_df2(V2, S, kt, want_a, want_b, f_kind, fconst, f_arg, t, L, false));  // diagonals: in the gather
   } else {
     const VtxDF<3>* const V3[4] = {V[0], V[1], V[2], V[3]};
-    ok = element_df3(V3, kt, want_a, want_b, f_kind, fconst, f_arg, t, tab, L, false);  // diagonals: in the gather
+    st = worst(st, element_df3(V3, kt, want_a, want_b, f_kind, fconst, f_arg, t, tab, L, false));  // diagonals: in the gather
   }
-  if (!ok) report(err, FEM_ERR_DEGENERATE);
+  if (st != FEM_OK) report(err, st);
   if (a.op == kOpApply) {
     // (A u)_i contribution of the element: sum_{j != i} a_ij (u_j - u_i), since a_ii = -sum_{j != i} a_ij
     const df2* ux = reinterpret_cast<const df2*>(sm + a.u_off);
@@ -418,9 +413,8 @@ int gather_warps(int max_row) {
 
 }  // namespace
 
-int tile_smem_need(const TilePlan& T, int d, bool sinprod) {
-  const int xs = ((T.max_v * (d == 2 ? staged_vtx_bytes<2>() : staged_vtx_bytes<3>())) + 15) / 16 * 16;
-  return xs + ((sinprod && d == 2) ? T.max_v * staged_sc_bytes<2>() : 0);
+int tile_smem_need(const TilePlan& T, int d, bool) {
+  return ((T.max_v * (d == 2 ? staged_vtx_bytes<2>() : staged_vtx_bytes<3>())) + 15) / 16 * 16;
 }
 
 // Shared memory of the fused kernel (staging of phase 1 or row copies of phase 2, whichever is larger);
@@ -446,7 +440,7 @@ int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_
     return FEM_OK;
   }
   if (reinterpret_cast<uintptr_t>(T.pk) & 31) return set_error(FEM_ERR_STATE, "packet buffer not 32-byte aligned");
-  TileArgs a;
+  TileArgs a{};
   a.NT = P->NT;
   a.ntiles = T.ntiles;
   a.elist = T.elist;

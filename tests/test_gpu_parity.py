@@ -250,6 +250,95 @@ def test_row_shards_on_the_gpu_give_the_global_rows_bit_for_bit(d):
         assert np.array_equal(np.concatenate([g[4] for g in got]).view(np.uint64), b.view(np.uint64))
 
 
+@pytest.mark.parametrize("d,e", [(2, -30), (2, -20), (2, 0), (2, 30), (3, -20), (3, -12), (3, 0), (3, 30)])
+def test_meshes_scaled_by_powers_of_two_keep_the_parity_bar(d, e):
+    """The mesh scaled by 2^e (coordinates exactly scaled, so the FP64 oracle's values scale exactly too):
+    stiffness (degree d - 2 in the coordinates), the load vector of f = 1 (degree d) and the adjoint stay
+    within the parity bar on every value path; the element's own power-of-two frame keeps every float-float
+    product of order one whatever the mesh's size. 2^-20 in 3-D is a mesh of 1e-7-sized tetrahedra (|tau|
+    near 2^-71) whose products of face normals, n_i . n_j ~ 2^-92, would have left the float-float range
+    without it. (A sine-product load is a different matter at these scales: at 2^-40 its values fall below
+    the float range, which test_inputs_beyond_the_float_float_range_are_reported covers, and at 2^30 the
+    FP64 rounding of the quadrature points alone moves sin(pi x) by more than the bar.)"""
+    d_, node, elem, k, _ = mesh_case("sq37p" if d == 2 else "kuhn7s")
+    node = np.ldexp(node, e)
+    N, NT = node.shape[0], elem.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    fa.fem_pattern_set_locality(p, dev(node))
+    _, _, vo, so = oracle.assemble(d, node, elem, k)
+    bo = oracle.rhs(d, node, elem, oracle.F_CONST)
+    for path, te in ((fa.FEM_PATH_TILES, 128), (fa.FEM_PATH_TILES_FUSED, 256), (fa.FEM_PATH_BLOCKED, 0)):
+        fa.fem_pattern_force_path(p, path, te or 256)
+        v, b = fa.assemble(p, dev(node), dev(k), fa.FEM_F_CONST, None, fa.FEM_DETERMINISTIC)
+        fa.get_error()
+        assert_close_scaled(host(v), vo, so, what="stiffness at 2^%d" % e)
+        assert_close_scaled(host(b), bo, np.abs(bo) + 1e-300, what="rhs at 2^%d" % e)
+    rp, col = host(p.row_ptr).astype(np.int64), host(p.col_idx).astype(np.int64)
+    slot = oracle.slots(d, N, elem, rp, col)
+    w, r = meshgen.normal(5, meshgen.TAG_W, p.nnz), meshgen.normal(5, meshgen.TAG_R, N)
+    gno, gko, gnm, gkm = oracle.backward(d, node, elem, k, oracle.F_CONST, None, slot, w, r, with_scale=True)
+    gn = torch.empty((N, d), dtype=torch.float64, device="cuda")
+    gk = torch.empty(NT, dtype=torch.float64, device="cuda")
+    fa.fem_assemble_backward(p, dev(node), dev(k), fa.FEM_F_CONST, None, dev(w), dev(r), gn, gk)
+    fa.get_error()
+    assert_close_scaled(host(gn), gno, gnm, tol=BWD_TOL, what="node gradient at 2^%d" % e)
+    assert_close_scaled(host(gk), gko, gkm, tol=BWD_TOL, what="k gradient at 2^%d" % e)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_inputs_beyond_the_float_float_range_are_reported(d):
+    """Where a float-float result cannot keep its precision the kernels say so (FEM_ERR_RANGE) instead of
+    returning a silently degraded value: a load vector whose element measures are below 2^-96 (mesh
+    scaled by 2^-70), or above 2^96 (scaled by 2^60), and a coefficient of 1e-40. Within range the
+    same pattern assembles normally afterwards, and a sine-product load on a mesh at 2^-40 (values near
+    2^-168) is reported too."""
+    d_, node, elem, k, _ = mesh_case("sq37p" if d == 2 else "kuhn5")
+    p = fa.Pattern(dev(elem), node.shape[0])
+    fa.fem_pattern_set_locality(p, dev(node))
+    kd = dev(k if k is not None else np.ones(elem.shape[0]))
+    for e in (-70, 60):
+        fa.assemble(p, dev(np.ldexp(node, e)), kd, fa.FEM_F_CONST, None, fa.FEM_DETERMINISTIC)
+        with pytest.raises(fa.FemError) as err:
+            fa.get_error()
+        assert err.value.code == fa.FEM_ERR_RANGE, e
+    fa.assemble(p, dev(np.ldexp(node, -40)), kd, fa.FEM_F_SINPROD, None, fa.FEM_DETERMINISTIC)
+    with pytest.raises(fa.FemError) as err:
+        fa.get_error()
+    assert err.value.code == fa.FEM_ERR_RANGE
+    kk = np.ones(elem.shape[0])
+    kk[3] = 1e-40
+    fa.assemble(p, dev(node), dev(kk), fa.FEM_F_CONST, None, fa.FEM_DETERMINISTIC)
+    with pytest.raises(fa.FemError) as err:
+        fa.get_error()
+    assert err.value.code == fa.FEM_ERR_RANGE
+    fa.assemble(p, dev(node), kd, fa.FEM_F_CONST, None, fa.FEM_DETERMINISTIC)
+    fa.get_error()
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_sine_load_at_large_coordinates(d):
+    """The sine-product load on a uniform mesh moved by 2^26 in every coordinate (plus 1 in the first, so
+    the sign flips): the coordinates stay exact in FP64 (multiples of 2^-6 or 2^-2), and by periodicity the
+    exact load is minus the oracle's load on the unmoved mesh (in 2-D the oracle's own midpoints stay exact
+    and it agrees; in 3-D its FP64 quadrature points round at 2^-26 and it does not). The reductions of x
+    must keep the parts of x below the leading float's last bit (2^3 at 2^26): every entry within the bar."""
+    m = meshgen.square_mesh(64) if d == 2 else meshgen.kuhn_mesh(4)
+    node = m["node"] + 2.0 ** 26
+    node[:, 0] += 1.0
+    elem = m["elem"]
+    p = fa.Pattern(dev(elem), node.shape[0])
+    fa.fem_pattern_set_locality(p, dev(node))
+    bo = -oracle.rhs(d, m["node"], elem, oracle.F_SINPROD)
+    if d == 2:
+        assert np.array_equal(oracle.rhs(d, node, elem, oracle.F_SINPROD), bo)
+    for path, te in ((fa.FEM_PATH_TILES, 128), (fa.FEM_PATH_BLOCKED, 0)):
+        fa.fem_pattern_force_path(p, path, te or 256)
+        b = torch.empty(p.N, dtype=torch.float64, device="cuda")
+        fa.fem_assemble(p, dev(node), None, fa.FEM_F_SINPROD, None, None, b, fa.FEM_DETERMINISTIC)
+        fa.get_error()
+        assert_close_scaled(host(b), bo, np.abs(bo) + 1e-300, what="rhs at 2^26")
+
+
 def test_long_rows_take_the_tile_path():
     """A vertex with 40 neighbours (row of 41 entries) is beyond the owner-computes records (32 per
     row) but within the tile path's (256)."""
