@@ -61,14 +61,30 @@ __device__ __forceinline__ int int_parity(float n) { return fabsf(n) < 16777216.
 // the zeros of the sine keep their relative accuracy; large x keep every bit of x).
 __device__ __forceinline__ SC sincospi_half(const f3& x, const float4* __restrict__ tab) {
   const float ah = 0.5f * x.a, bh = 0.5f * x.b, ch = 0.5f * x.c;
-  const float na = rintf(ah), nb = rintf(bh), nc = rintf(ch);
-  const df2 r0 = two_sum(__fsub_rn(ah, na), __fsub_rn(bh, nb));
-  df2 r = df_add(r0, df2{__fsub_rn(ch, nc), 0.0f});
-  const float n3 = rintf(r.h);
-  r = fast_two_sum(__fsub_rn(r.h, n3), r.l);
+  const float na = rintf(ah);
+  df2 r;
+  int par;
+  if (fabsf(x.a) < 4194304.0f) {
+    // |x| < 2^22: |b/2| < 2^-3 and c/2 is below the last bit of b/2, so the remainder (a/2 - rint(a/2))
+    // + b/2 + c/2 is formed exactly in float-float (a two-sum, then c/2 into the trailing part), is at most
+    // 5/8 in magnitude, and one more reduction by its nearest integer brings it to [-1/2, 1/2]; both
+    // integers are below 2^21
+    const df2 r0 = two_sum(__fsub_rn(ah, na), bh);
+    r = fast_two_sum(r0.h, __fadd_rn(r0.l, ch));
+    const float n3 = rintf(r.h);
+    r = fast_two_sum(__fsub_rn(r.h, n3), r.l);
+    par = (__float2int_rn(na) + __float2int_rn(n3)) & 1;
+  } else {
+    const float nb = rintf(bh), nc = rintf(ch);
+    const df2 r0 = two_sum(__fsub_rn(ah, na), __fsub_rn(bh, nb));
+    r = df_add(r0, df2{__fsub_rn(ch, nc), 0.0f});
+    const float n3 = rintf(r.h);
+    r = fast_two_sum(__fsub_rn(r.h, n3), r.l);
+    par = (int_parity(na) + int_parity(nb) + int_parity(nc) + int_parity(n3)) & 1;
+  }
   SC o;
   df_sincospi_small(r, tab, o.s, o.c);
-  if ((int_parity(na) + int_parity(nb) + int_parity(nc) + int_parity(n3)) & 1) {
+  if (par) {
     o.s = df_neg(o.s);
     o.c = df_neg(o.c);
   }
@@ -77,6 +93,21 @@ __device__ __forceinline__ SC sincospi_half(const f3& x, const float4* __restric
 
 // sin(pi (u + v)/2) = sin(pi u/2) cos(pi v/2) + cos(pi u/2) sin(pi v/2)
 __device__ __forceinline__ df2 sin_mid(const SC& u, const SC& v) { return df_add(df_mul(u.s, v.c), df_mul(u.c, v.s)); }
+
+// 2-D sine product at edge midpoints from per-vertex products. With sx, cx = sin, cos(pi x/2) and sy, cy
+// likewise, a vertex carries P = (sx sy, sx cy, cx sy, cx cy); at the midpoint m of vertices u and v
+//   f(m) = sin(pi (x_u + x_v)/2) sin(pi (y_u + y_v)/2) = sum_a P_u[a] P_v[3 - a]
+// (both angle additions expanded), one float-float dot product of four terms.
+__device__ __forceinline__ void sin_products(const SC& x, const SC& y, df2 (&P)[4]) {
+  P[0] = df_mul(x.s, y.s);
+  P[1] = df_mul(x.s, y.c);
+  P[2] = df_mul(x.c, y.s);
+  P[3] = df_mul(x.c, y.c);
+}
+__device__ __forceinline__ df2 sinprod_mid(const df2* u, const df2* v) {
+  const df2 A[4] = {u[0], u[1], u[2], u[3]}, B[4] = {v[3], v[2], v[1], v[0]};
+  return df_dot<4>(A, B);
+}
 
 // x - n as a float pair for an integer n near x, and the parity of n: n = rint of the leading float of
 // x (truncated), the subtraction in FP64 (rounded once, to 2^-53 of the difference), so sin(pi x) =
@@ -154,7 +185,8 @@ __device__ __forceinline__ int tet_frame(const VtxDF<3>* const (&V)[4], df2 (&e)
 }
 
 // want_diag = false sets L.a[0..2] (the diagonals) to 0, for callers that form them from row sums.
-__device__ __forceinline__ int element_df2(const VtxDF<2>* const (&V)[3], const SC* const (&S)[3], df2 kt, bool want_a,
+// P: the per-vertex sine products (sin_products) when f_kind is FEM_F_SINPROD.
+__device__ __forceinline__ int element_df2(const VtxDF<2>* const (&V)[3], const df2* const (&P)[3], df2 kt, bool want_a,
                                            bool want_b, int f_kind, df2 fconst, const double* __restrict__ f_arg,
                                            int t, LocalDF<2>& L, bool want_diag = true) {
   df2 e[3][2];
@@ -186,10 +218,7 @@ __device__ __forceinline__ int element_df2(const VtxDF<2>* const (&V)[3], const 
     df2 f[3];
     if (f_kind == FEM_F_SINPROD) {
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int u = (q + 1) % 3, v = (q + 2) % 3;
-        f[q] = df_mul(sin_mid(S[u][0], S[v][0]), sin_mid(S[u][1], S[v][1]));
-      }
+      for (int q = 0; q < 3; ++q) f[q] = sinprod_mid(P[(q + 1) % 3], P[(q + 2) % 3]);
     } else if (f_kind == FEM_F_QPVALUES) {
 #pragma unroll
       for (int q = 0; q < 3; ++q) f[q] = df_from_double(__ldg(f_arg + (size_t)t * 3 + q));

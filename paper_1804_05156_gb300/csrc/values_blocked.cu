@@ -135,8 +135,10 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
     for (int m = 0; m < D; ++m) x.x[m] = __ldg(node + (size_t)R * D + m);
     xs[v] = x;
     if (sinprod2) {
+      df2 Pv[4];
+      sin_products(sincospi_half(split3(x.x[0]), tab), sincospi_half(split3(x.x[1]), tab), Pv);
 #pragma unroll
-      for (int m = 0; m < D; ++m) scs[v * D + m] = sincospi_half(split3(x.x[m]), tab);
+      for (int c = 0; c < 4; ++c) reinterpret_cast<df2*>(scs)[v * 4 + c] = Pv[c];
     }
   }
   // the block's records and element data, loaded once, coalesced (their latency overlaps the staging)
@@ -214,8 +216,9 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
       LocalDF<D> L;
       if constexpr (D == 2) {
         const VtxDF<2>* const V[3] = {&xs[lv[0]], &xs[lv[1]], &xs[lv[2]]};
-        const SC* const S[3] = {&scs[lv[0] * 2], &scs[lv[1] * 2], &scs[lv[2] * 2]};
-        st = worst(st, element_df2(V, S, kt, want_a, want_b, f_kind, fconst, f_arg, t, L));
+        const df2* sp = reinterpret_cast<const df2*>(scs);
+        const df2* const Pv[3] = {sp + lv[0] * 4, sp + lv[1] * 4, sp + lv[2] * 4};
+        st = worst(st, element_df2(V, Pv, kt, want_a, want_b, f_kind, fconst, f_arg, t, L));
       } else {
         const VtxDF<3>* const V[4] = {&xs[lv[0]], &xs[lv[1]], &xs[lv[2]], &xs[lv[3]]};
         st = worst(st, element_df3(V, kt, want_a, want_b, f_kind, fconst, f_arg, t, tab, L));

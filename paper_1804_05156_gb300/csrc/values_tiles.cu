@@ -68,12 +68,12 @@ struct RowArgs {
   bool diag_in_packet;  // the packet's last pair is the diagonal entry (mass matrix), not a load term
 };
 
-// Staged 2-D record: the coordinates and, for the sine-product load, sin/cos(pi x/2) of each coordinate,
-// 48 bytes (three 16-byte bank groups): a warp's scattered reads of the records of different vertices
-// fall on all eight 16-byte groups of banks instead of four.
+// Staged 2-D record: the coordinates and, for the sine-product load, the vertex's sine products
+// (sin_products), 48 bytes (three 16-byte bank groups): a warp's scattered reads of the records of
+// different vertices fall on all eight 16-byte groups of banks instead of four.
 struct __align__(16) Vtx2 {
   VtxDF<2> v;
-  SC sc[2];
+  df2 P[4];
 };
 template <int D>
 __host__ __device__ constexpr int staged_vtx_bytes() { return D == 2 ? (int)sizeof(Vtx2) : (int)sizeof(VtxDF<3>); }
@@ -111,10 +111,7 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
     if constexpr (D == 2) {
       Vtx2* rec = reinterpret_cast<Vtx2*>(sm) + v;
       rec->v = x;
-      if (sinprod2) {
-#pragma unroll
-        for (int m = 0; m < 2; ++m) rec->sc[m] = sincospi_half(split3(x.x[m]), tab);
-      }
+      if (sinprod2) sin_products(sincospi_half(split3(x.x[0]), tab), sincospi_half(split3(x.x[1]), tab), rec->P);
     } else {
       xs[v] = x;
     }
@@ -148,8 +145,8 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
   } else if constexpr (D == 2) {
     const Vtx2* rec = reinterpret_cast<const Vtx2*>(sm);
     const VtxDF<2>* const V2[3] = {V[0], V[1], V[2]};
-    const SC* const S[3] = {rec[lv[0]].sc, rec[lv[1]].sc, rec[lv[2]].sc};
-    st = worst(st, element_df2(V2, S, kt, want_a, want_b, f_kind, fconst, f_arg, t, L, false));  // diagonals: in the gather
+    const df2* const Pv[3] = {rec[lv[0]].P, rec[lv[1]].P, rec[lv[2]].P};
+    st = worst(st, element_df2(V2, Pv, kt, want_a, want_b, f_kind, fconst, f_arg, t, L, false));  // diagonals: in the gather
   } else {
     const VtxDF<3>* const V3[4] = {V[0], V[1], V[2], V[3]};
     st = worst(st, element_df3(V3, kt, want_a, want_b, f_kind, fconst, f_arg, t, tab, L, false));  // diagonals: in the gather
