@@ -304,11 +304,33 @@ static double sinpi_ref(double x) {
   return (fmod(fabs(j), 2.0) == 1.0) ? -s : s;
 }
 
-static double f_eval(int kind, int d, const double* p, const double* farg, int64_t t, int q, int nq) {
+/* sin(pi x_m) and cos(pi x_m) at the point x = sum_i lam[i] x_i of element e (coordinate m). The vertices
+ * are first moved by the integer k nearest to the element's first vertex (exact differences), the point is
+ * formed from the moved vertices, and sin(pi (y + k)) = (-1)^k sin(pi y): next to an integer the point keeps
+ * its relative accuracy, which forming x first (a sum near the integer, rounded to the integer's ulp) would
+ * lose. */
+static void sincos_at(int d, const double* node, const int32_t* e, const double* lam, int m, double* s, double* c) {
+  double k0 = nearbyint(node[d * (int64_t)e[0] + m]);
+  double y = 0.0;
+  for (int i = 0; i <= d; ++i) y = y + lam[i] * (node[d * (int64_t)e[i] + m] - k0);
+  double j = nearbyint(y);
+  double r = y - j;
+  int odd = (fmod(fabs(k0), 2.0) == 1.0) != (fmod(fabs(j), 2.0) == 1.0);
+  *s = odd ? -sin(M_PI * r) : sin(M_PI * r);
+  *c = odd ? -cos(M_PI * r) : cos(M_PI * r);
+}
+
+/* f at quadrature point q of element t, barycentric weights lam (kind 1 through sincos_at) */
+static double f_eval(int kind, int d, const double* node, const int32_t* e, const double* lam, const double* farg,
+                     int64_t t, int q, int nq) {
   if (kind == 0) return farg ? farg[0] : 1.0;
   if (kind == 1) {
     double v = 1.0;
-    for (int m = 0; m < d; ++m) v = v * sinpi_ref(p[m]);
+    for (int m = 0; m < d; ++m) {
+      double sm, cm;
+      sincos_at(d, node, e, lam, m, &sm, &cm);
+      v = v * sm;
+    }
     return v;
   }
   return farg[t * nq + q];
@@ -357,7 +379,7 @@ int ora_rhs(int d, int64_t N, int64_t NT, const double* node, const int32_t* ele
     double pts[4][3], lam[4][4];
     int nq = ora_quad_points(d, node, e, pts, lam);
     double fq[4];
-    for (int q = 0; q < nq; ++q) fq[q] = f_eval(fkind, d, pts[q], farg, t, q, nq);
+    for (int q = 0; q < nq; ++q) fq[q] = f_eval(fkind, d, node, e, lam[q], farg, t, q, nq);
     for (int i = 0; i <= d; ++i) {
       double bt;
       if (d == 2) {
@@ -484,21 +506,14 @@ int ora_dirichlet(int64_t N, const int64_t* row_ptr, const int64_t* col, const u
  * gradient through f (f values are inputs).
  * Node gradients are summed over incident elements in element order.
  * ------------------------------------------------------------------------------------------------ */
-static void f_grad(int kind, int d, const double* p, double* g) {
+static void f_grad(int kind, int d, const double* node, const int32_t* e, const double* lam, double* g) {
   for (int m = 0; m < d; ++m) g[m] = 0.0;
   if (kind != 1) return;
+  double sv[3], cv[3];
+  for (int m = 0; m < d; ++m) sincos_at(d, node, e, lam, m, &sv[m], &cv[m]);
   for (int m = 0; m < d; ++m) {
     double v = 1.0;
-    for (int q = 0; q < d; ++q) {
-      if (q == m) {
-        double j = nearbyint(p[q]);
-        double rr = p[q] - j;
-        double c = M_PI * cos(M_PI * rr);
-        v = v * ((fmod(fabs(j), 2.0) == 1.0) ? -c : c);
-      } else {
-        v = v * sinpi_ref(p[q]);
-      }
-    }
+    for (int q = 0; q < d; ++q) v = v * ((q == m) ? M_PI * cv[q] : sv[q]);
     g[m] = v;
   }
 }
@@ -542,8 +557,8 @@ int ora_backward(int d, int64_t N, int64_t NT, const double* node, const int32_t
     int nq = ora_quad_points(d, node, e, pts, lam);
     double wq = (d == 2) ? 1.0 / 3.0 : 1.0 / 4.0;
     for (int q = 0; q < nq; ++q) {
-      fq[q] = f_eval(fkind, d, pts[q], farg, t, q, nq);
-      f_grad(fkind, d, pts[q], gf[q]);
+      fq[q] = f_eval(fkind, d, node, e, lam[q], farg, t, q, nq);
+      f_grad(fkind, d, node, e, lam[q], gf[q]);
     }
     double Rb = 0.0, Rba = 0.0;  /* sum_i r_i sum_q w_q f_q lambda_i(q), and its magnitude */
     if (r)
@@ -848,7 +863,7 @@ int ora_rhs_rule(int d, int64_t N, int64_t NT, const double* node, const int32_t
         f = 1.0;
         for (int m = 0; m < d; ++m) f = f * (fmod(k0[m], 2.0) != 0.0 ? -1.0 : 1.0) * sinpi_ref(z[m]);
       } else {
-        f = f_eval(fkind, d, p, farg, t, q, nq);
+        f = f_eval(fkind, d, node, e, bary + q * d1, farg, t, q, nq);
       }
       for (int i = 0; i < d1; ++i) c[i] = c[i] + (w[q] * f) * bary[q * d1 + i];
     }

@@ -49,8 +49,7 @@ __device__ __forceinline__ int element_adjoint(const VtxDF<D>* const (&V)[D + 1]
   int s;
   if constexpr (D == 2) {
     df2 ev[3][2];
-    s = tri_edges(V, ev);
-    dmeas = df_dot2m(ev[1][0], ev[2][1], ev[1][1], ev[2][0]);
+    s = tri_edges(V, ev, dmeas);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       n[i][0] = df_neg(ev[i][1]);

@@ -249,12 +249,47 @@ __device__ __forceinline__ double df_to_double(df2 v) { return __dadd_rn(f2d_bit
 // each as a (hi, lo) float pair: float4(sin.hi, sin.lo, cos.hi, cos.lo).
 constexpr int kSinTabN = 1024;
 
-// sin(pi r) and cos(pi r) for a df r with |r| <= 1/2 (table-driven: r = k/2048 + d, then the Taylor
-// series of sin and cos of theta = pi d, |theta| <= pi/4096, combined by the angle-addition formulas).
+// sin(theta) and cos(theta) for a small df theta (|theta| < pi/512): theta - theta^3/6 + theta^5/120 with the
+// cubic term in float-float, 1 - theta^2/2 + theta^4/24 with theta^2 in float-float (the next terms are below
+// 2^-57 relative); no term cancels another.
+__device__ __forceinline__ void df_sincos_series(df2 th, df2& s, df2& c) {
+  df2 sq = two_prod(th.h, th.h);
+  sq.l = __fmaf_rn(2.0f * th.h, th.l, sq.l);
+  const float t2 = sq.h;
+  const df2 SIXTH = {0.1666666716337204f, -4.9670538793e-09f};
+  const df2 c3 = df_mul(df_mul(th, sq), SIXTH);  // theta^3 / 6
+  const float t5 = __fmul_rn(__fmul_rn(th.h, __fmul_rn(t2, t2)), 1.0f / 120.0f);
+  s = df_add(th, df2{-c3.h, __fsub_rn(t5, c3.l)});
+  const df2 one_m = two_sum(1.0f, -0.5f * sq.h);
+  c = fast_two_sum(one_m.h, __fadd_rn(one_m.l, __fadd_rn(-0.5f * sq.l, __fmul_rn(__fmul_rn(t2, t2), 1.0f / 24.0f))));
+}
+
+// sin(pi r) and cos(pi r) for a df r with |r| <= 1/2. In the middle of the range (table-driven): r = k/2048 +
+// d with k = rint(2048 r), |d| <= 1/4096, the Taylor series of sin and cos of theta = pi d combined with the
+// table's sin, cos(pi k/2048) by the angle-addition formulas; there 3 <= |k| <= 1021, so where the two terms
+// of an addition have opposite signs their magnitudes add up to at most 7/5 of the result's (|k| + 1/2 over
+// |k| - 1/2). At the ends, where that ratio would grow to 3 (|k| = 1 or 1023), the series are
+// used directly: for |r| < 5/4096 on theta = pi r, and for 1/2 - |r| < 5/4096 on theta' = pi (1/2 - |r|),
+// with sin(pi |r|) = cos(theta') and cos(pi |r|) = sin(theta').
 __device__ __forceinline__ void df_sincospi_small(df2 r, const float4* __restrict__ tab, df2& s, df2& c) {
+  const df2 PI = {3.14159274101257324f, -8.74227765734758577e-8f};
+  const float ar = fabsf(r.h);
+  if (ar < 5.0f / 4096.0f) {
+    df_sincos_series(df_mul(PI, r), s, c);
+    return;
+  }
+  if (ar > 0.5f - 5.0f / 4096.0f) {
+    const bool neg = r.h < 0.0f;
+    const df2 ra = neg ? df_neg(r) : r;
+    const df2 rp = fast_two_sum(__fsub_rn(0.5f, ra.h), -ra.l);  // 1/2 - |r|, exact: 0.5 - ra.h by Sterbenz
+    df2 sp, cp;
+    df_sincos_series(df_mul(PI, rp), sp, cp);
+    s = neg ? df_neg(cp) : cp;
+    c = sp;
+    return;
+  }
   const float kf = rintf(__fmul_rn(r.h, 2048.0f));
   const df2 dlt = fast_two_sum(__fsub_rn(r.h, __fmul_rn(kf, 1.0f / 2048.0f)), r.l);
-  const df2 PI = {3.14159274101257324f, -8.74227765734758577e-8f};
   const df2 th = df_mul(PI, dlt);
   const float t2 = __fmul_rn(th.h, th.h);
   // sin(theta) = theta (1 - theta^2/6 + theta^4/120)

@@ -122,8 +122,10 @@ __device__ __forceinline__ float lead_float(double x) {
 
 // ---- element frames: FP64 edges, scaled by 2^-s --------------------------------------------------
 
-// Triangle: side vectors ve_i (opposite vertex i) as float pairs scaled by 2^-s; returns s.
-__device__ __forceinline__ int tri_edges(const VtxDF<2>* const (&V)[3], df2 (&e)[3][2]) {
+// Triangle: side vectors ve_i (opposite vertex i) as float pairs scaled by 2^-s, and twice the signed area
+// ve_1 x ve_2 scaled by 2^-2s, formed in FP64 from the FP64 sides (one product, one fused multiply-add:
+// within 2^-52 of |ve_1x ve_2y| + |ve_1y ve_2x|) and then split; returns s.
+__device__ __forceinline__ int tri_edges(const VtxDF<2>* const (&V)[3], df2 (&e)[3][2], df2& a2) {
   double ed[3][2];
 #pragma unroll
   for (int m = 0; m < 2; ++m) {
@@ -141,6 +143,7 @@ __device__ __forceinline__ int tri_edges(const VtxDF<2>* const (&V)[3], df2 (&e)
   for (int q = 0; q < 3; ++q)
 #pragma unroll
     for (int m = 0; m < 2; ++m) e[q][m] = df_from_double_shift(ed[q][m], s);
+  a2 = df_from_double_shift(__fma_rn(ed[1][0], ed[2][1], -__dmul_rn(ed[1][1], ed[2][0])), 2 * s);
   return s;
 }
 
@@ -189,9 +192,8 @@ __device__ __forceinline__ int tet_frame(const VtxDF<3>* const (&V)[4], df2 (&e)
 __device__ __forceinline__ int element_df2(const VtxDF<2>* const (&V)[3], const df2* const (&P)[3], df2 kt, bool want_a,
                                            bool want_b, int f_kind, df2 fconst, const double* __restrict__ f_arg,
                                            int t, LocalDF<2>& L, bool want_diag = true) {
-  df2 e[3][2];
-  const int s = tri_edges(V, e);
-  const df2 a2 = df_dot2m(e[1][0], e[2][1], e[1][1], e[2][0]);  // twice the signed area, times 2^-2s
+  df2 e[3][2], a2;
+  const int s = tri_edges(V, e, a2);  // a2: twice the signed area, times 2^-2s
   const df2 a2abs = a2.h < 0.0f ? df_neg(a2) : a2;
   int st = (a2abs.h > 0.0f && a2abs.h < INFINITY) ? FEM_OK : FEM_ERR_DEGENERATE;
   if (want_a) {
@@ -348,14 +350,13 @@ __device__ __forceinline__ df2 df_quad(const df2 (&n)[D], const df2 (&K)[D][D], 
 template <int D>
 __device__ __forceinline__ int element_normals_df(const VtxDF<D>* const (&V)[D + 1], df2 (&n)[D + 1][D], df2& dm) {
   if constexpr (D == 2) {
-    df2 e[3][2];
-    const int s = tri_edges(V, e);
+    df2 e[3][2], a2;
+    const int s = tri_edges(V, e, a2);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       n[i][0] = df_neg(e[i][1]);
       n[i][1] = e[i][0];
     }
-    const df2 a2 = df_dot2m(e[1][0], e[2][1], e[1][1], e[2][0]);
     dm = a2.h < 0.0f ? df_neg(a2) : a2;
     return s;
   } else {

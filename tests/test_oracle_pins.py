@@ -773,6 +773,45 @@ def _exact_sine_load(d, node, elem):
 
 
 @pytest.mark.parametrize("d", [2, 3])
+def test_sine_load_next_to_the_integers_keeps_relative_accuracy(d):
+    """The load vector of f = prod sin(pi x_m) (Sec. 3.2 midpoint rule; 3-D four-point rule) on one element
+    whose vertices lie within 4e-4 of the corner (1, 1[, 1]), where f is about 1e-3 per coordinate: against
+    the same rule evaluated in 40-digit arithmetic at the exact points, every entry within 2^-48 relative.
+    Forming a point first and reducing it by the integer afterwards (the sum of coordinates near 2 rounds to
+    2^-52) would be off by about 1e-12 here."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    rng = np.random.default_rng(7 + d)
+    if d == 2:
+        node = np.array([[1 - 3.7e-4, 1 - 1.1e-4], [1 - 0.9e-4, 1 - 3.3e-4], [1 - 1.3e-4, 1 - 0.7e-4]])
+        node += rng.uniform(-1e-6, 1e-6, node.shape)
+    else:
+        node = np.array([[1 - 3.7e-4, 1 - 1.1e-4, 1 - 2.1e-4], [1 - 0.9e-4, 1 - 3.3e-4, 1 - 1.9e-4],
+                         [1 - 1.3e-4, 1 - 0.7e-4, 1 - 3.9e-4], [1 - 2.2e-4, 1 - 2.6e-4, 1 - 0.6e-4]])
+        node += rng.uniform(-1e-6, 1e-6, node.shape)
+    elem = np.arange(d + 1, dtype=np.int32)[None, :]
+    meas = oracle.measure(d, node, elem)[0]
+    if meas < 0:  # positive orientation
+        elem = elem[:, [1, 0] + list(range(2, d + 1))]
+        meas = -meas
+    b = oracle.rhs(d, node, elem, oracle.F_SINPROD)
+    X = [[mpmath.mpf(float(v)) for v in node[i]] for i in elem[0]]
+    if d == 2:
+        mids = [[(X[(q + 1) % 3][m] + X[(q + 2) % 3][m]) / 2 for m in range(2)] for q in range(3)]
+        f = [mpmath.sin(mpmath.pi * p[0]) * mpmath.sin(mpmath.pi * p[1]) for p in mids]
+        exact = [mpmath.mpf(float(meas)) * (f[(i + 1) % 3] + f[(i + 2) % 3]) / 6 for i in range(3)]
+    else:
+        s5 = mpmath.sqrt(5)
+        al, be = (5 + 3 * s5) / 20, (5 - s5) / 20
+        pts = [[sum((al if i == q else be) * X[i][m] for i in range(4)) for m in range(3)] for q in range(4)]
+        f = [mpmath.sin(mpmath.pi * p[0]) * mpmath.sin(mpmath.pi * p[1]) * mpmath.sin(mpmath.pi * p[2]) for p in pts]
+        exact = [mpmath.mpf(float(meas)) / 4 * sum(f[q] * (al if i == q else be) for q in range(4)) for i in range(4)]
+    for i in range(d + 1):
+        v = int(elem[0][i])
+        assert abs(mpmath.mpf(float(b[v])) - exact[i]) <= 2.0 ** -48 * abs(exact[i]), (i, float(b[v]), exact[i])
+
+
+@pytest.mark.parametrize("d", [2, 3])
 def test_rule_sine_product_branch(d):
     """The sine-product branch of the rule load vector (the points are shifted by an integer near the
     element and the sign follows its parity) pinned two ways that do not use that branch:
