@@ -271,6 +271,29 @@ __device__ __forceinline__ void df_sincos_series(df2 th, df2& s, df2& c) {
 // |k| - 1/2). At the ends, where that ratio would grow to 3 (|k| = 1 or 1023), the series are
 // used directly: for |r| < 5/4096 on theta = pi r, and for 1/2 - |r| < 5/4096 on theta' = pi (1/2 - |r|),
 // with sin(pi |r|) = cos(theta') and cos(pi |r|) = sin(theta').
+// The table step: sin and cos of pi (k/2048 + d) for 3 <= |k| <= 1021 (or any k when d has the sign of k)
+// and |d| <= 1/4096, d a float pair accurate to 2^-48 of itself.
+__device__ __forceinline__ void df_sincospi_table(int k, df2 dlt, const float4* __restrict__ tab, df2& s, df2& c) {
+  const df2 PI = {3.14159274101257324f, -8.74227765734758577e-8f};
+  const df2 th = df_mul(PI, dlt);
+  const float t2 = __fmul_rn(th.h, th.h);
+  // sin(theta) = theta (1 - theta^2/6 + theta^4/120)
+  const float q = __fmul_rn(t2, __fmaf_rn(t2, -1.0f / 120.0f, 1.0f / 6.0f));
+  const df2 sn = fast_two_sum(th.h, __fmaf_rn(-th.h, q, th.l));
+  // cos(theta) = 1 - theta^2/2 + theta^4/24, with theta^2 in df
+  df2 sq = two_prod(th.h, th.h);
+  sq.l = __fmaf_rn(2.0f * th.h, th.l, sq.l);
+  const df2 one_m = two_sum(1.0f, -0.5f * sq.h);
+  const float tail = __fadd_rn(-0.5f * sq.l, __fmul_rn(__fmul_rn(t2, t2), 1.0f / 24.0f));
+  const df2 cs = fast_two_sum(one_m.h, __fadd_rn(one_m.l, tail));
+  const int ak = min(k < 0 ? -k : k, kSinTabN);  // |k| <= 1024 for |r| <= 1/2; the bound keeps the read in the table
+  const float4 e = tab[ak];
+  df2 Sk = {e.x, e.y}, Ck = {e.z, e.w};
+  if (k < 0) Sk = df_neg(Sk);
+  s = df_add(df_mul(Sk, cs), df_mul(Ck, sn));
+  c = df_sub(df_mul(Ck, cs), df_mul(Sk, sn));
+}
+
 __device__ __forceinline__ void df_sincospi_small(df2 r, const float4* __restrict__ tab, df2& s, df2& c) {
   const df2 PI = {3.14159274101257324f, -8.74227765734758577e-8f};
   const float ar = fabsf(r.h);
@@ -289,25 +312,7 @@ __device__ __forceinline__ void df_sincospi_small(df2 r, const float4* __restric
     return;
   }
   const float kf = rintf(__fmul_rn(r.h, 2048.0f));
-  const df2 dlt = fast_two_sum(__fsub_rn(r.h, __fmul_rn(kf, 1.0f / 2048.0f)), r.l);
-  const df2 th = df_mul(PI, dlt);
-  const float t2 = __fmul_rn(th.h, th.h);
-  // sin(theta) = theta (1 - theta^2/6 + theta^4/120)
-  const float q = __fmul_rn(t2, __fmaf_rn(t2, -1.0f / 120.0f, 1.0f / 6.0f));
-  const df2 sn = fast_two_sum(th.h, __fmaf_rn(-th.h, q, th.l));
-  // cos(theta) = 1 - theta^2/2 + theta^4/24, with theta^2 in df
-  df2 sq = two_prod(th.h, th.h);
-  sq.l = __fmaf_rn(2.0f * th.h, th.l, sq.l);
-  const df2 one_m = two_sum(1.0f, -0.5f * sq.h);
-  const float tail = __fadd_rn(-0.5f * sq.l, __fmul_rn(__fmul_rn(t2, t2), 1.0f / 24.0f));
-  const df2 cs = fast_two_sum(one_m.h, __fadd_rn(one_m.l, tail));
-  const int k = (int)kf;
-  const int ak = min(k < 0 ? -k : k, kSinTabN);  // |r| <= 1/2 gives |k| <= 1024; the bound keeps the read in the table
-  const float4 e = tab[ak];
-  df2 Sk = {e.x, e.y}, Ck = {e.z, e.w};
-  if (k < 0) Sk = df_neg(Sk);
-  s = df_add(df_mul(Sk, cs), df_mul(Ck, sn));
-  c = df_sub(df_mul(Ck, cs), df_mul(Sk, sn));
+  df_sincospi_table((int)kf, fast_two_sum(__fsub_rn(r.h, __fmul_rn(kf, 1.0f / 2048.0f)), r.l), tab, s, c);
 }
 
 // sin(pi x) and cos(pi x) for a df x of any size (reduction as in df_sinpi below).

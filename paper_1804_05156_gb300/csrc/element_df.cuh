@@ -55,35 +55,51 @@ __device__ __forceinline__ df2 coef_df(double v, int& st) {
 
 __device__ __forceinline__ int int_parity(float n) { return fabsf(n) < 16777216.0f ? (__float2int_rn(n) & 1) : 0; }
 
-// sin(pi x/2) and cos(pi x/2) from the exact split x = a + b + c: each half-part is reduced by its own
-// nearest integer (exactly: every remainder is at most 1/2), the three remainders are added in float-float
-// and reduced once more, so x/2 = n + r with |r| <= 1/2 and r exact to ~2^-47 of |r| for any x (values near
-// the zeros of the sine keep their relative accuracy; large x keep every bit of x).
+// sin(pi x/2) and cos(pi x/2) from the exact split x = a + b + c. x/2 = n + r with n = rint(a/2) and the
+// remainder r = (a/2 - n) + b/2 + c/2, every part exact. Coordinates below 2^15 (|b/2| < 2^-10, c/2 below
+// the last bit of b/2) take the steps of df_sincospi_small, but the small quantity each step works on (r
+// itself next to 0; 1/2 - |r| next to 1/2, at most 2^-10 past 0; r - k/2048 in the table step) is formed
+// from the exact parts with two-sums, so it keeps 2^-48 of itself and the cosine next to its zeros keeps
+// its relative accuracy (r carried as one float pair would have lost the last bits of x). Larger coordinates
+// reduce each part by its own nearest integer, then the float-float sum once more; their remainder is
+// carried to 2^-48 of 1/2.
 __device__ __forceinline__ SC sincospi_half(const f3& x, const float4* __restrict__ tab) {
   const float ah = 0.5f * x.a, bh = 0.5f * x.b, ch = 0.5f * x.c;
   const float na = rintf(ah);
-  df2 r;
+  SC o;
   int par;
-  if (fabsf(x.a) < 4194304.0f) {
-    // |x| < 2^22: |b/2| < 2^-3 and c/2 is below the last bit of b/2, so the remainder (a/2 - rint(a/2))
-    // + b/2 + c/2 is formed exactly in float-float (a two-sum, then c/2 into the trailing part), is at most
-    // 5/8 in magnitude, and one more reduction by its nearest integer brings it to [-1/2, 1/2]; both
-    // integers are below 2^21
-    const df2 r0 = two_sum(__fsub_rn(ah, na), bh);
-    r = fast_two_sum(r0.h, __fadd_rn(r0.l, ch));
-    const float n3 = rintf(r.h);
-    r = fast_two_sum(__fsub_rn(r.h, n3), r.l);
-    par = (__float2int_rn(na) + __float2int_rn(n3)) & 1;
+  if (fabsf(x.a) < 32768.0f) {
+    const float ra = __fsub_rn(ah, na);  // |ra| <= 1/2
+    const df2 r0 = two_sum(ra, bh);      // r = r0.h + r0.l + c/2 exactly, |r| <= 1/2 + 2^-10
+    const float ar = fabsf(r0.h);
+    const df2 PI = {3.14159274101257324f, -8.74227765734758577e-8f};
+    par = __float2int_rn(na) & 1;
+    if (ar < 5.0f / 4096.0f) {  // r small: its float-float sum keeps 2^-49 of itself
+      df_sincos_series(df_mul(PI, fast_two_sum(r0.h, __fadd_rn(r0.l, ch))), o.s, o.c);
+    } else if (ar > 0.5f - 5.0f / 4096.0f) {
+      // 1/2 - |r| = (1/2 - sg ra) - sg b/2 - sg c/2; |ra| > 0.49 here, so the first difference is exact
+      const float sg = r0.h < 0.0f ? -1.0f : 1.0f;
+      const df2 p = two_sum(__fsub_rn(0.5f, sg * ra), -sg * bh);
+      df2 sp, cp;
+      df_sincos_series(df_mul(PI, fast_two_sum(p.h, __fsub_rn(p.l, sg * ch))), sp, cp);  // of pi (1/2 - |r|)
+      o.s = sg < 0.0f ? df_neg(cp) : cp;  // sin(pi r) = sg cos(pi (1/2 - |r|))
+      o.c = sp;                            // cos(pi r) = sin(pi (1/2 - |r|))
+    } else {
+      // the table step's remainder d = r - k/2048 from the exact parts: (r0.h - k/2048) exactly (Sterbenz),
+      // then the two-sum with r0.l, then c/2
+      const float kf = rintf(__fmul_rn(r0.h, 2048.0f));
+      const df2 t = two_sum(__fsub_rn(r0.h, __fmul_rn(kf, 1.0f / 2048.0f)), r0.l);
+      df_sincospi_table((int)kf, fast_two_sum(t.h, __fadd_rn(t.l, ch)), tab, o.s, o.c);
+    }
   } else {
     const float nb = rintf(bh), nc = rintf(ch);
     const df2 r0 = two_sum(__fsub_rn(ah, na), __fsub_rn(bh, nb));
-    r = df_add(r0, df2{__fsub_rn(ch, nc), 0.0f});
+    df2 r = df_add(r0, df2{__fsub_rn(ch, nc), 0.0f});
     const float n3 = rintf(r.h);
     r = fast_two_sum(__fsub_rn(r.h, n3), r.l);
     par = (int_parity(na) + int_parity(nb) + int_parity(nc) + int_parity(n3)) & 1;
+    df_sincospi_small(r, tab, o.s, o.c);
   }
-  SC o;
-  df_sincospi_small(r, tab, o.s, o.c);
   if (par) {
     o.s = df_neg(o.s);
     o.c = df_neg(o.c);

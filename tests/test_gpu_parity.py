@@ -316,6 +316,25 @@ def test_inputs_beyond_the_float_float_range_are_reported(d):
 
 
 @pytest.mark.parametrize("d", [2, 3])
+def test_every_entry_of_a_fine_mesh(d):
+    """Every CSR value and every load entry of a fine jittered mesh (1024^2 triangles, element rows
+    permuted; 64^3 Kuhn tetrahedra) against the oracle, sine-product load: the rows next to x = 1 and y = 1,
+    where sin(pi x/2) and cos(pi x/2) are taken within 1e-3 of 1/2 and the last bits of x decide the
+    cosine's relative accuracy, are among them."""
+    m = meshgen.square_mesh(1024, 0.2, 1804, permute=True) if d == 2 else meshgen.kuhn_mesh(64, 0.1, 1807)
+    node, elem = m["node"], m["elem"]
+    k = meshgen.lognormal(1804, meshgen.TAG_COEF, elem.shape[0])
+    p = fa.Pattern(dev(elem), node.shape[0])
+    fa.fem_pattern_set_locality(p, dev(node))
+    val, b = fa.assemble(p, dev(node), dev(k), fa.FEM_F_SINPROD)
+    fa.get_error()
+    _, _, vo, so = oracle.assemble(d, node, elem, k)
+    bo = oracle.rhs(d, node, elem, oracle.F_SINPROD)
+    assert_close_scaled(host(val), vo, so, what="stiffness")
+    assert_close_scaled(host(b), bo, np.abs(bo) + 1e-300, what="rhs")
+
+
+@pytest.mark.parametrize("d", [2, 3])
 def test_sine_load_at_large_coordinates(d):
     """The sine-product load on a uniform mesh moved by 2^26 in every coordinate (plus 1 in the first, so
     the sign flips): the coordinates stay exact in FP64 (multiples of 2^-6 or 2^-2), and by periodicity the
