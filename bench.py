@@ -372,7 +372,7 @@ def run_ours(args):
         fa.build()  # one build (a no-op when the library is current); the other ranks wait for it
     if dist:
         dist.barrier()
-    mesh = meshgen.make_config(args.config)
+    mesh = meshgen.make_config(args.config, n=args.grid)
     d, node, elem, k = mesh["d"], mesh["node"], mesh["elem"], mesh["coef"]
     NT_job = elem.shape[0] * ws  # weak scaling: every rank assembles its own copy of the workload
     if args.shard == "rows" and ws > 1:
@@ -452,8 +452,9 @@ def run_ours(args):
     achieved = alg / (k_ms * 1e-3) / 1e9
     shape = fa.fem_pattern_launch_shape(p)
     path = fa.fem_pattern_value_path(p)
-    traffic, traffic_src = profiled(names, args.config, path, shape)
-    inst, inst_src = profiled(names, args.config, path, shape, "inst", "warp_inst_per_launch")
+    prof_cfg = args.config if args.grid is None else "%s@%d" % (args.config, args.grid)  # records are per workload
+    traffic, traffic_src = profiled(names, prof_cfg, path, shape)
+    inst, inst_src = profiled(names, prof_cfg, path, shape, "inst", "warp_inst_per_launch")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "traffic_source": traffic_src,
             # the DRAM bytes ncu counted for these kernels over their time here: the rate the memory system
@@ -519,7 +520,9 @@ def run_ours(args):
            "arithmetic": ("float-float on the FP32 pipe (pairs of floats, ~2^-48 relative); every FP64 output "
                           "rounded once; within 1e-12 of the FP64 oracle" if args.variant == "deterministic"
                           else "FP64 (atomicAdd in FP64)"),
-           "config": {"workload": workload_name(args.config), "N": N, "NT": NT, "nnz": p.nnz,
+           "config": {"workload": workload_name(args.config) + ("" if args.grid is None else
+                                                                    " (recipe at %d cells per side)" % args.grid),
+                      "N": N, "NT": NT, "nnz": p.nnz,
                       "variant": args.variant, "l2": "flushed by a 512 MB write between steps (outside timing)",
                       "parallelism": ("single GPU" if ws == 1 else
                                       "row ownership, rank-local rows of one mesh" if args.shard == "rows" else
@@ -612,6 +615,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the 3-D, batched and fwd+bwd rows")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-sample", type=int, default=400_000)
+    ap.add_argument("--grid", type=int, default=None,
+                    help="cells per side instead of the workload's own (the same recipe at another size; for profiling "
+                         "captures on a smaller case)")
     ap.add_argument("--shard", choices=["copies", "rows"], default="copies",
                     help="N>1: every rank assembles its own copy (weak scaling) or its rows of one mesh (strong)")
     args = ap.parse_args()
