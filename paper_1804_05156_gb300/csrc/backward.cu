@@ -57,10 +57,13 @@ __device__ __forceinline__ int element_adjoint(const VtxDF<D>* const (&V)[D + 1]
     }
   } else {
     df2 ed[3][3];
-    s = tet_frame(V, ed, n);
+    tet_frame(V, ed, n);
     dmeas = df_dot<3>(n[3], ed[2]);
+    s = 0;  // no frame in 3-D
   }
-  int st = (dmeas.h > 0.0f && dmeas.h < INFINITY) ? FEM_OK : FEM_ERR_DEGENERATE;
+  int st;
+  if constexpr (D == 3) st = tet_status(V, dmeas);
+  else st = (dmeas.h > 0.0f && dmeas.h < INFINITY) ? FEM_OK : FEM_ERR_DEGENERATE;
   const int eA = (D - 3) * s, eK = (D - 2) * s, e1 = (D - 1) * s, e2 = D * s;
   if (!(scale_in_range(eA) && scale_in_range(e2))) st = worst(st, FEM_ERR_RANGE);
   const int sA = scale_in_range(eA) ? eA : 0, sK = scale_in_range(eK) ? eK : 0;
@@ -172,11 +175,11 @@ __device__ __forceinline__ int element_adjoint(const VtxDF<D>* const (&V)[D + 1]
         const df2 al = {0.58541017770767212f, 1.8917296174e-08f}, be = {0.13819660246372223f, -1.3387116971e-09f};
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-          const float nn = rintf(lead_float(V[0]->x[m]));
-          const double nd = f2d_bits(nn);
+          const float nn = rintf(V[0]->x[m].a);
           df2 y[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) y[i] = df_from_double_shift(__dsub_rn(V[i]->x[m], nd), 0);
+          for (int i = 0; i < 4; ++i)
+            y[i] = df_add(two_sum(V[i]->x[m].a, -nn), fast_two_sum(V[i]->x[m].b, V[i]->x[m].c));
           const df2 sy = df_add(df_add(y[0], y[1]), df_add(y[2], y[3]));
           const float sgn = int_parity(nn) ? -1.0f : 1.0f;
 #pragma unroll
@@ -287,9 +290,7 @@ __global__ void __launch_bounds__(128, 4) k_backward_df(const int32_t* __restric
   for (int i = 0; i < D1; ++i) e[i] = __ldg(elem + (size_t)t * D1 + i);
   VtxDF<D> X[D1];
 #pragma unroll
-  for (int i = 0; i < D1; ++i)
-#pragma unroll
-    for (int m = 0; m < D; ++m) X[i].x[m] = __ldg(node + (size_t)e[i] * D + m);
+  for (int i = 0; i < D1; ++i) stage_vertex<D>(X[i], node + (size_t)e[i] * D);
   df2 Ws[D1][D1], rv[D1];
   if (w) sym_weights<D>(slot, NT, t, w, Ws);
   if (r) {
@@ -340,8 +341,7 @@ __global__ void __launch_bounds__(TE, 512 / TE) k_backward_tiles(
   for (int v = threadIdx.x; v < nv; v += TE) {
     const int R = __ldg(vlist + v0 + v);
     VtxDF<D> x;
-#pragma unroll
-    for (int m = 0; m < D; ++m) x.x[m] = __ldg(node + (size_t)R * D + m);
+    stage_vertex<D>(x, node + (size_t)R * D);
     xs[v] = x;
   }
   __syncthreads();

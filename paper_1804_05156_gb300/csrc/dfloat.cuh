@@ -264,15 +264,16 @@ __device__ __forceinline__ void df_sincos_series(df2 th, df2& s, df2& c) {
   c = fast_two_sum(one_m.h, __fadd_rn(one_m.l, __fadd_rn(-0.5f * sq.l, __fmul_rn(__fmul_rn(t2, t2), 1.0f / 24.0f))));
 }
 
-// sin(pi r) and cos(pi r) for a df r with |r| <= 1/2. In the middle of the range (table-driven): r = k/2048 +
-// d with k = rint(2048 r), |d| <= 1/4096, the Taylor series of sin and cos of theta = pi d combined with the
-// table's sin, cos(pi k/2048) by the angle-addition formulas; there 3 <= |k| <= 1021, so where the two terms
-// of an addition have opposite signs their magnitudes add up to at most 7/5 of the result's (|k| + 1/2 over
-// |k| - 1/2). At the ends, where that ratio would grow to 3 (|k| = 1 or 1023), the series are
-// used directly: for |r| < 5/4096 on theta = pi r, and for 1/2 - |r| < 5/4096 on theta' = pi (1/2 - |r|),
-// with sin(pi |r|) = cos(theta') and cos(pi |r|) = sin(theta').
-// The table step: sin and cos of pi (k/2048 + d) for 3 <= |k| <= 1021 (or any k when d has the sign of k)
-// and |d| <= 1/4096, d a float pair accurate to 2^-48 of itself.
+// sin(pi r) and cos(pi r) for a df r with |r| <= 1/2, table-driven: r = k/2048 + d with k = rint(2048 r),
+// |d| <= 1/4096, the Taylor series of sin and cos of theta = pi d combined with the table's sin, cos(pi k/2048)
+// by the angle-addition formulas. Where the two terms of an addition have opposite signs (d against k for the
+// sine; d with k for the cosine) their magnitudes add up to at most (|k| + 1/2) / (|k| - 1/2) times the
+// result's: 3 at |k| = 1 (sine) or 1023 (cosine), 7/5 from |k| = 3 on (and 1 at k = 0, where the sine is the
+// series itself). df_sincospi_small uses this step for every r (one path, no branches: it is evaluated at
+// every quadrature point); the staged per-vertex values (sincospi_half) take the series directly at both
+// ends, where the ratio would exceed 7/5.
+// The table step: sin and cos of pi (k/2048 + d) for |k| <= 1024 and |d| <= 1/4096, d a float pair
+// accurate to 2^-48 of itself.
 __device__ __forceinline__ void df_sincospi_table(int k, df2 dlt, const float4* __restrict__ tab, df2& s, df2& c) {
   const df2 PI = {3.14159274101257324f, -8.74227765734758577e-8f};
   const df2 th = df_mul(PI, dlt);
@@ -295,22 +296,6 @@ __device__ __forceinline__ void df_sincospi_table(int k, df2 dlt, const float4* 
 }
 
 __device__ __forceinline__ void df_sincospi_small(df2 r, const float4* __restrict__ tab, df2& s, df2& c) {
-  const df2 PI = {3.14159274101257324f, -8.74227765734758577e-8f};
-  const float ar = fabsf(r.h);
-  if (ar < 5.0f / 4096.0f) {
-    df_sincos_series(df_mul(PI, r), s, c);
-    return;
-  }
-  if (ar > 0.5f - 5.0f / 4096.0f) {
-    const bool neg = r.h < 0.0f;
-    const df2 ra = neg ? df_neg(r) : r;
-    const df2 rp = fast_two_sum(__fsub_rn(0.5f, ra.h), -ra.l);  // 1/2 - |r|, exact: 0.5 - ra.h by Sterbenz
-    df2 sp, cp;
-    df_sincos_series(df_mul(PI, rp), sp, cp);
-    s = neg ? df_neg(cp) : cp;
-    c = sp;
-    return;
-  }
   const float kf = rintf(__fmul_rn(r.h, 2048.0f));
   df_sincospi_table((int)kf, fast_two_sum(__fsub_rn(r.h, __fmul_rn(kf, 1.0f / 2048.0f)), r.l), tab, s, c);
 }

@@ -26,11 +26,28 @@
 
 namespace fem {
 
-// Staged vertex: the coordinates.
+// Staged vertex (16-byte aligned: staged vertices are read with 128-bit accesses). 2-D keeps the
+// coordinates as doubles (the edges are FP64 subtractions); 3-D keeps their exact three-float splits (the
+// edges are exact float-float differences: fifteen FP64 subtractions per tetrahedron would crowd the FP64
+// pipe).
 template <int D>
-struct __align__(16) VtxDF {  // 16-byte aligned: staged vertices are read with 128-bit accesses
-  double x[D];
+struct VtxDF;
+template <>
+struct __align__(16) VtxDF<2> {
+  double x[2];
 };
+template <>
+struct __align__(16) VtxDF<3> {
+  f3 x[3];
+};
+template <int D>
+__device__ __forceinline__ void stage_vertex(VtxDF<D>& v, const double* __restrict__ p) {
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    if constexpr (D == 2) v.x[m] = __ldg(p + m);
+    else v.x[m] = split3(__ldg(p + m));
+  }
+}
 struct __align__(16) SC {
   df2 s, c;
 };
@@ -49,7 +66,7 @@ __device__ __forceinline__ int worst(int st, int code) { return st != FEM_OK ? s
 // anything else (outside the float-float range, or not finite) sets FEM_ERR_RANGE.
 __device__ __forceinline__ df2 coef_df(double v, int& st) {
   const int E = (int)((abs_hiword(v) >> 20) & 0x7ffu);
-  if (v != 0.0 && (E < 1023 - 80 || E > 1023 + 96)) st = worst(st, FEM_ERR_RANGE);
+  if ((abs_hiword(v) | (uint32_t)__double2loint(v)) != 0u && (E < 1023 - 80 || E > 1023 + 96)) st = worst(st, FEM_ERR_RANGE);
   return df_from_double(v);
 }
 
@@ -57,10 +74,12 @@ __device__ __forceinline__ int int_parity(float n) { return fabsf(n) < 16777216.
 
 // sin(pi x/2) and cos(pi x/2) from the exact split x = a + b + c. x/2 = n + r with n = rint(a/2) and the
 // remainder r = (a/2 - n) + b/2 + c/2, every part exact. Coordinates below 2^15 (|b/2| < 2^-10, c/2 below
-// the last bit of b/2) take the steps of df_sincospi_small, but the small quantity each step works on (r
-// itself next to 0; 1/2 - |r| next to 1/2, at most 2^-10 past 0; r - k/2048 in the table step) is formed
-// from the exact parts with two-sums, so it keeps 2^-48 of itself and the cosine next to its zeros keeps
-// its relative accuracy (r carried as one float pair would have lost the last bits of x). Larger coordinates
+// the last bit of b/2) take one of three steps: the series of sin and cos of pi r for |r| < 5/4096, the
+// series of pi (1/2 - |r|) for 1/2 - |r| < 5/4096 (sin(pi |r|) = cos, cos(pi |r|) = sin of it), the table
+// step of df_sincospi_table otherwise (where its cancellation ratio is at most 7/5). The small quantity each
+// step works on (r itself next to 0; 1/2 - |r| next to 1/2, at most 2^-10 past 0; r - k/2048 in the table
+// step) is formed from the exact parts with two-sums, so it keeps 2^-48 of itself and the cosine next to its
+// zeros keeps its relative accuracy (r carried as one float pair would have lost the last bits of x). Larger coordinates
 // reduce each part by its own nearest integer, then the float-float sum once more; their remainder is
 // carried to 2^-48 of 1/2.
 __device__ __forceinline__ SC sincospi_half(const f3& x, const float4* __restrict__ tab) {
@@ -169,41 +188,39 @@ __device__ __forceinline__ void df_cross(const df2 (&u)[3], const df2 (&v)[3], d
   o[2] = df_dot2m(u[0], v[1], u[1], v[0]);
 }
 
-// Tetrahedron: edges e_m = x_{m+1} - x_0 and the scaled inward face normals n_i, from edges scaled by
-// 2^-s (normals by 2^-2s); returns s.
-__device__ __forceinline__ int tet_frame(const VtxDF<3>* const (&V)[4], df2 (&e)[3][3], df2 (&n)[4][3]) {
-  double ed[3][3], ud[3], vd[3];
+// Tetrahedron: edges e_m = x_{m+1} - x_0 and the scaled inward face normals n_i, every edge the exact
+// float-float difference of its endpoints' splits, at the element's own scale (no frame: in 3-D the extra
+// state of a scaled frame costs registers the kernels cannot spare). The products of normals (|e|^4), the
+// volume (|e|^3) and its reciprocal stay inside the float-float range for edges in [2^-24, 2^29];
+// tet_status checks that through 6 |tau|.
+__device__ __forceinline__ void tet_frame(const VtxDF<3>* const (&V)[4], df2 (&e)[3][3], df2 (&n)[4][3]) {
 #pragma unroll
-  for (int m = 0; m < 3; ++m) {
+  for (int q = 0; q < 3; ++q)
 #pragma unroll
-    for (int q = 0; q < 3; ++q) ed[q][m] = __dsub_rn(V[q + 1]->x[m], V[0]->x[m]);
-    ud[m] = __dsub_rn(V[3]->x[m], V[1]->x[m]);  // x_3 - x_1 and x_2 - x_1 (0-based): the edges of face [2 4 3]
-    vd[m] = __dsub_rn(V[2]->x[m], V[1]->x[m]);
-  }
-  uint32_t mx = 0;
-#pragma unroll
-  for (int m = 0; m < 3; ++m) {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) mx = max(mx, abs_hiword(ed[q][m]));
-    mx = max(mx, max(abs_hiword(ud[m]), abs_hiword(vd[m])));
-  }
-  const int s = exponent_of_hiword(mx);
-  df2 u[3], v[3];
-#pragma unroll
-  for (int m = 0; m < 3; ++m) {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) e[q][m] = df_from_double_shift(ed[q][m], s);
-    u[m] = df_from_double_shift(ud[m], s);
-    v[m] = df_from_double_shift(vd[m], s);
-  }
+    for (int m = 0; m < 3; ++m) e[q][m] = f3_diff(V[q + 1]->x[m], V[0]->x[m]);
   df_cross(e[1], e[2], n[1]);
   df_cross(e[2], e[0], n[2]);
   df_cross(e[0], e[1], n[3]);
+  df2 u[3], v[3];  // x_3 - x_1 and x_2 - x_1 (0-based): the edges of face [2 4 3]
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    u[m] = f3_diff(V[3]->x[m], V[1]->x[m]);
+    v[m] = f3_diff(V[2]->x[m], V[1]->x[m]);
+  }
   df_cross(u, v, n[0]);
-  return s;
+}
+// Status of a tetrahedron from its 6 tau (signed): FEM_OK within [2^-72, 2^87] (edges of about 2^-24 to
+// 2^29), FEM_ERR_RANGE above or below. A zero, negative or non-finite 6 tau is FEM_ERR_DEGENERATE when the
+// first edge's largest component is within [2^-24, 2^29] (the element itself is flat or inverted), else
+// FEM_ERR_RANGE (its volume under- or overflowed); that edge is formed again only on this rare branch.
+__device__ __forceinline__ int tet_status(const VtxDF<3>* const (&V)[4], df2 vol6) {
+  if (vol6.h > 0.0f && vol6.h < INFINITY) return (vol6.h >= 0x1p-72f && vol6.h <= 0x1p87f) ? FEM_OK : FEM_ERR_RANGE;
+  float a = 0.0f;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) a = fmaxf(a, fabsf(f3_diff(V[1]->x[m], V[0]->x[m]).h));
+  return (a >= 0x1p-24f && a <= 0x1p29f) ? FEM_ERR_DEGENERATE : FEM_ERR_RANGE;
 }
 
-// want_diag = false sets L.a[0..2] (the diagonals) to 0, for callers that form them from row sums.
 // P: the per-vertex sine products (sin_products) when f_kind is FEM_F_SINPROD.
 __device__ __forceinline__ int element_df2(const VtxDF<2>* const (&V)[3], const df2* const (&P)[3], df2 kt, bool want_a,
                                            bool want_b, int f_kind, df2 fconst, const double* __restrict__ f_arg,
@@ -260,15 +277,12 @@ __device__ __forceinline__ int element_df3(const VtxDF<3>* const (&V)[4], df2 kt
                                            int f_kind, df2 fconst, const double* __restrict__ f_arg, int t,
                                            const float4* __restrict__ tab, LocalDF<3>& L, bool want_diag = true) {
   df2 e[3][3], n[4][3];
-  const int s = tet_frame(V, e, n);
-  const df2 vol6 = df_dot<3>(n[3], e[2]);  // 6 x signed volume, times 2^-3s
-  int st = (vol6.h > 0.0f && vol6.h < INFINITY) ? FEM_OK : FEM_ERR_DEGENERATE;
+  tet_frame(V, e, n);
+  const df2 vol6 = df_dot<3>(n[3], e[2]);  // 6 x signed volume
+  int st = tet_status(V, vol6);
   if (want_a) {
-    // k / (36 vol) times 2^s: the 3-D stiffness is homogeneous of degree 1; k 2^s within [2^-80, 2^100]
-    // keeps every entry in range (no per-entry checks)
-    const int ke = (int)((__float_as_uint(kt.h) >> 23) & 0xffu) - 127;
-    if (!scale_in_range(s) || (kt.h != 0.0f && (ke + s < -80 || ke + s > 100))) st = worst(st, FEM_ERR_RANGE);
-    const df2 sc = df_ldexp(df_mul(kt, df_recip(df_mul_f(vol6, 6.0f))), scale_in_range(s) ? s : 0);
+    // k / (36 vol); with k in [2^-80, 2^96] and the edges in range every entry is (no per-entry checks)
+    const df2 sc = df_mul(kt, df_recip(df_mul_f(vol6, 6.0f)));
 #pragma unroll
     for (int i = 0; i < 4; ++i) L.a[i] = df2{0.0f, 0.0f};
 #pragma unroll
@@ -284,8 +298,7 @@ __device__ __forceinline__ int element_df3(const VtxDF<3>* const (&V)[4], df2 kt
       }
   }
   if (want_b) {
-    if (!scale_in_range(3 * s)) st = worst(st, FEM_ERR_RANGE);
-    const df2 vol = df_ldexp(df_mul(vol6, df2{0.1666666716337204f, -4.9670538793e-09f}), scale_in_range(3 * s) ? 3 * s : 0);
+    const df2 vol = df_mul(vol6, df2{0.1666666716337204f, -4.9670538793e-09f});
     df2 f[4];
     if (f_kind == FEM_F_SINPROD) {
       // points x_q = sum_i lambda_i(q) x_i; per coordinate, shifted by an integer n near the element
@@ -295,11 +308,10 @@ __device__ __forceinline__ int element_df3(const VtxDF<3>* const (&V)[4], df2 kt
       for (int q = 0; q < 4; ++q) f[q] = df_from(1.0f);
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
-        const float nn = rintf(lead_float(V[0]->x[m]));
-        const double nd = f2d_bits(nn);
-        df2 y[4];
+        const float nn = rintf(V[0]->x[m].a);
+        df2 y[4];  // x_i - n, exact: the leading parts' difference by two-sum, then the other parts
 #pragma unroll
-        for (int i = 0; i < 4; ++i) y[i] = df_from_double_shift(__dsub_rn(V[i]->x[m], nd), 0);
+        for (int i = 0; i < 4; ++i) y[i] = df_add(two_sum(V[i]->x[m].a, -nn), fast_two_sum(V[i]->x[m].b, V[i]->x[m].c));
         const df2 sy = df_add(df_add(y[0], y[1]), df_add(y[2], y[3]));
         const float sgn = int_parity(nn) ? -1.0f : 1.0f;
 #pragma unroll
@@ -361,8 +373,9 @@ __device__ __forceinline__ df2 df_quad(const df2 (&n)[D], const df2 (&K)[D][D], 
   return df_dot<D>(n, Km);
 }
 
-// Scaled normals n_i and d! |tau| (2-D: |2 area|, the paper's abs(); 3-D: 6 x signed volume) in the
-// element's frame scaled by 2^-s (normals times 2^-(d-1)s, the measure times 2^-ds); returns s.
+// Scaled normals n_i and d! |tau| (2-D: |2 area|, the paper's abs(); 3-D: 6 x signed volume); 2-D in the
+// element's frame scaled by 2^-s (normals times 2^-s, the measure times 2^-2s), returns s; 3-D at the
+// element's own scale, returns 0.
 template <int D>
 __device__ __forceinline__ int element_normals_df(const VtxDF<D>* const (&V)[D + 1], df2 (&n)[D + 1][D], df2& dm) {
   if constexpr (D == 2) {
@@ -377,9 +390,9 @@ __device__ __forceinline__ int element_normals_df(const VtxDF<D>* const (&V)[D +
     return s;
   } else {
     df2 e[3][3];
-    const int s = tet_frame(V, e, n);
+    tet_frame(V, e, n);
     dm = df_dot<3>(n[3], e[2]);
-    return s;
+    return 0;  // no frame in 3-D; tet_status tells whether the element is in range
   }
 }
 
@@ -391,7 +404,9 @@ __device__ __forceinline__ int element_df_operator(const VtxDF<D>* const (&V)[D 
   constexpr int D1 = D + 1;
   df2 n[D1][D], dm;
   const int s = element_normals_df<D>(V, n, dm);  // d! |tau| times 2^-ds
-  int st = (dm.h > 0.0f && dm.h < INFINITY) ? FEM_OK : FEM_ERR_DEGENERATE;
+  int st;
+  if constexpr (D == 3) st = tet_status(V, dm);
+  else st = (dm.h > 0.0f && dm.h < INFINITY) ? FEM_OK : FEM_ERR_DEGENERATE;
   if (op == kOpMass) {
     // c |tau| / ((d+1)(d+2)) = c d! |tau| / (2 * 12) in 2-D, / (6 * 20) in 3-D; homogeneous of degree d
     if (!scale_in_range(D * s)) st = worst(st, FEM_ERR_RANGE);

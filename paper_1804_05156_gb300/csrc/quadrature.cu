@@ -133,14 +133,14 @@ __global__ void __launch_bounds__(128) k_rhs_rule(int64_t NT, const int32_t* __r
   const VtxDF<D>* V[D1];
 #pragma unroll
   for (int i = 0; i < D1; ++i) {
-    const int v = __ldg(elem + t * D1 + i);
-#pragma unroll
-    for (int m = 0; m < D; ++m) X[i].x[m] = __ldg(node + (size_t)v * D + m);
+    stage_vertex<D>(X[i], node + (size_t)__ldg(elem + t * D1 + i) * D);
     V[i] = &X[i];
   }
   df2 n[D1][D], dm;
   const int s = element_normals_df<D>(reinterpret_cast<const VtxDF<D>* const(&)[D1]>(V), n, dm);  // d! |tau| 2^-ds
-  int st = (dm.h > 0.0f && dm.h < INFINITY) ? FEM_OK : FEM_ERR_DEGENERATE;
+  int st;
+  if constexpr (D == 3) st = tet_status(reinterpret_cast<const VtxDF<3>* const(&)[4]>(V), dm);
+  else st = (dm.h > 0.0f && dm.h < INFINITY) ? FEM_OK : FEM_ERR_DEGENERATE;
   if (!scale_in_range(D * s)) st = worst(st, FEM_ERR_RANGE);
   const df2 meas = df_ldexp((D == 2) ? df_scale(dm, 0.5f) : df_mul(dm, df2{0.1666666716337204f, -4.9670538793e-09f}),
                             scale_in_range(D * s) ? D * s : 0);
@@ -150,11 +150,19 @@ __global__ void __launch_bounds__(128) k_rhs_rule(int64_t NT, const int32_t* __r
   float sgn = 1.0f;
 #pragma unroll
   for (int m = 0; m < D; ++m) {
-    const float nn = rintf(lead_float(X[0].x[m]));
-    if (int_parity(nn)) sgn = -sgn;
-    const double nd = f2d_bits(nn);
+    if constexpr (D == 2) {
+      const float nn = rintf(lead_float(X[0].x[m]));
+      if (int_parity(nn)) sgn = -sgn;
+      const double nd = f2d_bits(nn);
 #pragma unroll
-    for (int i = 0; i < D1; ++i) y[i][m] = df_from_double_shift(__dsub_rn(X[i].x[m], nd), 0);
+      for (int i = 0; i < D1; ++i) y[i][m] = df_from_double_shift(__dsub_rn(X[i].x[m], nd), 0);
+    } else {
+      const float nn = rintf(X[0].x[m].a);
+      if (int_parity(nn)) sgn = -sgn;
+#pragma unroll
+      for (int i = 0; i < D1; ++i)
+        y[i][m] = df_add(two_sum(X[i].x[m].a, -nn), fast_two_sum(X[i].x[m].b, X[i].x[m].c));
+    }
   }
   const df2 fc = (f_kind == FEM_F_CONST && f_arg) ? df_from_double(__ldg(f_arg)) : df2{1.0f, 0.0f};
   df2 c[D1];

@@ -131,14 +131,15 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
   for (int v = tid; v < nv; v += BT) {
     const int R = a.vlist[v0 + v];
     VtxDF<D> x;
-#pragma unroll
-    for (int m = 0; m < D; ++m) x.x[m] = __ldg(node + (size_t)R * D + m);
+    stage_vertex<D>(x, node + (size_t)R * D);
     xs[v] = x;
-    if (sinprod2) {
-      df2 Pv[4];
-      sin_products(sincospi_half(split3(x.x[0]), tab), sincospi_half(split3(x.x[1]), tab), Pv);
+    if constexpr (D == 2) {
+      if (sinprod2) {
+        df2 Pv[4];
+        sin_products(sincospi_half(split3(x.x[0]), tab), sincospi_half(split3(x.x[1]), tab), Pv);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) reinterpret_cast<df2*>(scs)[v * 4 + c] = Pv[c];
+        for (int c = 0; c < 4; ++c) reinterpret_cast<df2*>(scs)[v * 4 + c] = Pv[c];
+      }
     }
   }
   // the block's records and element data, loaded once, coalesced (their latency overlaps the staging)

@@ -106,8 +106,7 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
   for (int v = threadIdx.x; v < nv; v += TE) {
     const int R = __ldg(a.vlist + v0 + v);
     VtxDF<D> x;
-#pragma unroll
-    for (int m = 0; m < D; ++m) x.x[m] = __ldg(node + (size_t)R * D + m);
+    stage_vertex<D>(x, node + (size_t)R * D);
     if constexpr (D == 2) {
       Vtx2* rec = reinterpret_cast<Vtx2*>(sm) + v;
       rec->v = x;
