@@ -41,18 +41,24 @@ __device__ __forceinline__ df2 two_prod(float a, float b) {
 __device__ __forceinline__ df2 df_neg(df2 a) { return {-a.h, -a.l}; }
 __device__ __forceinline__ df2 df_from(float a) { return {a, 0.0f}; }
 
+// Error bounds below are for pairs with |lo| <= u |hi| (u = 2^-24; the routines here return such pairs,
+// except df_from_double_shift: |lo| < 2u |hi|), to first order in u, with no result leaving the normal
+// float range.
+// df_add: |error| <= 3 u^2 (|a| + |b|): the leading parts' sum is exact (two-sum); the trailing parts' sum
+// (size <= u (|a| + |b|)) and its sum with the two-sum's error (size <= 2u (|a| + |b|)) round once each; the
+// final fast two-sum is exact. There is no bound relative to |a + b| itself when they cancel.
 __device__ __forceinline__ df2 df_add(df2 a, df2 b) {
   const df2 s = two_sum(a.h, b.h);
   return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
 }
 __device__ __forceinline__ df2 df_sub(df2 a, df2 b) { return df_add(a, df_neg(b)); }
-// accumulate without renormalising (the result's lo may exceed half an ulp of hi; renormalise later)
-__device__ __forceinline__ df2 df_acc(df2 a, df2 b) {
-  const df2 s = two_sum(a.h, b.h);
-  return {s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l))};
-}
-__device__ __forceinline__ df2 df_norm(df2 a) { return fast_two_sum(a.h, a.l); }
+// One step of a running sum: the operations of df_add, renormalised every step, so that the sum of m
+// terms c_j stays within 3 u^2 sum_j (|partial sum before j| + |c_j|) <= 3 m u^2 sum_j |c_j| (u = 2^-24).
+// (Carrying the trailing part unnormalised would let it grow with every step and the bound with m^2.)
+__device__ __forceinline__ df2 df_acc(df2 a, df2 b) { return df_add(a, b); }
 
+// df_mul: |error| <= 6 u^2 |a b|: the residual of a.h b.h is exact (FMA); adding a.h b.l, then a.l b.h,
+// rounds sums of size <= 2u |ab| and 3u |ab|; the dropped a.l b.l is <= u^2 |ab|.
 __device__ __forceinline__ df2 df_mul(df2 a, df2 b) {
   const float p = __fmul_rn(a.h, b.h);
   float e = __fmaf_rn(a.h, b.h, -p);
@@ -60,6 +66,7 @@ __device__ __forceinline__ df2 df_mul(df2 a, df2 b) {
   e = __fmaf_rn(a.l, b.h, e);
   return fast_two_sum(p, e);
 }
+// df_mul_f: |error| <= 2 u^2 |a b| (one rounding of a sum of size <= 2u |ab|).
 __device__ __forceinline__ df2 df_mul_f(df2 a, float b) {
   const float p = __fmul_rn(a.h, b);
   float e = __fmaf_rn(a.h, b, -p);
@@ -69,7 +76,9 @@ __device__ __forceinline__ df2 df_mul_f(df2 a, float b) {
 // scaling by a power of two (exact; any other factor needs df_mul_f)
 __device__ __forceinline__ df2 df_scale(df2 a, float pow2) { return {__fmul_rn(a.h, pow2), __fmul_rn(a.l, pow2)}; }
 
-// 1/a: a float reciprocal refined by one Newton step carried in df (error ~2^-46 relative)
+// 1/a: a float reciprocal r refined by one Newton step carried in df. Relative error <= 9 u^2: with
+// eps = a r - 1 (|eps| <= 2u), the step drops eps^2 (4 u^2) and rounds 1 - a.h r (u^2), the sum with a.l r
+// (2 u^2) and r t (2 u^2). For |a.l| up to 2u |a.h| (a pair that is not renormalised) the bound is 16 u^2.
 __device__ __forceinline__ df2 df_recip(df2 a) {
   const float r = __frcp_rn(a.h);
   float t = __fmaf_rn(-a.h, r, 1.0f);
@@ -77,7 +86,11 @@ __device__ __forceinline__ df2 df_recip(df2 a) {
   return fast_two_sum(r, __fmul_rn(r, t));
 }
 
-// Sum over m of a_m * b_m for df vectors, relative error ~2^-46 against sum_m |a_m b_m|.
+// Sum over m of a_m * b_m for df vectors. |error| <= g_D u^2 sum_m |a_m b_m| with g_2 = 19, g_3 = 36,
+// g_4 = 56: the leading products and their running sum are exact (residuals and two-sum errors); everything
+// else gathers in one float t, whose 4D - 2 roundings are each at most u times a partial sum of terms of
+// total size <= (D + 2) u sum |a_m b_m| (counted term by term, by position); the dropped a.l b.l add u^2,
+// and the final fast two-sum, inexact only when the leading sum has cancelled below |t|, at most u |t|.
 template <int D>
 __device__ __forceinline__ df2 df_dot(const df2 (&a)[D], const df2 (&b)[D]) {
   // leading products exact (product + FMA residual), their sum by two-sum; residuals, cross terms and
@@ -140,7 +153,8 @@ __device__ __forceinline__ f3 split3(double x) {
   return r;
 }
 
-// df approximation of a double (relative error <= 2^-47): the first two parts of split3, renormalised
+// df approximation of a double (relative error <= u^2 = 2^-48: the middle and last parts, 29 bits in all,
+// rounded to one float), renormalised
 __device__ __forceinline__ df2 df_from_double(double x) {
   const f3 s = split3(x);
   return fast_two_sum(s.a, __fadd_rn(s.b, s.c));
@@ -170,8 +184,9 @@ __device__ __forceinline__ int exponent_of_hiword(uint32_t m) { return (int)(m >
 
 // x * 2^-s as a float pair, from the IEEE bits with integer operations only: the leading part is the
 // top 24 significant bits (truncated, exponent shifted by s), the trailing part the remaining 29 bits
-// through one int32 -> float conversion (rounded to 24 bits), so the pair carries x 2^-s to 2^-47
-// relative. Both parts have the sign of x and |lo| < ulp(hi). Gives 0 when x 2^-s is below 2^-126 (for
+// through one int32 -> float conversion (rounded to 24 bits: 5 bits dropped, an error of at most 16 units
+// of the double's last place), so the pair carries x 2^-s to u^2 = 2^-48 relative. Both parts have the
+// sign of x and |lo| < ulp(hi) <= 2u |hi| (the leading part is truncated, not rounded). Gives 0 when x 2^-s is below 2^-126 (for
 // the element's own edges, which are scaled so that the largest component is in [1, 2), that is below
 // 2^-126 of the element's size).
 __device__ __forceinline__ df2 df_from_double_shift(double x, int s) {
@@ -211,8 +226,10 @@ __device__ __forceinline__ bool df_prod_in_range(df2 v, bool nonzero_factors) {
 __device__ __forceinline__ bool scale_in_range(int e) { return e >= -100 && e <= 100; }
 
 // xj - xi as df, from exact three-float splits: the difference of the leading parts and of the
-// middle parts are formed exactly with two-sum, so the result is accurate to ~2^-47 of |xj - xi|
-// however close xi and xj are.
+// middle parts are formed exactly with two-sum, so the result is within 4 u^2 |xj - xi| + 2^-67 max|x|
+// however close xi and xj are (three roundings of trailing sums of size <= 2u |xj - xi|, and the
+// difference of the last parts, each below 2^-45 |x|); the second term stays below u^2 |xj - xi| while
+// the coordinates are within 2^19 edge lengths of the origin.
 __device__ __forceinline__ df2 f3_diff(const f3& xj, const f3& xi) {
   const df2 A = two_sum(xj.a, -xi.a);
   const df2 B = two_sum(xj.b, -xi.b);
