@@ -194,7 +194,7 @@ def dirichlet(row_ptr, col, val, b, is_bd, gD=None):
 
 
 def solve_reduced(row_ptr, col, val, b, is_bd, gD=None):
-    """Sec. 3.3: u = g_D on the boundary, u(freeNode) = A(freeNode, freeNode) \ (b - A u_D)(freeNode), with A
+    r"""Sec. 3.3: u = g_D on the boundary, u(freeNode) = A(freeNode, freeNode) \ (b - A u_D)(freeNode), with A
     the assembled CSR matrix (before elimination) and a direct sparse solve (scipy.sparse.linalg.spsolve)."""
     import scipy.sparse as sp
     import scipy.sparse.linalg as spla

@@ -43,7 +43,7 @@ __device__ __forceinline__ int element_adjoint(const VtxDF<D>* const (&V)[D + 1]
                                                const float4* __restrict__ tab, df2 (&out)[D + 1][D], df2& gkv) {
   constexpr int D1 = D + 1;
   // scaled inward normals n_i and the positive measure |tau| (d! |tau| = signed 2-D area x 2, 3-D vol x 6),
-  // in the element's frame scaled by 2^-s
+  // 2-D in the element's frame scaled by 2^-s, 3-D at the element's own scale (s = 0)
   df2 n[D1][D];
   df2 dmeas;  // d! |tau| times 2^-ds
   int s;
@@ -57,7 +57,7 @@ __device__ __forceinline__ int element_adjoint(const VtxDF<D>* const (&V)[D + 1]
     }
   } else {
     df2 ed[3][3];
-    tet_frame(V, ed, n);
+    tet_normals(V, ed, n);
     dmeas = df_dot<3>(n[3], ed[2]);
     s = 0;  // no frame in 3-D
   }

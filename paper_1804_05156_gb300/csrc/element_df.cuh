@@ -2,14 +2,16 @@
 //
 // Same formulas as element.cuh (Sec. 3.1.3, eq. (dlambda) and the a_ij formula below it; Sec. 3.2),
 // arranged for the FP32 pipe:
-//  * staged vertices are the coordinates as doubles, and every edge vector is one FP64 subtraction of
-//    its own two endpoints: rounded once, to 2^-53 of the edge however far the element is from the
-//    origin (the edge the FP64 formula itself starts from);
-//  * the element is then scaled by 2^-s, s the exponent of its largest edge component, as the edges
-//    are converted to float pairs (df_from_double_shift, integer operations only): every product below
-//    is of order one whatever the element's size, and each result is scaled back exactly by the power
-//    of two its degree of homogeneity in the coordinates gives (2-D stiffness 0, 3-D stiffness 1,
-//    measure d);
+//  * 2-D: staged vertices are the coordinates as doubles, and every edge vector is one FP64 subtraction
+//    of its own two endpoints: rounded once, to 2^-53 of the edge however far the element is from the
+//    origin (the edge the FP64 formula itself starts from); the element is then scaled by 2^-s, s the
+//    exponent of its largest edge component, as the edges are converted to float pairs
+//    (df_from_double_shift, integer operations only): every product below is of order one whatever the
+//    element's size, and each result is scaled back exactly by the power of two its degree of
+//    homogeneity in the coordinates gives (stiffness 0, measure 2);
+//  * 3-D: staged vertices are the coordinates' exact three-float splits, every edge the exact float-float
+//    difference of its endpoints' splits (f3_diff), at the element's own scale; tet_status reports an
+//    element whose 6 |tau| leaves the range in which these products keep their precision;
 //  * 2-D: ve_0 = x3 - x2, ve_1 = x1 - x3, ve_2 = x2 - x1 (1-based vertices), 2 area = ve_1 x ve_2,
 //    a_ij = s ve_i.ve_j, s = k / (2 |2 area|) (the paper's abs() of the area);
 //  * 3-D: with e_m = x_{m+1} - x_1, n_1 = e_2 x e_3, n_2 = e_3 x e_1, n_3 = e_1 x e_2 (the paper's faces
@@ -193,7 +195,7 @@ __device__ __forceinline__ void df_cross(const df2 (&u)[3], const df2 (&v)[3], d
 // state of a scaled frame costs registers the kernels cannot spare). The products of normals (|e|^4), the
 // volume (|e|^3) and its reciprocal stay inside the float-float range for edges in [2^-24, 2^29];
 // tet_status checks that through 6 |tau|.
-__device__ __forceinline__ void tet_frame(const VtxDF<3>* const (&V)[4], df2 (&e)[3][3], df2 (&n)[4][3]) {
+__device__ __forceinline__ void tet_normals(const VtxDF<3>* const (&V)[4], df2 (&e)[3][3], df2 (&n)[4][3]) {
 #pragma unroll
   for (int q = 0; q < 3; ++q)
 #pragma unroll
@@ -277,7 +279,7 @@ __device__ __forceinline__ int element_df3(const VtxDF<3>* const (&V)[4], df2 kt
                                            int f_kind, df2 fconst, const double* __restrict__ f_arg, int t,
                                            const float4* __restrict__ tab, LocalDF<3>& L, bool want_diag = true) {
   df2 e[3][3], n[4][3];
-  tet_frame(V, e, n);
+  tet_normals(V, e, n);
   const df2 vol6 = df_dot<3>(n[3], e[2]);  // 6 x signed volume
   int st = tet_status(V, vol6);
   if (want_a) {
@@ -390,7 +392,7 @@ __device__ __forceinline__ int element_normals_df(const VtxDF<D>* const (&V)[D +
     return s;
   } else {
     df2 e[3][3];
-    tet_frame(V, e, n);
+    tet_normals(V, e, n);
     dm = df_dot<3>(n[3], e[2]);
     return 0;  // no frame in 3-D; tet_status tells whether the element is in range
   }

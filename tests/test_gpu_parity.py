@@ -250,36 +250,76 @@ def test_row_shards_on_the_gpu_give_the_global_rows_bit_for_bit(d):
         assert np.array_equal(np.concatenate([g[4] for g in got]).view(np.uint64), b.view(np.uint64))
 
 
-@pytest.mark.parametrize("d,e", [(2, -30), (2, -20), (2, 0), (2, 30), (3, -20), (3, -12), (3, 0), (3, 30)])
-def test_meshes_scaled_by_powers_of_two_keep_the_parity_bar(d, e):
+def _expect_in_range(d, node, elem):
+    """The documented range of the float-float path, predicted on the host from the FP64 oracle's
+    measures: (stiffness in range, load of f = 1 in range). 2-D: the element's power-of-two frame keeps the
+    stiffness (degree 0) in range at any scale; the load contribution |tau|/3 must lie in [2^-84, 2^120].
+    3-D: 6|tau| must lie in [2^-72, 2^87] for anything at all."""
+    meas = np.abs(oracle.measure(d, node, elem))
+    if d == 2:
+        c = meas / 3.0
+        return True, bool(c.min() >= 2.0 ** -84 and c.max() <= 2.0 ** 120)
+    v6 = 6.0 * meas
+    ok = bool(v6.min() >= 2.0 ** -72 and v6.max() <= 2.0 ** 87)
+    return ok, ok
+
+
+def _expect_range_error(call):
+    call()
+    with pytest.raises(fa.FemError) as err:
+        fa.get_error()
+    assert err.value.code == fa.FEM_ERR_RANGE
+
+
+@pytest.mark.parametrize("e", [-40, -27, -20, 0, 30, 40])
+@pytest.mark.parametrize("case", ["sq37p", "kuhn7s", "delaunay3"])
+def test_scaled_meshes_keep_the_parity_bar_or_report_the_range(case, e):
     """The mesh scaled by 2^e (coordinates exactly scaled, so the FP64 oracle's values scale exactly too):
-    stiffness (degree d - 2 in the coordinates), the load vector of f = 1 (degree d) and the adjoint stay
-    within the parity bar on every value path; the element's own power-of-two frame keeps every float-float
-    product of order one whatever the mesh's size. 2^-20 in 3-D is a mesh of 1e-7-sized tetrahedra (|tau|
-    near 2^-71) whose products of face normals, n_i . n_j ~ 2^-92, would have left the float-float range
-    without it. (A sine-product load is a different matter at these scales: at 2^-40 its values fall below
-    the float range, which test_inputs_beyond_the_float_float_range_are_reported covers, and at 2^30 the
-    FP64 rounding of the quadrature points alone moves sin(pi x) by more than the bar.)"""
-    d_, node, elem, k, _ = mesh_case("sq37p" if d == 2 else "kuhn7s")
+    where the documented range holds (_expect_in_range), the stiffness (degree d - 2 in the coordinates),
+    the load vector of f = 1 (degree d) and the adjoint stay within the parity bar on every value path;
+    where it does not, the call reports FEM_ERR_RANGE. 2-D computes in the element's own power-of-two
+    frame, so its stiffness is in range at every scale here while its load leaves the range below about
+    2^-40 (|tau|/3 < 2^-84). 3-D computes at the element's own scale: kuhn7s at 2^-20 is a mesh of
+    1e-7-sized tetrahedra (6|tau| near 2^-68) and still in range; at 2^-27 and 2^40 it is not. (A
+    sine-product load is a different matter at these scales: at 2^-40 its values fall below the float
+    range, which test_inputs_beyond_the_float_float_range_are_reported covers, and at 2^30 the FP64
+    rounding of the quadrature points alone moves sin(pi x) by more than the bar.)"""
+    d, node, elem, k, _ = mesh_case(case)
     node = np.ldexp(node, e)
     N, NT = node.shape[0], elem.shape[0]
+    a_ok, b_ok = _expect_in_range(d, node, elem)
     p = fa.Pattern(dev(elem), N)
     fa.fem_pattern_set_locality(p, dev(node))
+    nd, kd = dev(node), dev(k if k is not None else np.ones(NT))
     _, _, vo, so = oracle.assemble(d, node, elem, k)
     bo = oracle.rhs(d, node, elem, oracle.F_CONST)
     for path, te in ((fa.FEM_PATH_TILES, 128), (fa.FEM_PATH_TILES_FUSED, 256), (fa.FEM_PATH_BLOCKED, 0)):
         fa.fem_pattern_force_path(p, path, te or 256)
-        v, b = fa.assemble(p, dev(node), dev(k), fa.FEM_F_CONST, None, fa.FEM_DETERMINISTIC)
-        fa.get_error()
-        assert_close_scaled(host(v), vo, so, what="stiffness at 2^%d" % e)
-        assert_close_scaled(host(b), bo, np.abs(bo) + 1e-300, what="rhs at 2^%d" % e)
+        val = torch.empty(p.nnz, dtype=torch.float64, device="cuda")
+        b = torch.empty(N, dtype=torch.float64, device="cuda")
+        stiff = lambda: fa.fem_assemble_stiffness(p, nd, kd, val)
+        load = lambda: fa.fem_assemble_rhs(p, nd, fa.FEM_F_CONST, None, b)
+        if a_ok:
+            stiff()
+            fa.get_error()
+            assert_close_scaled(host(val), vo, so, what="stiffness at 2^%d" % e)
+        else:
+            _expect_range_error(stiff)
+        if b_ok:
+            load()
+            fa.get_error()
+            assert_close_scaled(host(b), bo, np.abs(bo) + 1e-300, what="rhs at 2^%d" % e)
+        else:
+            _expect_range_error(load)
+    if not (a_ok and b_ok):
+        return
     rp, col = host(p.row_ptr).astype(np.int64), host(p.col_idx).astype(np.int64)
     slot = oracle.slots(d, N, elem, rp, col)
     w, r = meshgen.normal(5, meshgen.TAG_W, p.nnz), meshgen.normal(5, meshgen.TAG_R, N)
     gno, gko, gnm, gkm = oracle.backward(d, node, elem, k, oracle.F_CONST, None, slot, w, r, with_scale=True)
     gn = torch.empty((N, d), dtype=torch.float64, device="cuda")
     gk = torch.empty(NT, dtype=torch.float64, device="cuda")
-    fa.fem_assemble_backward(p, dev(node), dev(k), fa.FEM_F_CONST, None, dev(w), dev(r), gn, gk)
+    fa.fem_assemble_backward(p, nd, kd, fa.FEM_F_CONST, None, dev(w), dev(r), gn, gk)
     fa.get_error()
     assert_close_scaled(host(gn), gno, gnm, tol=BWD_TOL, what="node gradient at 2^%d" % e)
     assert_close_scaled(host(gk), gko, gkm, tol=BWD_TOL, what="k gradient at 2^%d" % e)
