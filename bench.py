@@ -47,9 +47,22 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def algorithmic_bytes(d, N, NT, nnz):
-    """Minimum bytes of the value phase: elem, node (each vertex once), k, val, b."""
-    return NT * (d + 1) * 4 + N * d * 8 + NT * 8 + nnz * 8 + N * 8
+def algorithmic_bytes(d, N, NT, nnz, part="all"):
+    """Minimum bytes of the value phase: elem, node (each vertex once), k, val, b (part "stiffness": no b;
+    "load": no k and no val)."""
+    geo = NT * (d + 1) * 4 + N * d * 8
+    if part == "stiffness":
+        return geo + NT * 8 + nnz * 8
+    if part == "load":
+        return geo + N * 8
+    return geo + NT * 8 + nnz * 8 + N * 8
+
+
+def cg_iteration_bytes(d, N, NT):
+    """Minimum bytes of one matrix-free CG iteration: the operator (elem, node, k, the direction p and
+    the boundary mask read, A p written) and the vector kernels (p.q: p, q read; update: p, q, u, r read,
+    u, r written; direction: r, p read, p written), all FP64 vectors of N entries."""
+    return NT * (d + 1) * 4 + N * d * 8 + NT * 8 + N * 8 + N + N * 8 + 8 * N * (2 + 6 + 3)
 
 
 class ClockSampler:
@@ -384,8 +397,12 @@ def run_ours(args):
         node, elem = node[sh["vert_ids"]], sh["elem_local"]
         k = None if k is None else k[sh["elem_ids"]]
     N, NT = node.shape[0], elem.shape[0]
-    f_kind = fa.FEM_F_SINPROD if mesh["f"] == "sinprod" else fa.FEM_F_CONST
+    f_name = mesh["f"] if args.f == "workload" else args.f
+    f_kind = fa.FEM_F_SINPROD if f_name == "sinprod" else fa.FEM_F_CONST
     variant = fa.FEM_ATOMIC if args.variant == "atomic" else fa.FEM_DETERMINISTIC
+    # a slice of the call (stiffness or load alone, or another f) times part of the workload: a
+    # diagnostic run, without the e2e, secondary and CPU rows
+    diagnostic = args.part != "all" or f_name != mesh["f"]
     s = torch.cuda.current_stream()
 
     elem_d = torch.as_tensor(elem).cuda()
@@ -405,7 +422,12 @@ def run_ours(args):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
     def step():
-        fa.fem_assemble(p, node_d, k_d, f_kind, None, val, b, variant)
+        if args.part == "stiffness":
+            fa.fem_assemble_stiffness(p, node_d, k_d, val, variant)
+        elif args.part == "load":
+            fa.fem_assemble_rhs(p, node_d, f_kind, None, b, variant)
+        else:
+            fa.fem_assemble(p, node_d, k_d, f_kind, None, val, b, variant)
 
     for _ in range(args.warmup):
         step()
@@ -443,7 +465,7 @@ def run_ours(args):
     # roofline of the step's kernels (one or two launches per step, depending on the tuned path):
     # algorithmic bytes of the step / the summed mean durations of the kernels launched every step
     peak, peak_kind = peaks()
-    alg = algorithmic_bytes(d, N, NT, p.nnz)
+    alg = algorithmic_bytes(d, N, NT, p.nnz, args.part)
     per_step = {n: (c, t) for n, (c, t) in kt.items() if c >= args.steps}
     if not per_step:
         per_step = {"step": (args.steps, ms * args.steps)}
@@ -453,6 +475,8 @@ def run_ours(args):
     shape = fa.fem_pattern_launch_shape(p)
     path = fa.fem_pattern_value_path(p)
     prof_cfg = args.config if args.grid is None else "%s@%d" % (args.config, args.grid)  # records are per workload
+    if diagnostic:
+        prof_cfg += "/%s/%s" % (args.part, f_name)
     traffic, traffic_src = profiled(names, prof_cfg, path, shape)
     inst, inst_src = profiled(names, prof_cfg, path, shape, "inst", "warp_inst_per_launch")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -477,41 +501,47 @@ def run_ours(args):
                      "achieved": (inst / (k_ms * 1e-3)) if inst else None,
                      "frac": (inst / (k_ms * 1e-3) / issue_peak) if inst else None}
 
-    # e2e: host buffers through the C ABI (fem_assemble_host): every step copies its inputs in from
-    # page-locked host memory and its outputs (val, b) back; the call pipelines the steps (inputs of
-    # step i+1 and outputs of step i-1 in flight while step i computes)
-    node_h = torch.as_tensor(node).pin_memory()
-    k_h = torch.as_tensor(k).pin_memory() if k is not None else None
-    val_hs = [torch.empty(p.nnz, dtype=torch.float64).pin_memory() for _ in range(2)]
-    b_hs = [torch.empty(N, dtype=torch.float64).pin_memory() for _ in range(2)]
-    e2e_steps = max(3, args.steps)
-    nodes_l, ks_l = [node_h] * e2e_steps, [k_h] * e2e_steps
-    vals_l = [val_hs[i % 2] for i in range(e2e_steps)]
-    bs_l = [b_hs[i % 2] for i in range(e2e_steps)]
-    fa.fem_assemble_host(p, nodes_l[:2], ks_l[:2], f_kind, None, vals_l[:2], bs_l[:2], s)  # warm-up
-    torch.cuda.synchronize()
-    e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e_a.record(s)
-    fa.fem_assemble_host(p, nodes_l, ks_l, f_kind, None, vals_l, bs_l, s)
-    e_b.record(s)
-    torch.cuda.synchronize()
-    e2e_ms = e_a.elapsed_time(e_b) / e2e_steps
-    # the same, one step per call (no overlap between steps)
-    one = []
-    for i in range(3):
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(s)
-        fa.fem_assemble_host(p, nodes_l[:1], ks_l[:1], f_kind, None, vals_l[:1], bs_l[:1], s)
-        a1.record(s)
+    e2e = None
+    if not diagnostic:
+        # e2e: host buffers through the C ABI (fem_assemble_host): every step copies its inputs in from
+        # page-locked host memory and its outputs (val, b) back; the call pipelines the steps (inputs of
+        # step i+1 and outputs of step i-1 in flight while step i computes)
+        node_h = torch.as_tensor(node).pin_memory()
+        k_h = torch.as_tensor(k).pin_memory() if k is not None else None
+        val_hs = [torch.empty(p.nnz, dtype=torch.float64).pin_memory() for _ in range(2)]
+        b_hs = [torch.empty(N, dtype=torch.float64).pin_memory() for _ in range(2)]
+        e2e_steps = max(3, args.steps)
+        nodes_l, ks_l = [node_h] * e2e_steps, [k_h] * e2e_steps
+        vals_l = [val_hs[i % 2] for i in range(e2e_steps)]
+        bs_l = [b_hs[i % 2] for i in range(e2e_steps)]
+        fa.fem_assemble_host(p, nodes_l[:2], ks_l[:2], f_kind, None, vals_l[:2], bs_l[:2], s)  # warm-up
         torch.cuda.synchronize()
-        one.append(a0.elapsed_time(a1))
-    e2e_one_ms = sum(one) / len(one)
-    fa.get_error()
-    if dist:
-        e2e_ms = max_over_ranks(dist, e2e_ms)
-        e2e_one_ms = max_over_ranks(dist, e2e_one_ms)
-    h2d = node_h.numel() * 8 + (k_h.numel() * 8 if k_h is not None else 0)
-    d2h = (p.nnz + N) * 8
+        e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_a.record(s)
+        fa.fem_assemble_host(p, nodes_l, ks_l, f_kind, None, vals_l, bs_l, s)
+        e_b.record(s)
+        torch.cuda.synchronize()
+        e2e_ms = e_a.elapsed_time(e_b) / e2e_steps
+        # the same, one step per call (no overlap between steps)
+        one = []
+        for i in range(3):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(s)
+            fa.fem_assemble_host(p, nodes_l[:1], ks_l[:1], f_kind, None, vals_l[:1], bs_l[:1], s)
+            a1.record(s)
+            torch.cuda.synchronize()
+            one.append(a0.elapsed_time(a1))
+        e2e_one_ms = sum(one) / len(one)
+        fa.get_error()
+        if dist:
+            e2e_ms = max_over_ranks(dist, e2e_ms)
+            e2e_one_ms = max_over_ranks(dist, e2e_one_ms)
+        h2d = node_h.numel() * 8 + (k_h.numel() * 8 if k_h is not None else 0)
+        d2h = (p.nnz + N) * 8
+        e2e = {"value": NT_job / (e2e_ms * 1e-3) / 1e6, "unit": "Melem/s", "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+               "api": "fem_assemble_host (page-locked host buffers, steps pipelined in one call)",
+               "one_step_per_call_ms": e2e_one_ms}
 
     out = {"metric": METRIC, "value": value, "unit": "Melem/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -522,7 +552,7 @@ def run_ours(args):
                           else "FP64 (atomicAdd in FP64)"),
            "config": {"workload": workload_name(args.config) + ("" if args.grid is None else
                                                                     " (recipe at %d cells per side)" % args.grid),
-                      "N": N, "NT": NT, "nnz": p.nnz,
+                      "N": N, "NT": NT, "nnz": p.nnz, "part": args.part, "f": f_name,
                       "variant": args.variant, "l2": "flushed by a 512 MB write between steps (outside timing)",
                       "parallelism": ("single GPU" if ws == 1 else
                                       "row ownership, rank-local rows of one mesh" if args.shard == "rows" else
@@ -531,12 +561,15 @@ def run_ours(args):
            "launch_shape": shape,
            "value_path": path,
            "roofline": roof,
-           "e2e": {"value": NT_job / (e2e_ms * 1e-3) / 1e6, "unit": "Melem/s", "ms_per_step": e2e_ms,
-                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
-                   "api": "fem_assemble_host (page-locked host buffers, steps pipelined in one call)",
-                   "one_step_per_call_ms": e2e_one_ms},
+           "e2e": e2e,
            "gpu_launches": launches,
            "clocks": clocks}
+    if diagnostic:
+        print(json.dumps(out), flush=True)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     # secondary timings on the same mesh: atomic variant, boundary + Dirichlet elimination
     fa.fem_assemble(p, node_d, k_d, f_kind, None, val, b, fa.FEM_ATOMIC)
     ms_at = _time_steps(lambda: fa.fem_assemble(p, node_d, k_d, f_kind, None, val, b, fa.FEM_ATOMIC),
@@ -591,6 +624,27 @@ def run_ours(args):
         out["operators"]["apply_Melem_s"] = NT / (ms_ap * 1e-3) / 1e6
         out["operators"]["assembled_spmv_cusparse_ms"] = ms_sp
         del A_csr, u_d, y_d
+        # matrix-free CG on the reduced system (Sec. 3.3; whole boundary, g_D = 0): a fixed iteration count
+        # (rtol 0), so the rate does not depend on convergence; the call synchronises every 8 iterations
+        fa.fem_boundary_nodes(p, None, isbd)
+        fa.fem_assemble(p, node_d, k_d, f_kind, None, val, b, variant)
+        u_cg = torch.empty(N, dtype=torch.float64, device="cuda")
+        fa.fem_cg_solve(p, node_d, k_d, isbd, b, None, u_cg, max_iter=8, rtol=0.0)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, its, rel = fa.fem_cg_solve(p, node_d, k_d, isbd, b, None, u_cg, max_iter=64, rtol=0.0)
+        torch.cuda.synchronize()
+        cg_ms = 1e3 * (time.perf_counter() - t0)
+        fa.get_error()
+        it_ms = cg_ms / max(its, 1)
+        it_bytes = cg_iteration_bytes(d, N, NT)
+        out["cg_iterations"] = {"iterations": its, "ms": cg_ms, "ms_per_iteration": it_ms,
+                                "iterations_per_s": 1e3 / it_ms, "relres_after": rel,
+                                "algorithmic_bytes_per_iteration": it_bytes,
+                                "hbm_frac": it_bytes / (it_ms * 1e-3) / 1e9 / peak, "peak_GBs": peak,
+                                "timing": "wall clock around one call (lift and start included, host "
+                                          "convergence tests every 8 iterations)"}
+        del u_cg
         del K_d
     if not args.no_extras and ws == 1:
         out["extras"] = extras(fa, args, flush, value)
@@ -618,6 +672,10 @@ def main():
     ap.add_argument("--grid", type=int, default=None,
                     help="cells per side instead of the workload's own (the same recipe at another size; for profiling "
                          "captures on a smaller case)")
+    ap.add_argument("--part", choices=["all", "stiffness", "load"], default="all",
+                    help="time the whole call (default), or the stiffness or the load vector alone (diagnostic)")
+    ap.add_argument("--f", choices=["workload", "const", "sinprod"], default="workload",
+                    help="the workload's load function (default) or another one (diagnostic)")
     ap.add_argument("--shard", choices=["copies", "rows"], default="copies",
                     help="N>1: every rank assembles its own copy (weak scaling) or its rows of one mesh (strong)")
     args = ap.parse_args()

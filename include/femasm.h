@@ -38,11 +38,13 @@ extern "C" {
 #define FEM_ERR_TIMEOUT -6    /* a bounded device-side wait gave up */
 #define FEM_ERR_STATE -7      /* handle used in a way its construction does not allow */
 #define FEM_ERR_RANGE -8      /* a value outside the range the float-float kernels keep 1e-12 accuracy in:
-                                 a coefficient or tensor entry outside [2^-80, 2^96], an element so small or
-                                 large that a result's scale 2^(p s) (s the exponent of its largest edge
-                                 component, p the result's degree of homogeneity) leaves [2^-100, 2^100], or
-                                 an element contribution that is nonzero but below 2^-84 or above 2^120 in
-                                 magnitude */
+                                 an input value (coefficient or tensor entry, load value f, loss weight w or
+                                 r) nonzero and outside [2^-80, 2^96]; a 2-D element whose result scale
+                                 2^(p s) (s the exponent of its largest edge component, p the result's
+                                 degree of homogeneity) leaves [2^-100, 2^100]; a tetrahedron with 6|tau|
+                                 outside [2^-72, 2^87] (edges of about 2^-24 to 2^29); or an element
+                                 contribution whose terms are nonzero but below 2^-84 or above 2^120 in
+                                 magnitude (the check is on the terms, not on their sum, which may cancel) */
 
 /* Reduction variants of the value kernels (Sec. 2.2: `sparse` sums duplicate (i, j) entries). */
 #define FEM_DETERMINISTIC 0 /* fixed summation order per CSR slot: bitwise reproducible */

@@ -30,10 +30,11 @@ namespace {
 // coordinates V, the coefficient kt, the symmetrised loss weights Ws = W + W^T (with_w) and the
 // load-vector weights rv of the element's vertices (with_r). Returns FEM_OK, FEM_ERR_DEGENERATE or
 // FEM_ERR_RANGE (element_df.cuh).
-// The geometry is that of the value kernels: FP64 edges, the element scaled by 2^-s, so that g_i, |tau|
-// and every product of them stay of order one; each term is scaled back by its degree of homogeneity
-// in the coordinates: dL/dk and the stiffness part of dL/dx by 2^(d-2)s and 2^(d-3)s, the load part's
-// |tau| g_m term by 2^(d-1)s and its |tau| grad f term by 2^ds.
+// The geometry is that of the value kernels. 2-D: FP64 edges, the element scaled by 2^-s, so that g_i,
+// |tau| and every product of them stay of order one; each term is scaled back by its degree of
+// homogeneity in the coordinates: dL/dk and the stiffness part of dL/dx by 2^(d-2)s and 2^(d-3)s, the
+// load part's |tau| g_m term by 2^(d-1)s and its |tau| grad f term by 2^ds. 3-D: exact split edges at
+// the element's own scale (s = 0), within the 6 |tau| range tet_status checks.
 // Stiffness part in the form that needs the fewest products: h_j = sum_i Ws_ij g_i, then
 // S = (1/2) sum_j h_j . g_j and sum_i Q_im g_i = sum_j (g_j . g_m) h_j.
 template <int D>
@@ -66,6 +67,9 @@ __device__ __forceinline__ int element_adjoint(const VtxDF<D>* const (&V)[D + 1]
   else st = (dmeas.h > 0.0f && dmeas.h < INFINITY) ? FEM_OK : FEM_ERR_DEGENERATE;
   const int eA = (D - 3) * s, eK = (D - 2) * s, e1 = (D - 1) * s, e2 = D * s;
   if (!(scale_in_range(eA) && scale_in_range(e2))) st = worst(st, FEM_ERR_RANGE);
+  // the exponent of the element's size: 3-D, from 6 |tau| (about |e|^3), for the range checks of terms of
+  // other degrees; 2-D works in its frame, whose shifts s.. carry the size
+  const int ge = (D == 3) ? (fexp(dmeas.h) + 300) / 3 - 100 : 0;
   const int sA = scale_in_range(eA) ? eA : 0, sK = scale_in_range(eK) ? eK : 0;
   const int s1 = scale_in_range(e1) ? e1 : 0, s2 = scale_in_range(e2) ? e2 : 0;
   const df2 inv = df_recip(dmeas);
@@ -81,6 +85,16 @@ __device__ __forceinline__ int element_adjoint(const VtxDF<D>* const (&V)[D + 1]
     for (int c = 0; c < D; ++c) out[i][c] = df2{0.0f, 0.0f};
   gkv = df2{0.0f, 0.0f};
   if (with_w) {
+    // range, on the magnitudes of the terms (their sums may cancel, dfloat.cuh), by exponents: |tau| W g g
+    // for dL/dk (degree d - 2 in the coordinates) and k |tau| W g g g for dL/dx (degree d - 3)
+    float wm = 0.0f;
+#pragma unroll
+    for (int i = 0; i < D1; ++i)
+#pragma unroll
+      for (int j = 0; j < D1; ++j) wm = fmaxf(wm, fabsf(Ws[i][j].h));
+    if (wm != 0.0f && (!exp_in_range(fexp(wm) + sK + (D - 2) * ge) ||
+                       (kt.h != 0.0f && !exp_in_range(fexp(kt.h) + fexp(wm) + sA + (D - 3) * ge))))
+      st = worst(st, FEM_ERR_RANGE);
     // h_j = sum_i Ws_ij g_i, each component one fused float-float dot product
     df2 h[D1][D];
 #pragma unroll
@@ -208,12 +222,25 @@ __device__ __forceinline__ int element_adjoint(const VtxDF<D>* const (&V)[D + 1]
       }
     } else if (f_kind == FEM_F_QPVALUES) {
 #pragma unroll
-      for (int q = 0; q < D1; ++q) fq[q] = df_from_double_fast(__ldg(f_arg + (size_t)t * D1 + q));
+      for (int q = 0; q < D1; ++q) fq[q] = coef_df(__ldg(f_arg + (size_t)t * D1 + q), st);
     } else {
-      const df2 c0 = f_arg ? df_from_double_fast(__ldg(f_arg)) : df2{1.0f, 0.0f};
+      const df2 c0 = f_arg ? coef_df(__ldg(f_arg), st) : df2{1.0f, 0.0f};
 #pragma unroll
       for (int q = 0; q < D1; ++q) fq[q] = c0;
     }
+    // range, on the magnitudes of the terms, by exponents: |tau| g r f (degree d - 1) and, for the sine
+    // product, |tau| r grad f (degree d)
+    float rm = 0.0f, fm = 0.0f, dm = 0.0f;
+#pragma unroll
+    for (int q = 0; q < D1; ++q) {
+      rm = fmaxf(rm, fabsf(rv[q].h));
+      fm = fmaxf(fm, fabsf(fq[q].h));
+#pragma unroll
+      for (int c = 0; c < D; ++c) dm = fmaxf(dm, fabsf(gf[q][c].h));
+    }
+    if (rm != 0.0f && ((fm != 0.0f && !exp_in_range(fexp(rm) + fexp(fm) + s1 + (D - 1) * ge)) ||
+                       (dm != 0.0f && !exp_in_range(fexp(rm) + fexp(dm) + s2 + D * ge))))
+      st = worst(st, FEM_ERR_RANGE);
     // rl_q = sum_i r_i lambda_i(q) = lo sum_i r_i + ld r_q;  Rb = sum_q w_q f_q rl_q
     df2 rs = rv[0];
 #pragma unroll
@@ -248,19 +275,20 @@ __device__ __forceinline__ int element_adjoint(const VtxDF<D>* const (&V)[D + 1]
         out[m][c] = df_add(out[m][c], v);
       }
   }
-  if (!df_in_range(gkv)) st = worst(st, FEM_ERR_RANGE);
+  // and no result overflows
+  bool fin = fabsf(gkv.h) <= 0x1p120f;
 #pragma unroll
   for (int m = 0; m < D1; ++m)
 #pragma unroll
-    for (int c = 0; c < D; ++c)
-      if (!df_in_range(out[m][c])) st = worst(st, FEM_ERR_RANGE);
+    for (int c = 0; c < D; ++c) fin = fin && fabsf(out[m][c].h) <= 0x1p120f;
+  if (!fin) st = worst(st, FEM_ERR_RANGE);
   return st;
 }
 
 // Ws = W + W^T of element t from the loss weights on its slots (pairs summed in FP64, then split)
 template <int D>
 __device__ __forceinline__ void sym_weights(const int32_t* __restrict__ slot, int64_t NT, int t,
-                                            const double* __restrict__ w, df2 (&Ws)[D + 1][D + 1]) {
+                                            const double* __restrict__ w, df2 (&Ws)[D + 1][D + 1], int& st) {
   constexpr int D1 = D + 1;
 #pragma unroll
   for (int i = 0; i < D1; ++i)
@@ -268,7 +296,9 @@ __device__ __forceinline__ void sym_weights(const int32_t* __restrict__ slot, in
     for (int j = i; j < D1; ++j) {
       const double wij = __ldg(w + __ldg(slot + (size_t)(i * D1 + j) * NT + t));
       const double wji = (i == j) ? wij : __ldg(w + __ldg(slot + (size_t)(j * D1 + i) * NT + t));
-      Ws[i][j] = df_from_double_fast(__dadd_rn(wij, wji));
+      const double ws = __dadd_rn(wij, wji);
+      if (!input_in_range(ws)) st = worst(st, FEM_ERR_RANGE);
+      Ws[i][j] = df_from_double_fast(ws);
       Ws[j][i] = Ws[i][j];
     }
 }
@@ -292,12 +322,16 @@ __global__ void __launch_bounds__(128, 4) k_backward_df(const int32_t* __restric
 #pragma unroll
   for (int i = 0; i < D1; ++i) stage_vertex<D>(X[i], node + (size_t)e[i] * D);
   df2 Ws[D1][D1], rv[D1];
-  if (w) sym_weights<D>(slot, NT, t, w, Ws);
+  int st = FEM_OK;
+  if (w) sym_weights<D>(slot, NT, t, w, Ws, st);
   if (r) {
 #pragma unroll
-    for (int i = 0; i < D1; ++i) rv[i] = df_from_double_fast(__ldg(r + e[i]));
+    for (int i = 0; i < D1; ++i) {
+      const double ri = __ldg(r + e[i]);
+      if (!input_in_range(ri)) st = worst(st, FEM_ERR_RANGE);
+      rv[i] = df_from_double_fast(ri);
+    }
   }
-  int st = FEM_OK;
   const df2 kt = k ? coef_df(__ldg(k + t), st) : df2{1.0f, 0.0f};
   const VtxDF<D>* V[D1];
 #pragma unroll
@@ -347,12 +381,16 @@ __global__ void __launch_bounds__(TE, 512 / TE) k_backward_tiles(
   __syncthreads();
   if (!act) return;
   df2 Ws[D1][D1], rv[D1];
-  if (w) sym_weights<D>(slot, NT, t, w, Ws);
+  int st = FEM_OK;
+  if (w) sym_weights<D>(slot, NT, t, w, Ws, st);
   if (r) {
 #pragma unroll
-    for (int i = 0; i < D1; ++i) rv[i] = df_from_double_fast(__ldg(r + __ldg(vlist + v0 + lv[i])));
+    for (int i = 0; i < D1; ++i) {
+      const double ri = __ldg(r + __ldg(vlist + v0 + lv[i]));
+      if (!input_in_range(ri)) st = worst(st, FEM_ERR_RANGE);
+      rv[i] = df_from_double_fast(ri);
+    }
   }
-  int st = FEM_OK;
   const df2 kt = k ? coef_df(__ldg(k + t), st) : df2{1.0f, 0.0f};
   const VtxDF<D>* V[D1];
 #pragma unroll

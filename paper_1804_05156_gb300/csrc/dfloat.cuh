@@ -212,18 +212,32 @@ __device__ __forceinline__ df2 df_ldexp(df2 v, int e) {
 // The range the float-float results keep their precision in. A result's trailing part may be far below
 // its leading part; once it leaves the normal float range (2^-126) it is lost, an absolute error of up to
 // 2^-126, which is below 2^-42 of a result of magnitude 2^-84 or more. So a result is in range when its
-// leading part is 0 or of magnitude in [2^-84, 2^120] (sums of a row's contributions then stay finite);
-// a product of nonzero factors must not be 0 (it flushed). Scale exponents (the power of two an element's
-// normalised result is multiplied by) are kept within [-100, 100].
-__device__ __forceinline__ bool df_in_range(df2 v) {
-  const float a = fabsf(v.h);
-  return a <= 0x1p120f && (a == 0.0f || a >= 0x1p-84f);
-}
+// terms are of magnitude in [2^-84, 2^120] (sums of a row's contributions then stay finite); a product
+// of nonzero factors must not be 0 (it flushed). The check is made on the magnitude of a result's terms,
+// never on a sum of signed terms: such a sum may cancel far below its terms (a normal of an axis-aligned
+// face whose exact component is 0 comes out as a residue of its terms' roundings), which loses nothing
+// against the terms the error is measured by. Scale exponents (the power of two an element's normalised
+// result is multiplied by) are kept within [-100, 100].
 __device__ __forceinline__ bool df_prod_in_range(df2 v, bool nonzero_factors) {
   const float a = fabsf(v.h);
   return a <= 0x1p120f && (a >= 0x1p-84f || (a == 0.0f && !nonzero_factors));
 }
+// A term magnitude m (a float product of the magnitudes of a result's factors, formed in the element's
+// frame) that the result is then scaled by 2^e: in range when m 2^e is within [2^-84, 2^120] and m itself
+// is normal (a subnormal or zero m from nonzero factors has flushed already); m = 0 from a zero factor
+// is in range.
+__device__ __forceinline__ bool mag_in_range(float m, int e, bool nonzero_factors) {
+  const float a = fabsf(m);
+  if (a == 0.0f) return !nonzero_factors;
+  if (!(a <= 0x1p127f) || a < 0x1p-126f) return false;
+  const int x = (int)((__float_as_uint(a) >> 23) & 0xffu) - 127 + e;
+  return x >= -84 && x < 120;
+}
 __device__ __forceinline__ bool scale_in_range(int e) { return e >= -100 && e <= 100; }
+// Binary exponent of |a| for a normal float (0 and subnormals give -127), and the range test of a term
+// whose factors' exponents sum to x (the same [2^-84, 2^120] range, up to a factor 2 per factor).
+__device__ __forceinline__ int fexp(float a) { return (int)((__float_as_uint(a) >> 23) & 0xffu) - 127; }
+__device__ __forceinline__ bool exp_in_range(int x) { return x >= -84 && x < 120; }
 
 // xj - xi as df, from exact three-float splits: the difference of the leading parts and of the
 // middle parts are formed exactly with two-sum, so the result is within 4 u^2 |xj - xi| + 2^-67 max|x|

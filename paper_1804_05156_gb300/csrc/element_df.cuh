@@ -64,11 +64,17 @@ struct LocalDF {
 
 __device__ __forceinline__ int worst(int st, int code) { return st != FEM_OK ? st : code; }
 
-// A per-element coefficient (k, c) as a float pair: the exact split for |v| in [2^-80, 2^96] (or 0);
-// anything else (outside the float-float range, or not finite) sets FEM_ERR_RANGE.
-__device__ __forceinline__ df2 coef_df(double v, int& st) {
+// Whether an input value (a coefficient k or c, a load value f, a loss weight) is 0 or of magnitude in
+// [2^-80, 2^96]: inside the float-float range with room for the products it enters. Anything else
+// (outside that range, or not finite) is reported as FEM_ERR_RANGE by the caller.
+__device__ __forceinline__ bool input_in_range(double v) {
   const int E = (int)((abs_hiword(v) >> 20) & 0x7ffu);
-  if ((abs_hiword(v) | (uint32_t)__double2loint(v)) != 0u && (E < 1023 - 80 || E > 1023 + 96)) st = worst(st, FEM_ERR_RANGE);
+  return (abs_hiword(v) | (uint32_t)__double2loint(v)) == 0u || (E >= 1023 - 80 && E <= 1023 + 96);
+}
+// An input value as a float pair (the exact split for |v| in [2^-80, 2^96]); out of range sets
+// FEM_ERR_RANGE.
+__device__ __forceinline__ df2 coef_df(double v, int& st) {
+  if (!input_in_range(v)) st = worst(st, FEM_ERR_RANGE);
   return df_from_double(v);
 }
 
@@ -258,7 +264,7 @@ __device__ __forceinline__ int element_df2(const VtxDF<2>* const (&V)[3], const 
       for (int q = 0; q < 3; ++q) f[q] = sinprod_mid(P[(q + 1) % 3], P[(q + 2) % 3]);
     } else if (f_kind == FEM_F_QPVALUES) {
 #pragma unroll
-      for (int q = 0; q < 3; ++q) f[q] = df_from_double(__ldg(f_arg + (size_t)t * 3 + q));
+      for (int q = 0; q < 3; ++q) f[q] = coef_df(__ldg(f_arg + (size_t)t * 3 + q), st);
     } else {
 #pragma unroll
       for (int q = 0; q < 3; ++q) f[q] = fconst;
@@ -268,7 +274,9 @@ __device__ __forceinline__ int element_df2(const VtxDF<2>* const (&V)[3], const 
     for (int i = 0; i < 3; ++i) {
       const df2 fs = df_add(f[(i + 1) % 3], f[(i + 2) % 3]);
       L.bt[i] = df_mul(w, fs);
-      if (!df_prod_in_range(L.bt[i], w.h != 0.0f && fs.h != 0.0f)) st = worst(st, FEM_ERR_RANGE);
+      // range on the terms' magnitude |tau| max |f| (f_j + f_k itself may cancel, dfloat.cuh)
+      const float fm = fmaxf(fabsf(f[(i + 1) % 3].h), fabsf(f[(i + 2) % 3].h));
+      if (!mag_in_range(__fmul_rn(fabsf(w.h), fm), 0, w.h != 0.0f && fm != 0.0f)) st = worst(st, FEM_ERR_RANGE);
     }
   }
   return st;
@@ -325,7 +333,7 @@ __device__ __forceinline__ int element_df3(const VtxDF<3>* const (&V)[4], df2 kt
       }
     } else if (f_kind == FEM_F_QPVALUES) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) f[q] = df_from_double(__ldg(f_arg + (size_t)t * 4 + q));
+      for (int q = 0; q < 4; ++q) f[q] = coef_df(__ldg(f_arg + (size_t)t * 4 + q), st);
     } else {
 #pragma unroll
       for (int q = 0; q < 4; ++q) f[q] = fconst;
@@ -334,11 +342,11 @@ __device__ __forceinline__ int element_df3(const VtxDF<3>* const (&V)[4], df2 kt
     const df2 fs = df_add(df_add(f[0], f[1]), df_add(f[2], f[3]));
     const df2 w = df_scale(vol, 0.25f);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const df2 fi = df_add(df_mul(be, fs), df_mul(df_sub(al, be), f[i]));
-      L.bt[i] = df_mul(w, fi);
-      if (!df_prod_in_range(L.bt[i], w.h != 0.0f && fi.h != 0.0f)) st = worst(st, FEM_ERR_RANGE);
-    }
+    for (int i = 0; i < 4; ++i) L.bt[i] = df_mul(w, df_add(df_mul(be, fs), df_mul(df_sub(al, be), f[i])));
+    // range on the terms' magnitude |tau| max |f| (every point enters every entry with a positive weight;
+    // the sums themselves may cancel, dfloat.cuh)
+    const float fm = fmaxf(fmaxf(fabsf(f[0].h), fabsf(f[1].h)), fmaxf(fabsf(f[2].h), fabsf(f[3].h)));
+    if (!mag_in_range(__fmul_rn(fabsf(w.h), fm), 0, w.h != 0.0f && fm != 0.0f)) st = worst(st, FEM_ERR_RANGE);
   }
   return st;
 }
@@ -431,11 +439,19 @@ __device__ __forceinline__ int element_df_operator(const VtxDF<D>* const (&V)[D 
 #pragma unroll
     for (int i = 0; i < D1; ++i)
 #pragma unroll
-      for (int j = i + 1; j < D1; ++j) {
-        const df2 q = df_quad<D>(n[i], K, n[j]);
-        L.a[pidx<D>(i, j)] = df_mul(sc, q);
-        if (!df_prod_in_range(L.a[pidx<D>(i, j)], q.h != 0.0f)) st = worst(st, FEM_ERR_RANGE);
-      }
+      for (int j = i + 1; j < D1; ++j) L.a[pidx<D>(i, j)] = df_mul(sc, df_quad<D>(n[i], K, n[j]));
+    // range on the terms' magnitude max|n| max|K| max|n| / (d!^2 |tau|) (n_i^T K n_j may cancel)
+    float nm = 0.0f, km = 0.0f;
+#pragma unroll
+    for (int i = 0; i < D1; ++i)
+#pragma unroll
+      for (int c2 = 0; c2 < D; ++c2) nm = fmaxf(nm, fabsf(n[i][c2].h));
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b2 = 0; b2 < D; ++b2) km = fmaxf(km, fabsf(K[a][b2].h));
+    if (!mag_in_range(__fmul_rn(__fmul_rn(__fmul_rn(fabsf(sc.h), nm), nm), km), 0, km != 0.0f))
+      st = worst(st, FEM_ERR_RANGE);
   }
   return st;
 }

@@ -164,10 +164,11 @@ __global__ void __launch_bounds__(128) k_rhs_rule(int64_t NT, const int32_t* __r
         y[i][m] = df_add(two_sum(X[i].x[m].a, -nn), fast_two_sum(X[i].x[m].b, X[i].x[m].c));
     }
   }
-  const df2 fc = (f_kind == FEM_F_CONST && f_arg) ? df_from_double(__ldg(f_arg)) : df2{1.0f, 0.0f};
+  const df2 fc = (f_kind == FEM_F_CONST && f_arg) ? coef_df(__ldg(f_arg), st) : df2{1.0f, 0.0f};
   df2 c[D1];
 #pragma unroll
   for (int i = 0; i < D1; ++i) c[i] = df2{0.0f, 0.0f};
+  float wfm = 0.0f;  // the largest |w_q f_q|
   for (int q = 0; q < nq; ++q) {
     const df2* lq = lam + q * D1;
     df2 f;
@@ -181,18 +182,20 @@ __global__ void __launch_bounds__(128) k_rhs_rule(int64_t NT, const int32_t* __r
         f = df_mul(f, df_sinpi(xm, tab));
       }
     } else if (f_kind == FEM_F_QPVALUES) {
-      f = df_from_double(__ldg(f_arg + t * nq + q));
+      f = coef_df(__ldg(f_arg + t * nq + q), st);
     } else {
       f = fc;
     }
     const df2 wf = df_mul(wq[q], f);
+    wfm = fmaxf(wfm, fabsf(wf.h));
 #pragma unroll
     for (int i = 0; i < D1; ++i) c[i] = df_add(c[i], df_mul(wf, lq[i]));
   }
+  // range on the terms' magnitude |tau| max_q |w_q f_q| (the sums over the points may cancel)
+  if (!mag_in_range(__fmul_rn(fabsf(meas.h), wfm), 0, meas.h != 0.0f && wfm != 0.0f)) st = worst(st, FEM_ERR_RANGE);
 #pragma unroll
   for (int i = 0; i < D1; ++i) {
     const df2 v = df_mul(meas, c[i]);
-    if (!df_prod_in_range(v, c[i].h != 0.0f)) st = worst(st, FEM_ERR_RANGE);
     contrib[t * D1 + i] = make_float2(v.h, v.l);
   }
   if (st != FEM_OK) report(err, st);

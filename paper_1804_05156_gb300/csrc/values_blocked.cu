@@ -203,7 +203,8 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
   __syncthreads();
 
   const bool want_a = val != nullptr, want_b = bvec != nullptr;
-  const df2 fconst = (f_kind == FEM_F_CONST && f_arg) ? df_from_double(__ldg(f_arg)) : df2{1.0f, 0.0f};
+  int fst = FEM_OK;  // the constant load's range status, given to every element
+  const df2 fconst = (f_kind == FEM_F_CONST && f_arg) ? coef_df(__ldg(f_arg), fst) : df2{1.0f, 0.0f};
   for (int sb = 0; sb < ne; sb += a.SB) {
     const int nb = (ne - sb < a.SB) ? ne - sb : a.SB;
     for (int e = tid; e < nb; e += BT) {
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(BT, MINB) k_blocked_df(BlkArgs a, const double
       int lv[D1];
 #pragma unroll
       for (int i = 0; i < D1; ++i) lv[i] = slv[el * D1 + i];
-      int st = FEM_OK;
+      int st = fst;
       const df2 kt = want_k ? coef_df(sk[el], st) : df2{1.0f, 0.0f};
       LocalDF<D> L;
       if constexpr (D == 2) {

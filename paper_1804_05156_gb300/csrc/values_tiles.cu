@@ -122,7 +122,7 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
   if (!act) return;
   int st = FEM_OK;
   const df2 kt = (k && want_a) ? coef_df(kd, st) : df2{1.0f, 0.0f};
-  const df2 fconst = (f_kind == FEM_F_CONST && f_arg) ? df_from_double(__ldg(f_arg)) : df2{1.0f, 0.0f};
+  const df2 fconst = (f_kind == FEM_F_CONST && f_arg) ? coef_df(__ldg(f_arg), st) : df2{1.0f, 0.0f};
   LocalDF<D> L;
 #pragma unroll
   for (int c = 0; c < D1 * (D1 + 1) / 2; ++c) L.a[c] = df2{0.0f, 0.0f};
