@@ -179,9 +179,10 @@ __device__ __forceinline__ void elements_of_tile(const TileArgs& a, int tile, un
       if constexpr (FUSED) {  // read back through L2 in the same launch: one 256-bit access per packet
         store_packet32(a.pk + 2 * (size_t)qi[i], make_float4(o[0].h, o[0].l, o[1].h, o[1].l),
                        make_float4(L.bt[i].h, L.bt[i].l, 0.0f, 0.0f));
-      } else {
-        a.pk[qi[i]] = make_float4(o[0].h, o[0].l, o[1].h, o[1].l);
-        reinterpret_cast<float2*>(a.pk + a.NT * 3)[qi[i]] = make_float2(L.bt[i].h, L.bt[i].l);
+      } else {  // a stiffness-only or load-only call writes (and its gather reads) only its own array
+        if (want_a) a.pk[qi[i]] = make_float4(o[0].h, o[0].l, o[1].h, o[1].l);
+        if (want_b || a.op == kOpMass)  // the mass matrix's diagonal travels in the load slot
+          reinterpret_cast<float2*>(a.pk + a.NT * 3)[qi[i]] = make_float2(L.bt[i].h, L.bt[i].l);
       }
     } else {
       store_packet32(a.pk + 2 * (size_t)qi[i], make_float4(o[0].h, o[0].l, o[1].h, o[1].l),
@@ -232,14 +233,17 @@ __device__ __forceinline__ float2 load_pair(const float2* p) {
 }
 // packet q as (p0, p1): 2-D (a_ij, a_ik) and b_i from their two arrays, 3-D four pairs (32 bytes)
 template <int D, bool FRESH>
-__device__ __forceinline__ void load_packet(const float4* pk, const float2* pkb, int64_t q, float4& p0, float4& p1) {
+__device__ __forceinline__ void load_packet(const float4* pk, const float2* pkb, int64_t q, float4& p0, float4& p1,
+                                            bool want_a, bool want_b) {
   if constexpr (D == 2 && FRESH) {
     // fused form: 32-byte packets (a_ij, a_ik, b_i, unused) in one 256-bit load
     load_packet32<FRESH>(pk + 2 * q, p0, p1);
   } else if constexpr (D == 2) {
-    // two-launch form: (a_ij, a_ik) from the pair array, b_i from the load array: two aligned loads
-    p0 = load_packet_half<FRESH>(pk + q);
-    const float2 z = load_pair<FRESH>(pkb + q);
+    // two-launch form: (a_ij, a_ik) from the pair array, b_i from the load array: two aligned loads. A
+    // stiffness-only or load-only call writes only its own array; the other load then reads entry 0 over
+    // and over (an L1 hit; add_packet ignores the value)
+    p0 = load_packet_half<FRESH>(pk + (want_a ? q : 0));
+    const float2 z = load_pair<FRESH>(pkb + (want_b ? q : 0));
     p1 = make_float4(z.x, z.y, 0.0f, 0.0f);
   } else {
     load_packet32<FRESH>(pk + 2 * q, p0, p1);
@@ -274,7 +278,7 @@ __device__ __forceinline__ void rows_of_warp(const RowArgs& g, int64_t R0, df2* 
       uint32_t w[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        load_packet<D, FRESH>(g.pk, g.pkb, q + u, x0[u], x1[u]);
+        load_packet<D, FRESH>(g.pk, g.pkb, q + u, x0[u], x1[u], want_a, want_b || g.diag_in_packet);
         w[u] = (uint32_t)__ldg(pw + q + u);
       }
 #pragma unroll
@@ -282,7 +286,7 @@ __device__ __forceinline__ void rows_of_warp(const RowArgs& g, int64_t R0, df2* 
     }
     for (; q < q1; ++q) {
       float4 x0, x1;
-      load_packet<D, FRESH>(g.pk, g.pkb, q, x0, x1);
+      load_packet<D, FRESH>(g.pk, g.pkb, q, x0, x1, want_a, want_b || g.diag_in_packet);
       add_packet<D>(x0, x1, (uint32_t)__ldg(pw + q), o, acc, dacc, bacc, want_a, want_b, g.diag_in_packet);
     }
     if (want_a && rl > 0) acc[o + __ldg(g.rdp + R)] = dacc;
