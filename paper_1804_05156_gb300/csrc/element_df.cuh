@@ -163,6 +163,11 @@ __device__ __forceinline__ float lead_float(double x) {
                               : 0.0f;
 }
 
+// sin(pi x) at one of the 3-D load's twelve points (four points, three coordinates), as one out-of-line
+// copy: fewer registers held across the element routine and a shorter kernel (measured: 1 % faster on
+// the 64^3 sine-product forward, 0.4 % on the 128^3 element phase; the same bits)
+static __device__ __noinline__ df2 sinpi_point(df2 x, const float4* __restrict__ tab) { return df_sinpi(x, tab); }
+
 // ---- element frames: FP64 edges, scaled by 2^-s --------------------------------------------------
 
 // Triangle: side vectors ve_i (opposite vertex i) as float pairs scaled by 2^-s, and twice the signed area
@@ -327,7 +332,7 @@ __device__ __forceinline__ int element_df3(const VtxDF<3>* const (&V)[4], df2 kt
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const df2 xq = df_add(df_mul(be, sy), df_mul(df_sub(al, be), y[q]));
-          const df2 sv = df_sinpi(xq, tab);
+          const df2 sv = sinpi_point(xq, tab);
           f[q] = df_mul(f[q], df2{sv.h * sgn, sv.l * sgn});
         }
       }
