@@ -325,6 +325,45 @@ def test_scaled_meshes_keep_the_parity_bar_or_report_the_range(case, e):
     assert_close_scaled(host(gk), gko, gkm, tol=BWD_TOL, what="k gradient at 2^%d" % e)
 
 
+@pytest.mark.parametrize("shear", [0.0, 40.0, 200.0])
+def test_2d_stiffness_within_its_error_bound_on_sheared_meshes(shear):
+    """The per-entry error bound of the 2-D stiffness (the design's section 2: (65.1 + 0.1 kappa_A) u^2 per
+    contribution against its scale term, 3 u^2 per running-sum step, u = 2^-24), on meshes sheared so
+    that the conditioning of the element area kappa_A = (|e1x e2y| + |e1y e2x|) / |2 area| grows to
+    about 2 shear: every CSR value of the GPU path within that bound, with kappa_A the mesh's largest and
+    m the entry's number of contributions, plus the FP64 oracle's own rounding of the area
+    ((2 kappa_A + 1) 2^-53). The bound's kappa_A term comes from the one FP64 cross product; the
+    largest error seen is printed in u^2."""
+    m = meshgen.square_mesh(48, 0.2, 77, permute=True)
+    node, elem = m["node"].copy(), m["elem"]
+    node[:, 0] += shear * node[:, 1]
+    node[:, 1] *= 1e-3
+    NT = elem.shape[0]
+    k = meshgen.lognormal(77, meshgen.TAG_COEF, NT)
+    X = node[elem]
+    e1, e2 = X[:, 0] - X[:, 2], X[:, 1] - X[:, 0]
+    kap = (np.abs(e1[:, 0] * e2[:, 1]) + np.abs(e1[:, 1] * e2[:, 0])) / np.abs(e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0])
+    kmax = float(kap.max())
+    p = fa.Pattern(dev(elem), node.shape[0])
+    fa.fem_pattern_set_locality(p, dev(node))
+    val = torch.empty(p.nnz, dtype=torch.float64, device="cuda")
+    fa.fem_assemble_stiffness(p, dev(node), dev(k), val)
+    fa.get_error()
+    rp, col, vo, so = oracle.assemble(2, node, elem, k)
+    # contributions per entry: elements on the edge (off-diagonal) or at the vertex (diagonal)
+    N = node.shape[0]
+    deg = np.bincount(elem.ravel(), minlength=N)
+    rows = np.repeat(np.arange(N), np.diff(rp))
+    diag = rows == col
+    mcount = np.where(diag, deg[rows], 2)
+    u2 = 2.0 ** -48
+    per = 65.1 + 0.1 * kmax + (2 * kmax + 1) / 32 + np.where(diag, 3.0, 0.0)
+    bound = (per + 3.0 * mcount + 0.05) * u2 * so
+    err = np.abs(host(val) - vo)
+    assert (err <= bound).all(), (kmax, float((err / np.maximum(so, 1e-300)).max() / u2))
+    print("kappa_A max %.1f: worst error %.1f u^2 of the scale" % (kmax, float((err / np.maximum(so, 1e-300)).max() / u2)))
+
+
 @pytest.mark.parametrize("d", [2, 3])
 def test_inputs_beyond_the_float_float_range_are_reported(d):
     """Where a float-float result cannot keep its precision the kernels say so (FEM_ERR_RANGE) instead of
