@@ -255,6 +255,23 @@ int fem_cg_solve(fem_pattern_t p, const double* node, const double* k, const uin
                  const double* gD, double* u, int max_iter, double rtol, int* iters, double* relres,
                  fem_stream_t stream);
 
+/* ---- the same solve with the assembled matrix ---------------------------------------------------------
+ * fem_csr_spmv: y = A x with the pattern's CSR structure (row_ptr, col_idx) and the values val [nnz]
+ * (device; e.g. from fem_assemble_stiffness or fem_assemble), x, y [N] (device, distinct). With is_bd
+ * [N] (uint8, nullable) it is the Dirichlet-eliminated operator of fem_apply_dirichlet: a row of an
+ * eliminated vertex gives y_i = x_i, and the columns of eliminated vertices are skipped. Each row is
+ * summed by one thread in column order (FP64 multiply-adds), so the result is bitwise reproducible; it
+ * agrees with fem_apply_stiffness within rounding. Errors: FEM_ERR_ARG (null or misaligned arrays,
+ * x == y).
+ * fem_cg_solve_csr: the reduced solve of fem_cg_solve (same arguments, outputs, stopping rule and
+ * errors) with the operator fem_csr_spmv of the assembled values val instead of the matrix-free one:
+ * the matrix is formed once, and an iteration reads val and col_idx instead of recomputing the elements.
+ * The paper's own route: A is assembled (Sec. 3.1), then solved on freeNode (Sec. 3.3). */
+int fem_csr_spmv(fem_pattern_t p, const double* val, const double* x, const uint8_t* is_bd, double* y,
+                 fem_stream_t stream);
+int fem_cg_solve_csr(fem_pattern_t p, const double* val, const uint8_t* is_bd, const double* b, const double* gD,
+                     double* u, int max_iter, double rtol, int* iters, double* relres, fem_stream_t stream);
+
 /* ---- load vector with rules of any order ("Numerical Quadrature") ---------------------------------
  * I_n(f) = |tau| sum_q w_q f(p_q) on each simplex, with the conical-product Gauss rule of n points per
  * direction (n^d points, exact for total degree 2n - 1; 1 <= n <= FEM_RULE_MAX_N), built by the library

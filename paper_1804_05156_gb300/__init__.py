@@ -69,6 +69,8 @@ def lib():
             "fem_quad_rule": (I32, [I32, I32, P, P, P]),
             "fem_apply_stiffness": (I32, [P, P, P, P, P, P, P]),
             "fem_cg_solve": (I32, [P, P, P, P, P, P, P, I32, C.c_double, P, P, P]),
+            "fem_csr_spmv": (I32, [P, P, P, P, P, P]),
+            "fem_cg_solve_csr": (I32, [P, P, P, P, P, P, I32, C.c_double, P, P, P]),
             "fem_rule_points": (I32, [P, P, I32, P, P]),
             "fem_assemble_rhs_rule": (I32, [P, P, I32, I32, P, P, P]),
             "fem_side_points": (I32, [P, P, P, P]),
@@ -247,6 +249,24 @@ def fem_cg_solve(p: Pattern, node, k, is_bd, b, gD=None, u=None, max_iter=10000,
     it, rr = C.c_int(), C.c_double()
     _check(lib().fem_cg_solve(p.handle, _ptr(node), _ptr(k), _ptr(is_bd), _ptr(b), _ptr(gD), _ptr(u), int(max_iter),
                               float(rtol), C.byref(it), C.byref(rr), _stream(stream)))
+    return u, it.value, rr.value
+
+
+def fem_csr_spmv(p: Pattern, val, x, is_bd=None, y=None, stream=None):
+    """y = A x with the pattern's CSR structure and the values val (is_bd: the eliminated operator)."""
+    if y is None:
+        y = torch.empty_like(x)
+    _check(lib().fem_csr_spmv(p.handle, _ptr(val), _ptr(x), _ptr(is_bd), _ptr(y), _stream(stream)))
+    return y
+
+
+def fem_cg_solve_csr(p: Pattern, val, is_bd, b, gD=None, u=None, max_iter=10000, rtol=1e-10, stream=None):
+    """Reduced Dirichlet solve by conjugate gradients on the assembled matrix val: (u [N], iterations, relres)."""
+    if u is None:
+        u = torch.empty(p.N, dtype=torch.float64, device=b.device)
+    it, rr = C.c_int(), C.c_double()
+    _check(lib().fem_cg_solve_csr(p.handle, _ptr(val), _ptr(is_bd), _ptr(b), _ptr(gD), _ptr(u), int(max_iter),
+                                  float(rtol), C.byref(it), C.byref(rr), _stream(stream)))
     return u, it.value, rr.value
 
 

@@ -1,4 +1,5 @@
-// Conjugate gradients on the Dirichlet-eliminated system, driven by the matrix-free operator.
+// Conjugate gradients on the Dirichlet-eliminated system, driven by the matrix-free operator
+// (fem_cg_solve) or by the assembled CSR matrix (fem_cg_solve_csr, with the product fem_csr_spmv).
 //
 // Sec. 3.3 ends the method with the reduced solve u(freeNode) = A(freeNode, freeNode) \ b(freeNode), after
 // the boundary values are lifted out: b <- b - A u_D. Here the stiffness matrix is never formed. The lift
@@ -194,27 +195,71 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_direction(int64_t N, const d
   }
 }
 
+// y = A x for the assembled CSR values, one thread per row: the row's entries in order, four at a time
+// (their column indices and values, then the four x values, then four FP64 multiply-adds), so that
+// several independent loads are in flight per thread; the sum order is fixed, so the result is bitwise
+// reproducible. (A group of lanes per row with a shuffle tree was 3.5x slower: its dependent chain of
+// row_ptr, col, x loads per row left too few rows in flight.) With is_bd, the Dirichlet-eliminated
+// operator: a row of an eliminated vertex gives y_i = x_i and the columns of eliminated vertices are
+// skipped.
+__global__ void __launch_bounds__(256) k_csr_spmv(int64_t N, const int32_t* __restrict__ row_ptr,
+                                                  const int32_t* __restrict__ col, const double* __restrict__ val,
+                                                  const double* __restrict__ x, const uint8_t* __restrict__ isbd,
+                                                  double* __restrict__ y) {
+  for (int64_t R = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; R < N; R += (int64_t)gridDim.x * blockDim.x) {
+    if (isbd && isbd[R]) {
+      y[R] = x[R];
+      continue;
+    }
+    const int a = __ldg(row_ptr + R), e = __ldg(row_ptr + R + 1);
+    double sum = 0.0;
+    int q = a;
+    for (; q + 4 <= e; q += 4) {
+      int c[4];
+      double v[4], xv[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        c[j] = __ldg(col + q + j);
+        v[j] = __ldg(val + q + j);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) xv[j] = (!isbd || !__ldg(isbd + c[j])) ? __ldg(x + c[j]) : 0.0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sum = __fma_rn(v[j], xv[j], sum);
+    }
+    for (; q < e; ++q) {
+      const int c = __ldg(col + q);
+      if (!isbd || !__ldg(isbd + c)) sum = __fma_rn(__ldg(val + q), __ldg(x + c), sum);
+    }
+    y[R] = sum;
+  }
+}
+
 }  // namespace
 }  // namespace fem
 
 using fem::set_error;
 
-extern "C" int fem_cg_solve(fem_pattern_t p, const double* node, const double* k, const uint8_t* is_bd,
-                            const double* b, const double* gD, double* u, int max_iter, double rtol, int* iters,
-                            double* relres, fem_stream_t stream) {
+namespace {
+
+int launch_spmv(const fem::Pattern& P, const double* val, const double* x, const uint8_t* is_bd, double* y,
+                cudaStream_t s) {
   using namespace fem;
-  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
-  const Pattern& P = p->P;
-  if (max_iter < 0 || !(rtol >= 0.0)) return set_error(FEM_ERR_ARG, "max_iter must be >= 0 and rtol >= 0");
-  if (P.N > 0 && (!node || !is_bd || !b || !u)) return set_error(FEM_ERR_ARG, "node, is_bd, b and u are required");
-  auto al = [](const void* q) { return ((uintptr_t)q % 8) == 0; };
-  if (!al(node) || !al(k) || !al(b) || !al(gD) || !al(u)) return set_error(FEM_ERR_ARG, "misaligned double array");
-  if (u == b || u == gD) return set_error(FEM_ERR_ARG, "u must not alias b or gD");
+  k_csr_spmv<<<grid_for(P.N, 256), 256, 0, s>>>(P.N, P.row_ptr, P.col_idx, val, x, is_bd, y);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? FEM_OK : cuda_error(e, "k_csr_spmv");
+}
+
+// The CG iteration of both entry points; apply(x, is_bd, y) is the operator (is_bd null: the full one).
+template <class Apply>
+int cg_run(const fem::Pattern& P, Apply apply, const uint8_t* is_bd, const double* b, const double* gD, double* u,
+           int max_iter, double rtol, int* iters, double* relres, cudaStream_t s) {
+  using namespace fem;
   if (iters) *iters = 0;
   if (relres) *relres = 0.0;
   const int64_t N = P.N;
   if (N == 0) return FEM_OK;
-  cudaStream_t s = (cudaStream_t)stream;
   const int nb = red_blocks(N);
   // workspace: r, p, q [N]; partials rr (two, alternating), pq [nb]; doubles then ints
   const size_t nd = 3 * (size_t)N + 3 * (size_t)nb + 2;
@@ -254,12 +299,12 @@ extern "C" int fem_cg_solve(fem_pattern_t p, const double* node, const double* k
   } while (0)
   // lift: r = b - A u_D on free rows
   CG_LAUNCH(k_cg_lift, grid_for(N, 256), 256, N, is_bd, gD, pv);
-  CG_TRY(fem_apply_stiffness(p, node, k, pv, nullptr, q, stream));
+  CG_TRY(apply(pv, nullptr, q));
   CG_LAUNCH(k_cg_init, nb, kRedThreads, N, is_bd, b, gD, q, u, r, pv, part_rr[0]);
   CG_LAUNCH(k_cg_start, 1, 32, part_rr[0], nb, dsc, isc);
   for (it = 0; it < max_iter; ++it) {
     const int par = it & 1;
-    CG_TRY(fem_apply_stiffness(p, node, k, pv, is_bd, q, stream));
+    CG_TRY(apply(pv, is_bd, q));
     CG_LAUNCH(k_cg_pq, nb, kRedThreads, N, pv, q, part_pq, isc);
     CG_LAUNCH(k_cg_update, nb, kRedThreads, N, pv, q, u, r, part_rr[par], part_pq, part_rr[1 - par], isc);
     CG_LAUNCH(k_cg_direction, nb, kRedThreads, N, r, pv, part_rr[par], part_rr[1 - par], tol2, dsc, isc);
@@ -282,4 +327,53 @@ done_label:
 #undef CG_LAUNCH
   cudaFreeAsync(ws, s);
   return rc;
+}
+
+bool aligned8(const void* q) { return ((uintptr_t)q % 8) == 0; }
+
+}  // namespace
+
+extern "C" int fem_cg_solve(fem_pattern_t p, const double* node, const double* k, const uint8_t* is_bd,
+                            const double* b, const double* gD, double* u, int max_iter, double rtol, int* iters,
+                            double* relres, fem_stream_t stream) {
+  using namespace fem;
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  const Pattern& P = p->P;
+  if (max_iter < 0 || !(rtol >= 0.0)) return set_error(FEM_ERR_ARG, "max_iter must be >= 0 and rtol >= 0");
+  if (P.N > 0 && (!node || !is_bd || !b || !u)) return set_error(FEM_ERR_ARG, "node, is_bd, b and u are required");
+  if (!aligned8(node) || !aligned8(k) || !aligned8(b) || !aligned8(gD) || !aligned8(u))
+    return set_error(FEM_ERR_ARG, "misaligned double array");
+  if (u == b || u == gD) return set_error(FEM_ERR_ARG, "u must not alias b or gD");
+  auto apply = [&](const double* x, const uint8_t* bd, double* y) {
+    return fem_apply_stiffness(p, node, k, x, bd, y, stream);
+  };
+  return cg_run(P, apply, is_bd, b, gD, u, max_iter, rtol, iters, relres, (cudaStream_t)stream);
+}
+
+extern "C" int fem_csr_spmv(fem_pattern_t p, const double* val, const double* x, const uint8_t* is_bd, double* y,
+                            fem_stream_t stream) {
+  using namespace fem;
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  const Pattern& P = p->P;
+  if (P.N == 0) return FEM_OK;
+  if (!val || !x || !y) return set_error(FEM_ERR_ARG, "val, x and y are required");
+  if (!aligned8(val) || !aligned8(x) || !aligned8(y)) return set_error(FEM_ERR_ARG, "misaligned double array");
+  if (x == y) return set_error(FEM_ERR_ARG, "x and y must be distinct");
+  return launch_spmv(P, val, x, is_bd, y, (cudaStream_t)stream);
+}
+
+extern "C" int fem_cg_solve_csr(fem_pattern_t p, const double* val, const uint8_t* is_bd, const double* b,
+                                const double* gD, double* u, int max_iter, double rtol, int* iters, double* relres,
+                                fem_stream_t stream) {
+  using namespace fem;
+  if (!p) return set_error(FEM_ERR_ARG, "null pattern");
+  const Pattern& P = p->P;
+  if (max_iter < 0 || !(rtol >= 0.0)) return set_error(FEM_ERR_ARG, "max_iter must be >= 0 and rtol >= 0");
+  if (P.N > 0 && (!val || !is_bd || !b || !u)) return set_error(FEM_ERR_ARG, "val, is_bd, b and u are required");
+  if (!aligned8(val) || !aligned8(b) || !aligned8(gD) || !aligned8(u))
+    return set_error(FEM_ERR_ARG, "misaligned double array");
+  if (u == b || u == gD || u == val) return set_error(FEM_ERR_ARG, "u must not alias val, b or gD");
+  const cudaStream_t s = (cudaStream_t)stream;
+  auto apply = [&](const double* x, const uint8_t* bd, double* y) { return launch_spmv(P, val, x, bd, y, s); };
+  return cg_run(P, apply, is_bd, b, gD, u, max_iter, rtol, iters, relres, s);
 }

@@ -1200,6 +1200,69 @@ def test_cg_matches_the_direct_reduced_solve(d):
     assert itz == 0 and relz == 0.0 and not host(uz).any()
 
 
+@pytest.mark.parametrize("case", ["sq37p", "kuhn7s", "delaunay3"])
+def test_csr_spmv_matches_the_assembled_product(case):
+    """fem_csr_spmv with the GPU's own assembled values: the plain product against scipy's CSR product of
+    the same arrays (within 1e-13 of each row's sum of |a_ij x_j|), the eliminated one against
+    fem_apply_stiffness's eliminated operator (within the parity bar of the same magnitudes: both sides
+    round differently), and the same bits on a second call."""
+    import scipy.sparse as sp
+    d, node, elem, k, _ = mesh_case(case)
+    N = node.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    fa.fem_pattern_set_locality(p, dev(node))
+    kd = dev(k if k is not None else np.ones(elem.shape[0]))
+    val = torch.empty(p.nnz, dtype=torch.float64, device="cuda")
+    fa.fem_assemble_stiffness(p, dev(node), kd, val)
+    isbd = torch.empty(N, dtype=torch.uint8, device="cuda")
+    fa.fem_boundary_nodes(p, None, isbd)
+    x = meshgen.normal(41, 3, N)
+    y = fa.fem_csr_spmv(p, val, dev(x))
+    fa.get_error()
+    rp, col, v = host(p.row_ptr).astype(np.int64), host(p.col_idx).astype(np.int64), host(val)
+    A = sp.csr_matrix((v, col, rp), shape=(N, N))
+    mag = sp.csr_matrix((np.abs(v), col, rp), shape=(N, N)) @ np.abs(x)
+    assert_close_scaled(host(y), A @ x, mag, tol=1e-13, what="csr product")
+    assert torch.equal(y, fa.fem_csr_spmv(p, val, dev(x)))
+    ye = fa.fem_csr_spmv(p, val, dev(x), isbd)
+    ya = torch.empty_like(ye)
+    fa.fem_apply_stiffness(p, dev(node), kd, dev(x), isbd, ya)
+    fa.get_error()
+    bd = host(isbd).astype(bool)
+    assert np.array_equal(host(ye)[bd], x[bd])
+    xm = np.where(bd, 0.0, x)
+    mag_e = sp.csr_matrix((np.abs(v), col, rp), shape=(N, N)) @ np.abs(xm)
+    assert_close_scaled(host(ye)[~bd], host(ya)[~bd], mag_e[~bd], what="eliminated csr product")
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_cg_on_the_assembled_matrix_matches_the_direct_reduced_solve(d):
+    """fem_cg_solve_csr with the GPU's assembled values (nonzero g_D, lognormal k, sine-product load)
+    against the oracle's direct solve of the same reduced system, and against the matrix-free CG: boundary
+    values exact, free values within the CG tolerance; the same bits and iteration count twice."""
+    node, elem, k = _cg_case(d, 24 if d == 2 else 6, 91 + d)
+    N = node.shape[0]
+    p = fa.Pattern(dev(elem), N)
+    fa.fem_pattern_set_locality(p, dev(node))
+    val, b = fa.assemble(p, dev(node), dev(k), fa.FEM_F_SINPROD)
+    fa.get_error()
+    isbd = torch.empty(N, dtype=torch.uint8, device="cuda")
+    fa.fem_boundary_nodes(p, None, isbd)
+    gD = 0.5 + node @ np.arange(1.0, d + 1.0)
+    u, it, rel = fa.fem_cg_solve_csr(p, val, isbd, b, dev(gD), rtol=1e-13)
+    fa.get_error()
+    assert 0 < it < 10 * N and rel <= 1e-13
+    rp, col, vo, _ = oracle.assemble(d, node, elem, k)
+    uo = oracle.solve_reduced(rp, col, vo, host(b), host(isbd), gD)
+    bd = host(isbd).astype(bool)
+    assert np.array_equal(host(u)[bd], gD[bd])
+    assert np.abs(host(u) - uo).max() <= 1e-10 * np.abs(uo).max(), np.abs(host(u) - uo).max()
+    um, itm, _ = fa.fem_cg_solve(p, dev(node), dev(k), isbd, b, dev(gD), rtol=1e-13)
+    assert np.abs(host(u) - host(um)).max() <= 1e-10 * np.abs(uo).max() and abs(it - itm) <= max(3, itm // 20)
+    u2, it2, rel2 = fa.fem_cg_solve_csr(p, val, isbd, b, dev(gD), rtol=1e-13)
+    assert torch.equal(u, u2) and it == it2 and rel == rel2
+
+
 @pytest.mark.parametrize("d", [2, 3])
 def test_cg_solution_converges_at_second_order(d):
     """-Laplace u = sin-product with u = 0 on the boundary, solved on the GPU by the load vector and the
