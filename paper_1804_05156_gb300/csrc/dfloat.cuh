@@ -160,7 +160,7 @@ __device__ __forceinline__ df2 df_from_double(double x) {
   return fast_two_sum(s.a, __fadd_rn(s.b, s.c));
 }
 
-// df approximation of a double that need not be exact (relative error ~2^-47): the leading 24 bits
+// df approximation of a double that need not be exact (relative error <= u^2 = 2^-48): the leading 24 bits
 // from the IEEE bits, the remaining 29 bits through one int32->float conversion.
 __device__ __forceinline__ df2 df_from_double_fast(double x) {
   const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
