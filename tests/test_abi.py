@@ -60,6 +60,9 @@ def test_host_side_argument_checks(libpath):
     assert L.fem_assemble(None, None, None, 0, None, None, None, 0, None) == fa.FEM_ERR_ARG
     assert L.fem_batch_plan(2, 0, None, None, None, C.byref(h), None) == fa.FEM_ERR_ARG
     assert L.fem_pattern_barrier_fault(None, 1, 16) == fa.FEM_ERR_ARG
+    assert L.fem_csr_spmv(None, None, None, None, None, None) == fa.FEM_ERR_ARG
+    assert L.fem_cg_solve_csr(None, None, None, None, None, None, 10, C.c_double(1e-8), None, None, None) == fa.FEM_ERR_ARG
+    assert L.fem_cg_solve(None, None, None, None, None, None, None, 10, C.c_double(1e-8), None, None, None) == fa.FEM_ERR_ARG
     assert L.fem_launch_count() >= 0
 
 
