@@ -255,7 +255,7 @@ __device__ __forceinline__ void load_packet(const float4* pk, const float2* pkb,
 template <int D, typename PW, bool FRESH>
 __device__ __forceinline__ void rows_of_warp(const RowArgs& g, int64_t R0, df2* acc, double* __restrict__ val,
                                              double* __restrict__ bvec) {
-  constexpr int U = (D == 2) ? 2 : 4;
+  constexpr int U = 3;  // measured: 2-D 3 against 2 and 4, 3-D 3 against 2, 4 and 6
   const PW* __restrict__ pw = static_cast<const PW*>(g.pw);
   const int lane = threadIdx.x & 31;
   const int64_t R = R0 + lane;
@@ -559,9 +559,10 @@ int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_
   const int64_t grid = (P->N + bt - 1) / bt;
   if (D == 2) {
     FEM_CUDA(cudaFuncSetAttribute(k_row_gather<2, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm));
-    // a quarter of the unified L1/shared storage as shared memory: fewer resident warps, but the L1 keeps
-    // a row's packet sectors until its next packets are read (measured: 0.194 against 0.203 ms)
-    FEM_CUDA(cudaFuncSetAttribute(k_row_gather<2, uint16_t>, cudaFuncAttributePreferredSharedMemoryCarveout, 25));
+    // a third of the unified L1/shared storage as shared memory: fewer resident warps, but the L1 keeps
+    // a row's packet sectors until its next packets are read (measured with three packets in flight per
+    // thread: 0.187 ms, against 0.195 at a quarter or a sixth, 0.190 at a half, 0.194 at two thirds)
+    FEM_CUDA(cudaFuncSetAttribute(k_row_gather<2, uint16_t>, cudaFuncAttributePreferredSharedMemoryCarveout, 33));
     FEM_LAUNCH((k_row_gather<2, uint16_t>), (int)grid, bt, gsm, s, g, val, b);
   } else {
     FEM_CUDA(cudaFuncSetAttribute(k_row_gather<3, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm));
