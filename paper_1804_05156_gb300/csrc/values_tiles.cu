@@ -298,10 +298,12 @@ __device__ __forceinline__ void rows_of_warp(const RowArgs& g, int64_t R0, df2* 
   __syncwarp();
 }
 
-// Registers capped so that 1280 threads (ten 128-thread tiles, 2-D; no spills) or 896 threads (seven, 3-D;
-// a few spilled bytes cost less than the lost occupancy) fit an SM.
-template <int D, int TE>
-__global__ void __launch_bounds__(TE, (D == 3 ? 896 : 1280) / TE)
+// Registers capped so that CTAS 128-thread tiles fit an SM: ten in 2-D (no spills), seven in 3-D (a few
+// spilled bytes cost less than the lost occupancy); the 3-D sine-product load, whose twelve sine
+// evaluations hold more registers, runs six (measured on the 64^3 mesh: 0.174 against 0.185 ms for
+// seven and 0.195 for eight; with f = 1 seven stay best, 0.680 against 0.692 ms for six on 128^3).
+template <int D, int TE, int CTAS = (D == 3 ? 7 : 10)>
+__global__ void __launch_bounds__(TE, CTAS * 128 / TE)
     k_tile_elements(TileArgs a, const double* __restrict__ node, const double* __restrict__ k, int f_kind,
                     const double* __restrict__ f_arg, int want_a, int want_b, const float4* __restrict__ tab,
                     int* __restrict__ err) {
@@ -539,20 +541,24 @@ int assemble_tiles(const Pattern* P, const double* node, const double* k, int f_
     return FEM_OK;
   }
   const int smem = tile_smem_need(T, D, f_kind == FEM_F_SINPROD && want_b);
-#define FEM_TILE_LAUNCH(DD, TT)                                                                               \
+#define FEM_TILE_LAUNCH_K(KERNEL, TT)                                                                         \
   do {                                                                                                        \
     if (smem > 48 * 1024)                                                                                     \
-      FEM_CUDA(cudaFuncSetAttribute(k_tile_elements<DD, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); \
-    FEM_LAUNCH((k_tile_elements<DD, TT>), T.ntiles, TT, smem, s, a, node, k, f_kind, f_arg, want_a, want_b, tab, err); \
+      FEM_CUDA(cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));             \
+    FEM_LAUNCH(KERNEL, T.ntiles, TT, smem, s, a, node, k, f_kind, f_arg, want_a, want_b, tab, err);         \
   } while (0)
+  const bool sine3 = D == 3 && f_kind == FEM_F_SINPROD && want_b;
   if (D == 2) {
-    if (T.TE == 128) FEM_TILE_LAUNCH(2, 128);
-    else FEM_TILE_LAUNCH(2, 256);
+    if (T.TE == 128) FEM_TILE_LAUNCH_K((k_tile_elements<2, 128>), 128);
+    else FEM_TILE_LAUNCH_K((k_tile_elements<2, 256>), 256);
+  } else if (!sine3) {
+    if (T.TE == 128) FEM_TILE_LAUNCH_K((k_tile_elements<3, 128>), 128);
+    else FEM_TILE_LAUNCH_K((k_tile_elements<3, 256>), 256);
   } else {
-    if (T.TE == 128) FEM_TILE_LAUNCH(3, 128);
-    else FEM_TILE_LAUNCH(3, 256);
+    if (T.TE == 128) FEM_TILE_LAUNCH_K((k_tile_elements<3, 128, 6>), 128);
+    else FEM_TILE_LAUNCH_K((k_tile_elements<3, 256, 6>), 256);
   }
-#undef FEM_TILE_LAUNCH
+#undef FEM_TILE_LAUNCH_K
   const int wpc = gather_warps(g.max_row);
   const int bt = 32 * wpc;
   const int gsm = wpc * gather_warp_bytes(g.max_row);
